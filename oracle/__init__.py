@@ -1,0 +1,226 @@
+"""FP64 CPU oracle of the RealLiFe HSGD hot path (test infrastructure only).
+
+Only the test-suite, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package.  The product path (the CUDA library and
+its Python binding) never loads it and shares no code with it; the two meet only
+through the seeded inputs of ``scenegen``.
+
+The arithmetic lives in ``reallife_oracle.c`` (plain loops, ``double``), built
+here with gcc and loaded through ctypes.  Each wrapper below states the equation
+of the paper it follows; see the C file's header for the readings of the paper
+it fixes (plane spacing, camera convention, loss, tie rule, level schedule).
+
+Parity status: every function is pinned by the tests in
+``tests/test_oracle_pins.py`` (closed forms, invariants, brute force, finite
+differences, hand-derived fixtures under ``tests/golden/``).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "reallife_oracle.c")
+_LIB_PATH = os.path.join(_HERE, "libreallife_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+
+class _Cam(ctypes.Structure):
+    _fields_ = [("K", ctypes.c_double * 9), ("R", ctypes.c_double * 9), ("t", ctypes.c_double * 3)]
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (IEEE double, no FMA contraction) if needed."""
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+        tmp = _LIB_PATH + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
+                               "-shared", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = ctypes.CDLL(build())
+            P = ctypes.POINTER
+            d, i, dp = ctypes.c_double, ctypes.c_int, P(ctypes.c_double)
+            cam = P(_Cam)
+            u8p, u64p = P(ctypes.c_uint8), P(ctypes.c_uint64)
+            lib.orc_plane_inverse_depths.argtypes = [i, d, d, dp]
+            lib.orc_camera_at_level.argtypes = [cam, i, cam]
+            lib.orc_view_to_ref.argtypes = [cam, cam, d, d, d, dp, dp]
+            lib.orc_view_to_ref.restype = i
+            lib.orc_render.argtypes = [dp, i, i, i, d, d, cam, cam, dp]
+            lib.orc_vjp.argtypes = [dp, i, i, i, d, d, cam, cam, i, dp, dp]
+            lib.orc_loss_grad.argtypes = [dp, i, i, i, d, d, cam, dp, cam, i, dp, dp]
+            lib.orc_loss_grad.restype = d
+            lib.orc_alpha_weights.argtypes = [dp, i, i, i, dp]
+            lib.orc_select_topk.argtypes = [dp, i, i, i, i, u8p, u64p]
+            lib.orc_downsample2.argtypes = [dp, i, i, i, i, dp]
+            lib.orc_down_levels.argtypes = [dp, i, i, i, i, i, dp]
+            lib.orc_hsgd_step.argtypes = [dp, i, i, i, d, d, cam, dp, cam, i, i, d, i, i, u8p, u8p, dp]
+            lib.orc_hsgd_step.restype = i
+            lib.orc_gd_step.argtypes = [dp, i, i, i, d, d, cam, dp, cam, i, d, i, i, dp]
+            lib.orc_gd_step.restype = i
+            _lib = lib
+    return _lib
+
+
+def _cam(c) -> _Cam:
+    s = _Cam()
+    s.K[:] = np.asarray(c.K, dtype=np.float64).reshape(9).tolist()
+    s.R[:] = np.asarray(c.R, dtype=np.float64).reshape(9).tolist()
+    s.t[:] = np.asarray(c.t, dtype=np.float64).reshape(3).tolist()
+    return s
+
+
+def _cams(cs):
+    arr = (_Cam * len(cs))()
+    for j, c in enumerate(cs):
+        arr[j] = _cam(c)
+    return arr
+
+
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _ptr(a: np.ndarray, ct=ctypes.c_double):
+    return a.ctypes.data_as(ctypes.POINTER(ct))
+
+
+def plane_inverse_depths(D: int, near: float, far: float) -> np.ndarray:
+    """rho_d, uniform in inverse depth from 1/far (d=0) to 1/near (d=D-1)."""
+    out = np.empty(D)
+    _load().orc_plane_inverse_depths(D, near, far, _ptr(out))
+    return out
+
+
+def camera_at_level(cam, level: int):
+    """(K, R, t) of ``cam`` at pyramid level ``level`` (f / 2^l, c' = (c+0.5)/2^l - 0.5)."""
+    out = _Cam()
+    _load().orc_camera_at_level(ctypes.byref(_cam(cam)), level, ctypes.byref(out))
+    return (np.array(out.K[:]).reshape(3, 3), np.array(out.R[:]).reshape(3, 3), np.array(out.t[:]))
+
+
+def view_to_ref(ref, view, z: float, u: float, v: float):
+    """Reference pixel hit by the view's ray through (u, v) on the plane at depth z; None if not met."""
+    px, py = ctypes.c_double(), ctypes.c_double()
+    ok = _load().orc_view_to_ref(ctypes.byref(_cam(ref)), ctypes.byref(_cam(view)), z, u, v,
+                                 ctypes.byref(px), ctypes.byref(py))
+    return (px.value, py.value) if ok else None
+
+
+def render(M, near: float, far: float, ref, view) -> np.ndarray:
+    """Eq. (eq_render) / (eq_over): view of the MPI ``M[D][H][W][4]`` -> ``[H][W][3]``."""
+    M = _f64(M)
+    D, H, W, _ = M.shape
+    out = np.empty((H, W, 3))
+    _load().orc_render(_ptr(M), D, H, W, near, far, ctypes.byref(_cam(ref)), ctypes.byref(_cam(view)), _ptr(out))
+    return out
+
+
+def vjp(M, near: float, far: float, ref, views, g_out) -> np.ndarray:
+    """dL/dM given dL/dC for each view (``g_out[N][H][W][3]``): the exact adjoint of warp + composite."""
+    M = _f64(M)
+    D, H, W, _ = M.shape
+    g_out = _f64(g_out)
+    grad = np.zeros_like(M)
+    _load().orc_vjp(_ptr(M), D, H, W, near, far, ctypes.byref(_cam(ref)), _cams(views), len(views),
+                    _ptr(g_out), _ptr(grad))
+    return grad
+
+
+def loss_grad(M, near: float, far: float, ref, views, images, want_grad: bool = True, want_renders: bool = False):
+    """Photometric loss 1/(2N) sum (C - I)^2 and its gradient dL/dM (dense)."""
+    M = _f64(M)
+    D, H, W, _ = M.shape
+    images = _f64(images)
+    N = len(views)
+    grad = np.empty_like(M) if want_grad else None
+    rend = np.empty((N, H, W, 3)) if want_renders else None
+    L = _load().orc_loss_grad(_ptr(M), D, H, W, near, far, ctypes.byref(_cam(ref)), _ptr(images), _cams(views), N,
+                              _ptr(grad) if want_grad else None, _ptr(rend) if want_renders else None)
+    return L, grad, rend
+
+
+def alpha_weights(M) -> np.ndarray:
+    """Reference-view A_d = alpha_d prod_{j>d} (1 - alpha_j) -> ``[D][H][W]`` (Eq. eq_gradient)."""
+    M = _f64(M)
+    D, H, W, _ = M.shape
+    A = np.empty((D, H, W))
+    _load().orc_alpha_weights(_ptr(M), D, H, W, _ptr(A))
+    return A
+
+
+def select_topk(A, k: int):
+    """Top-k planes per pixel by key (ties to lower d), ascending: (S[k][H][W] uint8, mask[H][W] uint64)."""
+    A = _f64(A)
+    D, H, W = A.shape
+    S = np.empty((k, H, W), dtype=np.uint8)
+    mask = np.empty((H, W), dtype=np.uint64)
+    _load().orc_select_topk(_ptr(A), D, H, W, k, _ptr(S, ctypes.c_uint8), _ptr(mask, ctypes.c_uint64))
+    return S, mask
+
+
+def down(x, level: int) -> np.ndarray:
+    """Down^l over the two spatial axes of ``x[P][H][W][C]`` (l successive 2x2 box averages)."""
+    x = _f64(x)
+    P, H, W, C = x.shape
+    out = np.empty((P, H >> level, W >> level, C))
+    _load().orc_down_levels(_ptr(x), P, H, W, C, level, _ptr(out))
+    return out
+
+
+def hsgd_step(M, near, far, ref, views, images, k: int, lam: float = 1.0, clamp: bool = True, level: int = 0,
+              S_pin=None):
+    """One HSGD iteration (Sec. 3.3) at ``level`` on a copy of ``M``: returns (M_new, loss, S)."""
+    M = _f64(M).copy()
+    D, H, W, _ = M.shape
+    images = _f64(images)
+    h, w = H >> level, W >> level
+    S = np.empty((k, h, w), dtype=np.uint8)
+    pin = None
+    if S_pin is not None:
+        pin = np.ascontiguousarray(S_pin, dtype=np.uint8)
+        assert pin.shape == (k, h, w)
+    L = ctypes.c_double()
+    rc = _load().orc_hsgd_step(_ptr(M), D, H, W, near, far, ctypes.byref(_cam(ref)), _ptr(images), _cams(views),
+                               len(views), k, lam, int(clamp), level,
+                               _ptr(pin, ctypes.c_uint8) if pin is not None else None, _ptr(S, ctypes.c_uint8),
+                               ctypes.byref(L))
+    if rc:
+        raise ValueError("oracle hsgd_step: invalid arguments")
+    return M, L.value, S
+
+
+def gd_step(M, near, far, ref, views, images, lam: float = 1.0, clamp: bool = True, level: int = 0):
+    """Dense analytic gradient-descent step (Sec. 3.1) at ``level``: returns (M_new, loss)."""
+    M = _f64(M).copy()
+    D, H, W, _ = M.shape
+    images = _f64(images)
+    L = ctypes.c_double()
+    rc = _load().orc_gd_step(_ptr(M), D, H, W, near, far, ctypes.byref(_cam(ref)), _ptr(images), _cams(views),
+                             len(views), lam, int(clamp), level, ctypes.byref(L))
+    if rc:
+        raise ValueError("oracle gd_step: invalid arguments")
+    return M, L.value
+
+
+def refine(M, near, far, ref, views, images, k: int, schedule=(2, 1, 0), lam: float = 1.0, clamp: bool = True,
+           S_pins=None):
+    """HSGD refinement: one ``hsgd_step`` per entry of ``schedule``; returns (M, losses, selections)."""
+    losses, sels = [], []
+    for it, level in enumerate(schedule):
+        M, L, S = hsgd_step(M, near, far, ref, views, images, k, lam, clamp, level,
+                            None if S_pins is None else S_pins[it])
+        losses.append(L)
+        sels.append(S)
+    return M, losses, sels

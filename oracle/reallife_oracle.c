@@ -1,0 +1,426 @@
+/*
+ * reallife_oracle.c -- plain, slow FP64 CPU oracle of the RealLiFe HSGD hot path.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product path may link, load or call
+ * this file: only the test-suite, the package smoke check and the CPU-baseline leg
+ * of the benchmark use it.  It shares no code, header, table or constant with the
+ * CUDA library; every function is written from the paper's equations, in the
+ * paper's order, with straightforward loops and no blocking or fusion.
+ *
+ * Conventions (the readings of the paper this oracle fixes):
+ *   - MPI M[d][y][x][c], c = (R,G,B,alpha), d = 0 farthest ... D-1 nearest, so the
+ *     over operator of Eq. (eq_over) puts the unoccluded plane at the top index.
+ *   - Plane depths are uniform in inverse depth: rho_d = 1/far + d/(D-1) (1/near - 1/far)
+ *     (rho_0 = 1/far when D = 1).  The paper does not state the spacing.
+ *   - Cameras are world->camera, x_cam = R X + t; a pixel is K x_cam / z, pixel centres
+ *     at integer coordinates.  Under this convention Eq. (eq_homo) is exactly the
+ *     plane-induced homography of the plane z = z_d in the reference frame.
+ *   - Warping the MPI into a view (Eq. eq_render) samples plane d at the reference
+ *     pixel where the ray of the view's pixel meets that plane (ray-plane intersection,
+ *     computed geometrically here, not through Eq. eq_homo's matrix), with bilinear
+ *     interpolation and zero padding per tap (grid_sample with zero padding, Sec. 3.2).
+ *     A ray that meets the plane behind the camera samples nothing.
+ *   - Composite: C = sum_d c_d alpha_d prod_{j>d} (1 - alpha_j), no background (Eq. eq_over).
+ *   - Photometric loss: L = 1/(2N) sum_i sum_q sum_ch (C_i(q) - I_i(q))^2; the analytic
+ *     gradient step of Sec. 3.1 is read as descent, M <- M - lambda dL/dM.
+ *   - Selection key: the reference-view alpha weight A_d = alpha_d prod_{j>d}(1-alpha_j)
+ *     (Eq. eq_gradient / eq_overA); keep the k largest per pixel, ties to the lower d,
+ *     indices stored in ascending depth order (Sec. 3.3, "Gradient Sparsification").
+ *   - Levels: an iteration at level l works on Down^l(M) and Down^l(I) (2x2 box
+ *     averages, Sec. 3.2 "Hierarchical PSV construction"), intrinsics scaled by 2^-l,
+ *     and adds the nearest-neighbour upsampled masked step to the full MPI (the
+ *     restore operator R(., S) of Sec. 3.3 followed by the coarse-to-fine upsampling).
+ *   - Update: M[d] <- clamp(M[d] - lambda g[d], 0, 1) for selected d (clamp optional).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+typedef struct {
+    double K[9]; /* row-major intrinsics */
+    double R[9]; /* row-major world->camera rotation */
+    double t[3]; /* world->camera translation */
+} orc_camera;
+
+/* ---------------------------------------------------------------- geometry */
+
+/* Plane inverse depths (uniform in inverse depth between far and near). */
+void orc_plane_inverse_depths(int D, double near_, double far_, double* rho) {
+    for (int d = 0; d < D; ++d)
+        rho[d] = (D == 1) ? 1.0 / far_ : 1.0 / far_ + ((double)d / (double)(D - 1)) * (1.0 / near_ - 1.0 / far_);
+}
+
+static void inv3(const double* A, double* B) {
+    double det = A[0] * (A[4] * A[8] - A[5] * A[7]) - A[1] * (A[3] * A[8] - A[5] * A[6]) +
+                 A[2] * (A[3] * A[7] - A[4] * A[6]);
+    B[0] = (A[4] * A[8] - A[5] * A[7]) / det;
+    B[1] = (A[2] * A[7] - A[1] * A[8]) / det;
+    B[2] = (A[1] * A[5] - A[2] * A[4]) / det;
+    B[3] = (A[5] * A[6] - A[3] * A[8]) / det;
+    B[4] = (A[0] * A[8] - A[2] * A[6]) / det;
+    B[5] = (A[2] * A[3] - A[0] * A[5]) / det;
+    B[6] = (A[3] * A[7] - A[4] * A[6]) / det;
+    B[7] = (A[1] * A[6] - A[0] * A[7]) / det;
+    B[8] = (A[0] * A[4] - A[1] * A[3]) / det;
+}
+
+/* Camera scaled to pyramid level l: focal lengths / 2^l, principal point (c + 0.5)/2^l - 0.5. */
+void orc_camera_at_level(const orc_camera* in, int level, orc_camera* out) {
+    *out = *in;
+    double s = ldexp(1.0, -level);
+    out->K[0] = in->K[0] * s;
+    out->K[1] = in->K[1] * s;
+    out->K[4] = in->K[4] * s;
+    out->K[2] = (in->K[2] + 0.5) * s - 0.5;
+    out->K[5] = (in->K[5] + 0.5) * s - 0.5;
+}
+
+/*
+ * Geometric warp (Eq. eq_render's omega, Eq. eq_homo by construction): pixel (u,v) of
+ * camera `view`, plane z_ref = z of the reference frustum -> reference pixel (px,py).
+ * Casts the view's ray through (u,v), intersects it with the plane, projects into the
+ * reference camera.  Returns 0 when the plane is not met in front of the view.
+ */
+int orc_view_to_ref(const orc_camera* ref, const orc_camera* view, double z, double u, double v,
+                    double* px, double* py) {
+    double Kinv[9];
+    inv3(view->K, Kinv);
+    double m[3] = {Kinv[0] * u + Kinv[1] * v + Kinv[2], Kinv[3] * u + Kinv[4] * v + Kinv[5],
+                   Kinv[6] * u + Kinv[7] * v + Kinv[8]};
+    /* world-frame ray: origin = camera centre -R^T t, direction R^T m */
+    double Cw[3], dw[3];
+    for (int a = 0; a < 3; ++a) {
+        Cw[a] = -(view->R[0 * 3 + a] * view->t[0] + view->R[1 * 3 + a] * view->t[1] + view->R[2 * 3 + a] * view->t[2]);
+        dw[a] = view->R[0 * 3 + a] * m[0] + view->R[1 * 3 + a] * m[1] + view->R[2 * 3 + a] * m[2];
+    }
+    /* into the reference camera frame */
+    double Cr[3], dr[3];
+    for (int a = 0; a < 3; ++a) {
+        Cr[a] = ref->R[a * 3 + 0] * Cw[0] + ref->R[a * 3 + 1] * Cw[1] + ref->R[a * 3 + 2] * Cw[2] + ref->t[a];
+        dr[a] = ref->R[a * 3 + 0] * dw[0] + ref->R[a * 3 + 1] * dw[1] + ref->R[a * 3 + 2] * dw[2];
+    }
+    if (!(dr[2] > 0.0) || !(z - Cr[2] > 0.0)) return 0;
+    double s = (z - Cr[2]) / dr[2];
+    double X[3] = {Cr[0] + s * dr[0], Cr[1] + s * dr[1], z};
+    const double* K = ref->K;
+    double hx = K[0] * X[0] + K[1] * X[1] + K[2] * X[2];
+    double hy = K[3] * X[0] + K[4] * X[1] + K[5] * X[2];
+    double hz = K[6] * X[0] + K[7] * X[1] + K[8] * X[2];
+    *px = hx / hz;
+    *py = hy / hz;
+    return 1;
+}
+
+/* Bilinear taps at (x,y): integer corners and weights; taps outside the image get weight 0. */
+static void bilinear_taps(double x, double y, int W, int H, int tx[4], int ty[4], double w[4]) {
+    double x0 = floor(x), y0 = floor(y);
+    double fx = x - x0, fy = y - y0;
+    int ix = (int)x0, iy = (int)y0;
+    tx[0] = ix;     ty[0] = iy;     w[0] = (1.0 - fx) * (1.0 - fy);
+    tx[1] = ix + 1; ty[1] = iy;     w[1] = fx * (1.0 - fy);
+    tx[2] = ix;     ty[2] = iy + 1; w[2] = (1.0 - fx) * fy;
+    tx[3] = ix + 1; ty[3] = iy + 1; w[3] = fx * fy;
+    for (int k = 0; k < 4; ++k)
+        if (tx[k] < 0 || tx[k] >= W || ty[k] < 0 || ty[k] >= H) w[k] = 0.0;
+}
+
+/* ------------------------------------------------------------ forward model */
+
+typedef struct {
+    int tx[4], ty[4];
+    double w[4];
+    double m[4]; /* sampled (R,G,B,alpha) */
+} sample_t;
+
+static void sample_plane(const double* M, int d, int H, int W, int valid, double px, double py, sample_t* s) {
+    memset(s, 0, sizeof(*s));
+    if (!valid) return;
+    bilinear_taps(px, py, W, H, s->tx, s->ty, s->w);
+    for (int k = 0; k < 4; ++k) {
+        if (s->w[k] == 0.0) continue;
+        const double* v = M + (((size_t)d * H + s->ty[k]) * W + s->tx[k]) * 4;
+        for (int c = 0; c < 4; ++c) s->m[c] += s->w[k] * v[c];
+    }
+}
+
+/*
+ * Render one view of size H x W (same size as the MPI): Eq. (eq_render) with the over
+ * operator of Eq. (eq_over).  out[y][x][3].
+ */
+void orc_render(const double* M, int D, int H, int W, double near_, double far_, const orc_camera* ref,
+                const orc_camera* view, double* out) {
+    double* rho = (double*)malloc(sizeof(double) * D);
+    orc_plane_inverse_depths(D, near_, far_, rho);
+    for (int y = 0; y < H; ++y)
+        for (int x = 0; x < W; ++x) {
+            double C[3] = {0, 0, 0};
+            /* sum_d c_d alpha_d prod_{j>d}(1-alpha_j), accumulated from the nearest plane */
+            double T = 1.0;
+            for (int d = D - 1; d >= 0; --d) {
+                double px, py;
+                int ok = orc_view_to_ref(ref, view, 1.0 / rho[d], x, y, &px, &py);
+                sample_t s;
+                sample_plane(M, d, H, W, ok, px, py, &s);
+                for (int c = 0; c < 3; ++c) C[c] += s.m[c] * s.m[3] * T;
+                T *= (1.0 - s.m[3]);
+            }
+            for (int c = 0; c < 3; ++c) out[((size_t)y * W + x) * 3 + c] = C[c];
+        }
+    free(rho);
+}
+
+/*
+ * Vector-Jacobian product of warp + composite for N views: given dL/dC_i (g_out[N][H][W][3]),
+ * accumulate dL/dM into grad[D][H][W][4] (which the caller zeroes).  For each view pixel:
+ *   dC/dc_d     = alpha_d T_d                         (Eq. eq_gradient)
+ *   dC/dalpha_d = T_d (c_d - B_d),   B_d = over-composite of the planes below d
+ * with T_d = prod_{j>d}(1 - alpha_j); then the bilinear transpose scatters the per-sample
+ * gradient onto the four taps.  No division by (1 - alpha).
+ */
+void orc_vjp(const double* M, int D, int H, int W, double near_, double far_, const orc_camera* ref,
+             const orc_camera* views, int N, const double* g_out, double* grad) {
+    double* rho = (double*)malloc(sizeof(double) * D);
+    sample_t* smp = (sample_t*)malloc(sizeof(sample_t) * D);
+    double* T = (double*)malloc(sizeof(double) * D);
+    orc_plane_inverse_depths(D, near_, far_, rho);
+    for (int i = 0; i < N; ++i)
+        for (int y = 0; y < H; ++y)
+            for (int x = 0; x < W; ++x) {
+                const double* r = g_out + (((size_t)i * H + y) * W + x) * 3;
+                double Tr = 1.0;
+                for (int d = D - 1; d >= 0; --d) {
+                    double px, py;
+                    int ok = orc_view_to_ref(ref, &views[i], 1.0 / rho[d], x, y, &px, &py);
+                    sample_plane(M, d, H, W, ok, px, py, &smp[d]);
+                    T[d] = Tr;
+                    Tr *= (1.0 - smp[d].m[3]);
+                }
+                double B[3] = {0, 0, 0};
+                for (int d = 0; d < D; ++d) {
+                    const double* m = smp[d].m;
+                    double g[4];
+                    for (int c = 0; c < 3; ++c) g[c] = T[d] * m[3] * r[c];
+                    g[3] = 0.0;
+                    for (int c = 0; c < 3; ++c) g[3] += T[d] * (m[c] - B[c]) * r[c];
+                    for (int c = 0; c < 3; ++c) B[c] = m[c] * m[3] + (1.0 - m[3]) * B[c];
+                    for (int k = 0; k < 4; ++k) {
+                        if (smp[d].w[k] == 0.0) continue;
+                        double* gp = grad + (((size_t)d * H + smp[d].ty[k]) * W + smp[d].tx[k]) * 4;
+                        for (int c = 0; c < 4; ++c) gp[c] += smp[d].w[k] * g[c];
+                    }
+                }
+            }
+    free(T);
+    free(smp);
+    free(rho);
+}
+
+/*
+ * Photometric loss of N views and, if grad != NULL, its gradient dL/dM (dense, overwritten).
+ * renders (optional) receives the N rendered views.  Returns L.
+ */
+double orc_loss_grad(const double* M, int D, int H, int W, double near_, double far_, const orc_camera* ref,
+                     const double* images, const orc_camera* views, int N, double* grad, double* renders) {
+    size_t npx = (size_t)H * W * 3;
+    double* Ct = (double*)malloc(sizeof(double) * npx * N);
+    for (int i = 0; i < N; ++i) orc_render(M, D, H, W, near_, far_, ref, &views[i], Ct + i * npx);
+    double L = 0.0;
+    double* r = (double*)malloc(sizeof(double) * npx * N);
+    for (size_t j = 0; j < npx * (size_t)N; ++j) {
+        double e = Ct[j] - images[j];
+        L += e * e;
+        r[j] = e / N;
+    }
+    L /= (2.0 * N);
+    if (grad) {
+        memset(grad, 0, sizeof(double) * (size_t)D * H * W * 4);
+        orc_vjp(M, D, H, W, near_, far_, ref, views, N, r, grad);
+    }
+    if (renders) memcpy(renders, Ct, sizeof(double) * npx * N);
+    free(r);
+    free(Ct);
+    return L;
+}
+
+/* ------------------------------------------------------------ sparsification */
+
+/* Reference-view alpha weights A_d = alpha_d prod_{j>d}(1 - alpha_j)  (Eq. eq_gradient, eq_overA). */
+void orc_alpha_weights(const double* M, int D, int H, int W, double* A) {
+    for (int y = 0; y < H; ++y)
+        for (int x = 0; x < W; ++x)
+            for (int d = 0; d < D; ++d) {
+                double a = M[(((size_t)d * H + y) * W + x) * 4 + 3];
+                double T = 1.0;
+                for (int j = d + 1; j < D; ++j) T *= (1.0 - M[(((size_t)j * H + y) * W + x) * 4 + 3]);
+                A[((size_t)d * H + y) * W + x] = a * T;
+            }
+}
+
+/*
+ * Top-k along depth: the k planes with the largest key, ties to the lower plane index;
+ * S[j][y][x] lists them in ascending plane order, mask[y][x] has bit d set for each.
+ * Written as the definition: sort the D (key, d) pairs by (key descending, d ascending)
+ * and keep the first k.
+ */
+void orc_select_topk(const double* A, int D, int H, int W, int k, uint8_t* S, uint64_t* mask) {
+    int* order = (int*)malloc(sizeof(int) * D);
+    for (int y = 0; y < H; ++y)
+        for (int x = 0; x < W; ++x) {
+            size_t p = (size_t)y * W + x;
+            for (int d = 0; d < D; ++d) order[d] = d;
+            /* insertion sort by (A desc, d asc) */
+            for (int a = 1; a < D; ++a) {
+                int cur = order[a];
+                double ka = A[(size_t)cur * H * W + p];
+                int b = a - 1;
+                while (b >= 0) {
+                    int o = order[b];
+                    double kb = A[(size_t)o * H * W + p];
+                    int before = (ka > kb) || (ka == kb && cur < o);
+                    if (!before) break;
+                    order[b + 1] = o;
+                    --b;
+                }
+                order[b + 1] = cur;
+            }
+            uint64_t mk = 0;
+            for (int j = 0; j < k; ++j) mk |= (uint64_t)1 << order[j];
+            mask[p] = mk;
+            int j = 0;
+            for (int d = 0; d < D; ++d)
+                if (mk >> d & 1) S[(size_t)j++ * H * W + p] = (uint8_t)d;
+        }
+    free(order);
+}
+
+/* ------------------------------------------------------------------ pyramid */
+
+/* 2x2 box average of P stacked [H][W][C] slices -> [H/2][W/2][C]. */
+void orc_downsample2(const double* x, int P, int H, int W, int C, double* y) {
+    int h = H / 2, w = W / 2;
+    for (int s = 0; s < P; ++s)
+        for (int yy = 0; yy < h; ++yy)
+            for (int xx = 0; xx < w; ++xx)
+                for (int c = 0; c < C; ++c) {
+                    const double* b = x + (size_t)s * H * W * C;
+                    double v = b[((size_t)(2 * yy) * W + 2 * xx) * C + c] + b[((size_t)(2 * yy) * W + 2 * xx + 1) * C + c] +
+                               b[((size_t)(2 * yy + 1) * W + 2 * xx) * C + c] + b[((size_t)(2 * yy + 1) * W + 2 * xx + 1) * C + c];
+                    y[((size_t)s * h * w + (size_t)yy * w + xx) * C + c] = 0.25 * v;
+                }
+}
+
+/* Down^l: l successive 2x2 box averages.  Returns a malloc'd buffer (caller frees). */
+static double* down_levels(const double* x, int P, int H, int W, int C, int level) {
+    size_t n = (size_t)P * H * W * C;
+    double* cur = (double*)malloc(sizeof(double) * n);
+    memcpy(cur, x, sizeof(double) * n);
+    for (int l = 0; l < level; ++l) {
+        double* nxt = (double*)malloc(sizeof(double) * (size_t)P * (H >> (l + 1)) * (W >> (l + 1)) * C);
+        orc_downsample2(cur, P, H >> l, W >> l, C, nxt);
+        free(cur);
+        cur = nxt;
+    }
+    return cur;
+}
+
+void orc_down_levels(const double* x, int P, int H, int W, int C, int level, double* y) {
+    double* r = down_levels(x, P, H, W, C, level);
+    memcpy(y, r, sizeof(double) * (size_t)P * (H >> level) * (W >> level) * C);
+    free(r);
+}
+
+/* ------------------------------------------------------------------- update */
+
+static double clamp01(double v) { return v < 0.0 ? 0.0 : (v > 1.0 ? 1.0 : v); }
+
+/*
+ * One HSGD iteration at pyramid level `level` (Sec. 3.3), updating the full-resolution
+ * MPI in place:
+ *   M_l = Down^l(M), I_l = Down^l(I), cameras at level l;
+ *   S   = top-k of A(M_l) (or S_pin when given);
+ *   g   = dL/dM_l (dense);
+ *   M[d][Y][X] <- clamp(M[d][Y][X] - lambda g[d][Y>>l][X>>l]) for d in S[.][Y>>l][X>>l].
+ * S_out (optional) receives the selection [k][H_l][W_l]; loss_out the loss at level l.
+ */
+int orc_hsgd_step(double* M, int D, int H, int W, double near_, double far_, const orc_camera* ref,
+                  const double* images, const orc_camera* views, int N, int k, double lambda, int clamp,
+                  int level, const uint8_t* S_pin, uint8_t* S_out, double* loss_out) {
+    if (k < 1 || k > D || D > 64 || (H % (1 << level)) || (W % (1 << level))) return 1;
+    int h = H >> level, w = W >> level;
+    double* Ml = down_levels(M, D, H, W, 4, level);
+    double* Il = down_levels(images, N, H, W, 3, level);
+    orc_camera refl;
+    orc_camera_at_level(ref, level, &refl);
+    orc_camera* vl = (orc_camera*)malloc(sizeof(orc_camera) * N);
+    for (int i = 0; i < N; ++i) orc_camera_at_level(&views[i], level, &vl[i]);
+
+    uint8_t* S = (uint8_t*)malloc((size_t)k * h * w);
+    if (S_pin) {
+        memcpy(S, S_pin, (size_t)k * h * w);
+    } else {
+        double* A = (double*)malloc(sizeof(double) * (size_t)D * h * w);
+        uint64_t* mk = (uint64_t*)malloc(sizeof(uint64_t) * (size_t)h * w);
+        orc_alpha_weights(Ml, D, h, w, A);
+        orc_select_topk(A, D, h, w, k, S, mk);
+        free(mk);
+        free(A);
+    }
+    double* g = (double*)malloc(sizeof(double) * (size_t)D * h * w * 4);
+    double L = orc_loss_grad(Ml, D, h, w, near_, far_, &refl, Il, vl, N, g, NULL);
+    for (int yy = 0; yy < h; ++yy)
+        for (int xx = 0; xx < w; ++xx)
+            for (int j = 0; j < k; ++j) {
+                int d = S[(size_t)j * h * w + (size_t)yy * w + xx];
+                const double* gd = g + (((size_t)d * h + yy) * w + xx) * 4;
+                for (int Y = yy << level; Y < (yy + 1) << level; ++Y)
+                    for (int X = xx << level; X < (xx + 1) << level; ++X)
+                        for (int c = 0; c < 4; ++c) {
+                            double* mv = M + (((size_t)d * H + Y) * W + X) * 4 + c;
+                            double nv = *mv - lambda * gd[c];
+                            *mv = clamp ? clamp01(nv) : nv;
+                        }
+            }
+    if (S_out) memcpy(S_out, S, (size_t)k * h * w);
+    if (loss_out) *loss_out = L;
+    free(g);
+    free(S);
+    free(vl);
+    free(Il);
+    free(Ml);
+    return 0;
+}
+
+/*
+ * Dense analytic gradient descent step (Sec. 3.1) at level `level`, no sparsification:
+ * every plane of every pixel takes the step.  The keep-everything case of HSGD must
+ * reduce to this.
+ */
+int orc_gd_step(double* M, int D, int H, int W, double near_, double far_, const orc_camera* ref,
+                const double* images, const orc_camera* views, int N, double lambda, int clamp, int level,
+                double* loss_out) {
+    if ((H % (1 << level)) || (W % (1 << level))) return 1;
+    int h = H >> level, w = W >> level;
+    double* Ml = down_levels(M, D, H, W, 4, level);
+    double* Il = down_levels(images, N, H, W, 3, level);
+    orc_camera refl;
+    orc_camera_at_level(ref, level, &refl);
+    orc_camera* vl = (orc_camera*)malloc(sizeof(orc_camera) * N);
+    for (int i = 0; i < N; ++i) orc_camera_at_level(&views[i], level, &vl[i]);
+    double* g = (double*)malloc(sizeof(double) * (size_t)D * h * w * 4);
+    double L = orc_loss_grad(Ml, D, h, w, near_, far_, &refl, Il, vl, N, g, NULL);
+    for (int d = 0; d < D; ++d)
+        for (int Y = 0; Y < H; ++Y)
+            for (int X = 0; X < W; ++X)
+                for (int c = 0; c < 4; ++c) {
+                    double* mv = M + (((size_t)d * H + Y) * W + X) * 4 + c;
+                    double nv = *mv - lambda * g[(((size_t)d * h + (Y >> level)) * w + (X >> level)) * 4 + c];
+                    *mv = clamp ? clamp01(nv) : nv;
+                }
+    if (loss_out) *loss_out = L;
+    free(g);
+    free(vl);
+    free(Il);
+    free(Ml);
+    return 0;
+}

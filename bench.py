@@ -1,0 +1,435 @@
+#!/usr/bin/env python3
+"""Benchmark of the RealLiFe hot path on GB300: MPI refinements/s at 512x384, D=32.
+
+One step = one HSGD refinement (3 iterations at pyramid levels 2, 1, 0; N=4 source
+views, k=5 kept planes) of a seeded synthetic scene plus 9 novel views rendered from the
+refined MPI, all through the C ABI.  Inputs are resident in HBM before the timed region;
+before every timed step the MPI is reset from a pristine copy and L2 is flushed by
+writing a 512 MB buffer (both outside the step's CUDA events).
+
+Prints one JSON line.  ``--impl reference`` times the FP64 CPU oracle instead (a bounded
+sample per step, on the host cores).  Under torchrun every rank refines its own scene
+(independent problems, no collective on the data path) and rank 0 reports the aggregate.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import glob
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "MPI refinements/s and HBM GB/s at 512x384 D=32; p50/p99 serve latency"
+UNIT = "refinements/s"
+L2_FLUSH_BYTES = 512 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="paper", choices=["paper", "paper_bf16", "display", "small"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-clocks", action="store_true")
+    ap.add_argument("--seed", type=int, default=0)
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def reduce_max(x: float, dist, device) -> float:
+    """Max of a per-rank scalar over all ranks (identity without a process group)."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def csrc_digest() -> str:
+    h = hashlib.sha256()
+    for p in sorted(glob.glob(os.path.join(ROOT, "paper_2307_03017_gb300", "csrc", "*"))):
+        with open(p, "rb") as f:
+            h.update(os.path.basename(p).encode())
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.t = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.t = threading.Thread(target=self._read, daemon=True)
+        self.t.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict | None:
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.t.join(timeout=5)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# --------------------------------------------------------------------- workload
+
+def load_scene(name: str, seed: int):
+    import scenegen as sg
+    sc, cfg = sg.workload(name, seed)
+    return sc, cfg
+
+
+def k3_algorithmic_bytes(cfg, sc, level: int, elt: int) -> int:
+    """Minimal DRAM bytes of one fused warp/composite/adjoint launch at `level`:
+    read the level MPI once, the full-resolution source images once, the selection mask
+    once, write the compact gradient once."""
+    h, w = sc.H >> level, sc.W >> level
+    return (sc.D * h * w * 4 * elt + cfg["N"] * sc.H * sc.W * 3 * 4 + h * w * 8 + cfg["k"] * h * w * 16)
+
+
+def step_algorithmic_bytes(cfg, sc, elt: int) -> int:
+    """Minimal DRAM bytes of one step: per level-l iteration read M (select / pyramid),
+    write M_l (l > 0), K3 traffic, read-modify-write the kept k/D of M; 9 renders read M
+    once each and write their RGB output."""
+    Mb = sc.D * sc.H * sc.W * 4 * elt
+    tot = 0
+    for l in cfg["schedule"]:
+        tot += Mb + (Mb >> (2 * l) if l else 0) + k3_algorithmic_bytes(cfg, sc, l, elt) + 2 * cfg["k"] * Mb // sc.D
+    tot += len(sc.novel) * (Mb + sc.H * sc.W * 12)
+    return tot
+
+
+def run_ours(args, world, rank, local):
+    import torch
+    import paper_2307_03017_gb300 as rl
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    sc, cfg = load_scene(args.workload, args.seed + rank)
+    dtype = torch.bfloat16 if cfg["dtype"] == "bf16" else torch.float32
+    elt = 2 if dtype == torch.bfloat16 else 4
+    k, sched = cfg["k"], tuple(cfg["schedule"])
+    N = len(sc.src)
+    M0 = torch.from_numpy(sc.coarse_mpi).to(dev).to(dtype).contiguous()
+    M = M0.clone()
+    images = torch.from_numpy(sc.images).to(dev)
+    mpi = rl.make_mpi(M, sc.near, sc.far, sc.ref)
+    ws = rl.workspace(N, sc.D, sc.H, sc.W, k, dtype, dev)
+    out = torch.empty((len(sc.novel), sc.H, sc.W, 3), dtype=torch.float32, device=dev)
+    loss = torch.empty(len(sched), dtype=torch.float32, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        rl.reallife_refine(mpi, images, sc.src, k, sched, loss_per_iter=loss, ws=ws)
+        rl.reallife_render(mpi, sc.novel, out=out)
+
+    for _ in range(args.warmup):
+        M.copy_(M0)
+        step()
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(local) if not args.no_clocks else None
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    stops = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    if clocks:
+        clocks.start()
+    rl.reallife_trace_enable(True)
+    rl.reallife_trace_read()  # reset counters
+    for i in range(args.steps):
+        rl.reallife_trace_enable(False)  # reset + flush are not part of the step
+        M.copy_(M0)
+        flush.fill_(i & 0xFF)
+        rl.reallife_trace_enable(True)
+        starts[i].record(stream)
+        step()
+        stops[i].record(stream)
+    torch.cuda.synchronize()
+    rl.reallife_trace_enable(False)
+    trace = rl.reallife_trace_read()
+    clk = clocks.stop() if clocks else None
+    ms_steps = [a.elapsed_time(b) for a, b in zip(starts, stops)]
+    total_ms = reduce_max(sum(ms_steps), dist, dev)
+    if dist:
+        dist.barrier()
+    value = world * args.steps / (total_ms / 1e3)
+
+    # dominant kernel: roofline from its live CUDA-event durations inside the timed region
+    launches = sum(v[0] for v in trace.values())
+    dom = max(trace.items(), key=lambda kv: kv[1][1])
+    dom_name, (dom_n, dom_ms) = dom
+    peaks = {}
+    pk = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(pk):
+        peaks = json.load(open(pk))
+    peak_gbs, peak_src = (peaks["hbm_gbs"], "measured") if "hbm_gbs" in peaks else (6800.0, "fallback")
+    if dom_name.startswith("grad"):
+        per_step = sum(k3_algorithmic_bytes(cfg, sc, l, elt) for l in sched)
+        alg_bytes = per_step * args.steps
+    elif dom_name.startswith("render"):
+        Mb = sc.D * sc.H * sc.W * 4 * elt
+        alg_bytes = args.steps * len(sc.novel) * (Mb + sc.H * sc.W * 12)
+    else:
+        alg_bytes = None
+    achieved = alg_bytes / (dom_ms / 1e3) / 1e9 if alg_bytes else None
+    traffic = None
+    tf = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(tf):
+        try:
+            tr = json.load(open(tf)).get(f"{args.workload}:{dom_name}")
+            if tr and tr.get("csrc_digest") == csrc_digest():
+                traffic = tr["dram_bytes_per_launch"]
+        except Exception:
+            traffic = None
+    roofline = {"bound": "hbm", "kernel": dom_name, "achieved": round(achieved, 1) if achieved else None,
+                "peak": peak_gbs, "unit": "GB/s", "frac": round(achieved / peak_gbs, 4) if achieved else None,
+                "traffic": traffic, "alg_bytes_per_launch": int(alg_bytes / dom_n) if alg_bytes else None,
+                "avg_launch_us": round(dom_ms / dom_n * 1e3, 2), "peak_source": peak_src}
+    step_bytes = step_algorithmic_bytes(cfg, sc, elt)
+    kernels = {n: {"launches": c, "ms_per_step": round(t / args.steps, 4)} for n, (c, t) in sorted(trace.items())}
+
+    e2e = None
+    if not args.no_e2e:
+        e2e = run_e2e(args, rl, sc, cfg, dtype, dev, world, dist)
+
+    result = None
+    if rank == 0:
+        result = {
+            "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(total_ms / args.steps, 4), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32" if elt == 4 else "bf16",
+            "data": "synthetic (seeded ray-cast layered scenes; no dataset)",
+            "config": {"workload": f"{args.workload}: {sc.W}x{sc.H} D={sc.D} N={N} k={k} levels={list(sched)} "
+                                   f"+ {len(sc.novel)} novel views", "storage": cfg["dtype"],
+                       "l2": "flushed (512 MB write) before every timed step", "parallelism": f"replicas{world}"},
+            "hbm_gbs_step": round(step_bytes / (total_ms / args.steps / 1e3) / 1e9, 1),
+            "roofline": roofline, "kernels": kernels, "gpu_launches": int(launches),
+            "clocks": clk, "e2e": e2e,
+        }
+    if dist:
+        dist.destroy_process_group()
+    return result
+
+
+def run_e2e(args, rl, sc, cfg, dtype, dev, world, dist):
+    """Same metric through the public API from pinned host memory: H2D of the coarse MPI and
+    the source images, refine + render, D2H of the rendered views, every step."""
+    import torch
+    k, sched = cfg["k"], tuple(cfg["schedule"])
+    N = len(sc.src)
+    h_M = torch.from_numpy(sc.coarse_mpi).to(dtype).pin_memory()
+    h_I = torch.from_numpy(sc.images).pin_memory()
+    h_out = torch.empty((len(sc.novel), sc.H, sc.W, 3), dtype=torch.float32).pin_memory()
+    M = torch.empty_like(h_M, device=dev)
+    images = torch.empty_like(h_I, device=dev)
+    out = torch.empty_like(h_out, device=dev)
+    ws = rl.workspace(N, sc.D, sc.H, sc.W, k, dtype, dev)
+    mpi = rl.make_mpi(M, sc.near, sc.far, sc.ref)
+
+    def step():
+        M.copy_(h_M, non_blocking=True)
+        images.copy_(h_I, non_blocking=True)
+        rl.reallife_refine(mpi, images, sc.src, k, sched, ws=ws)
+        rl.reallife_render(mpi, sc.novel, out=out)
+        h_out.copy_(out, non_blocking=True)
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(args.steps):
+        step()
+    b.record()
+    torch.cuda.synchronize()
+    ms = reduce_max(a.elapsed_time(b), dist, dev)
+    return {"value": round(world * args.steps / (ms / 1e3), 3), "unit": UNIT,
+            "h2d_bytes_per_step": int(h_M.numel() * h_M.element_size() + h_I.numel() * 4),
+            "d2h_bytes_per_step": int(h_out.numel() * 4)}
+
+
+# ------------------------------------------------------------------- CPU oracle
+
+def crop_scene(sc, rows: int):
+    """Rows [y0, y0 + rows) of the scene (MPI, images, cameras with the principal point
+    shifted): the same problem on a horizontal band, for bounded CPU samples."""
+    import copy
+    import scenegen as sg
+    y0 = ((sc.H - rows) // 2) & ~7
+    out = copy.copy(sc)
+    out.H = rows
+    out.coarse_mpi = np.ascontiguousarray(sc.coarse_mpi[:, y0:y0 + rows])
+    out.images = np.ascontiguousarray(sc.images[:, y0:y0 + rows])
+
+    def shift(c):
+        K = c.K.copy()
+        K[1, 2] -= y0
+        return sg.Camera(K, c.R, c.t)
+    out.ref = shift(sc.ref)
+    out.src = [shift(c) for c in sc.src]
+    out.novel = [shift(c) for c in sc.novel]
+    return out
+
+
+def oracle_step(sc, cfg):
+    import oracle
+    M, _, _ = oracle.refine(sc.coarse_mpi, sc.near, sc.far, sc.ref, sc.src, sc.images, cfg["k"],
+                            tuple(cfg["schedule"]))
+    for cam in sc.novel:
+        oracle.render(M, sc.near, sc.far, sc.ref, cam)
+
+
+def sample_rows(sc, frac: float) -> int:
+    """Band height for a CPU sample: about frac of the rows, a multiple of 8 (pyramid levels)."""
+    return max(8, int(sc.H * frac) // 8 * 8)
+
+
+def cpu_baseline(sc, cfg, frac: float = 0.5) -> dict:
+    """The FP64 oracle as it stands, single-threaded, on one step of a band of the same
+    workload (about half of its rows), scaled to refinements/s by the band's share of pixels."""
+    import oracle
+    oracle.build()
+    rows = sample_rows(sc, frac)
+    band = crop_scene(sc, rows)
+    t0 = time.perf_counter()
+    oracle_step(band, cfg)
+    dt = time.perf_counter() - t0
+    share = rows / sc.H
+    return {"value": round(share / dt, 5), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"one step ({len(cfg['schedule'])}-level refine + {len(sc.novel)} renders) on a {sc.W}x{rows} "
+                      f"band ({share:.3f} of the pixels) of the same scene, FP64, single thread, {dt:.2f} s; "
+                      f"value scaled by the pixel share",
+            "cpu": platform_cpu()}
+
+
+def platform_cpu() -> str:
+    try:
+        import platform
+        m = platform.processor() or platform.machine()
+        if os.path.exists("/proc/cpuinfo"):
+            for ln in open("/proc/cpuinfo"):
+                if ln.lower().startswith(("model name", "cpu part")):
+                    return f"{platform.machine()} {ln.split(':', 1)[1].strip()}"
+        return m
+    except Exception:
+        return "unknown"
+
+
+def run_reference(args, world, rank):
+    """The oracle on the host cores, each step a 1/8-height band of the workload (scaled)."""
+    if rank != 0:
+        return None
+    import oracle
+    oracle.build()
+    sc, cfg = load_scene(args.workload, args.seed)
+    rows = sample_rows(sc, 0.125)
+    band = crop_scene(sc, rows)
+    share = rows / sc.H
+    for _ in range(args.warmup):
+        oracle_step(band, cfg)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle_step(band, cfg)
+    dt = time.perf_counter() - t0
+    v = share * args.steps / dt
+    return {"impl": "reference", "metric": METRIC, "value": round(v, 5), "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt / args.steps * 1e3, 2),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded ray-cast layered scenes; no dataset)",
+            "config": {"workload": f"{args.workload}: {sc.W}x{sc.H} D={sc.D} N={len(sc.src)} k={cfg['k']} "
+                                   f"levels={list(cfg['schedule'])} + {len(sc.novel)} novel views"},
+            "cpu_baseline": {"value": round(v, 5), "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"each step = one step on a {sc.W}x{rows} band ({share:.3f} of the pixels) "
+                                       f"of the workload, FP64 oracle, single thread; value scaled by the share",
+                             "cpu": platform_cpu()},
+            "e2e": {"value": round(v, 5), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    args = parse()
+    world, rank, local = dist_env()
+    if args.impl == "reference":
+        res = run_reference(args, world, rank)
+    else:
+        res = run_ours(args, world, rank, local)
+        if res is not None and not args.no_cpu_baseline and world == 1:
+            sc, cfg = load_scene(args.workload, args.seed)
+            res["cpu_baseline"] = cpu_baseline(sc, cfg)
+        elif res is not None:
+            res["cpu_baseline"] = None
+    if res is not None:
+        print(json.dumps(res), flush=True)
+
+
+if __name__ == "__main__":
+    main()

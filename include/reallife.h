@@ -1,0 +1,199 @@
+/*
+ * reallife.h -- C ABI of the GB300 (sm_103a) RealLiFe hot path: Hierarchical Sparse
+ * Gradient Descent (HSGD) refinement of a multi-plane image (MPI) and MPI rendering.
+ *
+ * Paper: "RealLiFe: Real-Time Light Field Reconstruction via Hierarchical Sparse
+ * Gradient Descent" (arXiv 2307.03017).  Problem statement (Sec. 3, 3.2): sparse posed
+ * source images in, an MPI in the reference frustum out, novel views rendered from it.
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ *  - MPI layout: [D][H][W][4] (R, G, B, alpha) row-major, plane d = 0 farthest and
+ *    d = D-1 nearest, so the over operator of Eq. (eq_over) puts the unoccluded plane at
+ *    the top index.  Storage is FP32 (RL_F32) or BF16 (RL_BF16, round-to-nearest-even
+ *    on every store); all arithmetic is FP32.
+ *  - Plane depths are uniform in inverse depth: rho_d = 1/far + d/(D-1) (1/near - 1/far)
+ *    (rho_0 = 1/far when D = 1).
+ *  - Cameras are world->camera, x_cam = R X + t, pixel = K x_cam / z with pixel centres
+ *    on integer coordinates; K must have zero skew and last row (0, 0, 1).  Source and
+ *    target images have the MPI's resolution H x W.
+ *  - Images: [N][H][W][3] FP32.  Selections S: [k][H_l][W_l] uint8 plane indices in
+ *    ascending order; masks: [H_l][W_l] uint64 with bit d set for each kept plane.
+ *  - Pyramid level l works at H_l = H / 2^l, W_l = W / 2^l: images and MPI are 2x2 box
+ *    averaged l times, intrinsics become f / 2^l and (c + 0.5) / 2^l - 0.5.
+ *
+ * Ownership and execution
+ * -----------------------
+ *  - The caller owns every buffer (MPI, images, outputs, workspace); the library
+ *    allocates no device memory.  Pointers named "device" must be device memory of the
+ *    current CUDA device; camera/parameter structs are host memory read before return.
+ *  - Every call is asynchronous on `stream` (0 = legacy default stream) and enqueues
+ *    kernels only, so it can be captured into a CUDA graph.  Results are valid once the
+ *    stream reaches them.  Calls that share a workspace must be ordered on one stream.
+ *  - Validation happens on the host before anything is launched: a call that returns
+ *    RL_EINVAL launched nothing.  A launch failure returns RL_ECUDA (details from
+ *    reallife_last_error()).  No C++ exception crosses this boundary.
+ *  - Gradients are accumulated with FP32 atomics, so results agree run to run within
+ *    FP32 rounding of the summation order, not bit for bit.
+ */
+#ifndef REALLIFE_H
+#define REALLIFE_H
+
+#include <stddef.h>
+#include <stdint.h>
+#include <cuda_runtime_api.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    RL_OK = 0,
+    RL_EINVAL = 1,    /* invalid argument; nothing was launched */
+    RL_ENOMEM = 2,    /* workspace too small */
+    RL_ECUDA = 3,     /* a CUDA call or launch failed */
+    RL_ETIMEOUT = 4,  /* a bounded device-side wait gave up */
+    RL_ENOTIMPL = 5
+} rl_status;
+
+typedef enum { RL_F32 = 0, RL_BF16 = 1 } rl_dtype;
+
+/* Pinhole camera, world->camera, row-major. */
+typedef struct {
+    double K[9];
+    double R[9];
+    double t[3];
+} rl_camera;
+
+/* A multi-plane image in the frustum of camera `ref` (Sec. 3.1).  `data` is device
+ * memory [D][H][W][4] of `dtype`, owned by the caller. */
+typedef struct {
+    int D, H, W;
+    double near_, far_;
+    rl_dtype dtype;
+    void* data;
+    rl_camera ref;
+} rl_mpi;
+
+/* One HSGD iteration: keep k planes per pixel (Sec. 3.3 "Gradient Sparsification"),
+ * step `lambda` (the analytic update of Sec. 3.1 read as descent), clamp the updated
+ * values to [0,1] when clamp01 != 0, work at pyramid level `level`. */
+typedef struct {
+    int k;
+    float lambda;
+    int clamp01;
+    int level;
+} rl_hsgd_params;
+
+/* Upper bounds checked on the host. */
+#define RL_MAX_PLANES 64
+#define RL_MAX_VIEWS 16
+
+/* ------------------------------------------------------------------ top level */
+
+/* Bytes of workspace that reallife_hsgd_step / reallife_refine need for an MPI of
+ * D x H x W with N source views and k kept planes (any level of the schedule). */
+size_t reallife_workspace_bytes(int N, int D, int H, int W, int k, rl_dtype dtype);
+
+/* Novel views (Eq. eq_render with the over operator of Eq. eq_over): warp every plane
+ * into each target camera by its plane-induced homography (Eq. eq_homo), bilinear
+ * sampling with zero padding, composite front to back with no background.
+ *   tgt:  host array of T cameras.
+ *   out:  device [T][H][W][3] FP32.
+ * No workspace.  RL_EINVAL for T < 1, null pointers or invalid MPI/cameras. */
+rl_status reallife_render(const rl_mpi* m, const rl_camera* tgt, int T, float* out, cudaStream_t stream);
+
+/* One HSGD iteration on `m` in place (Sec. 3.3 with the analytic gradient of Sec. 3.1):
+ *   M_l = Down^l(M); S = top-k of the reference-view alpha weight A_d of M_l
+ *   (Eq. eq_gradient, ties to the lower plane); G = dL/dM_l on the kept voxels, where
+ *   L = 1/(2N) sum_i sum_q |O(w_i(M_l))(q) - I_i^l(q)|^2 (warp, composite, loss and the
+ *   exact adjoint, transmittance recomputed); M[S] <- clamp(M[S] - lambda U_l(G)) with
+ *   U_l nearest-neighbour replication (the restore operator R(., S)).
+ *   images:   device [N][H][W][3] FP32 at full resolution (the call averages to level l).
+ *   src:      host array of N source cameras.
+ *   loss_out: device float[1] (loss at level l) or NULL.
+ *   S_out:    device uint8 [k][H_l][W_l] receiving the selection, or NULL.
+ *   ws:       device workspace of at least reallife_workspace_bytes(...) bytes.
+ * RL_ENOMEM if ws_bytes is too small; RL_EINVAL for 1 <= k <= D <= 64, 1 <= N <= 16,
+ * H and W divisible by 2^level violated, or null pointers. */
+rl_status reallife_hsgd_step(rl_mpi* m, const float* images, const rl_camera* src, int N, const rl_hsgd_params* p,
+                             float* loss_out, uint8_t* S_out, void* ws, size_t ws_bytes, cudaStream_t stream);
+
+/* HSGD refinement: reallife_hsgd_step at levels schedule[0..iters-1] (coarse to fine,
+ * e.g. {2,1,0}; Fig. 3 and Sec. 5.2), p->level ignored.
+ *   loss_per_iter: device float[iters] or NULL.
+ * Errors as reallife_hsgd_step, checked for every level before the first launch. */
+rl_status reallife_refine(rl_mpi* m, const float* images, const rl_camera* src, int N, const rl_hsgd_params* p,
+                          const int* schedule, int iters, float* loss_per_iter, void* ws, size_t ws_bytes,
+                          cudaStream_t stream);
+
+/* -------------------------------------------------------- steps of the iteration */
+
+/* Down^l of P stacked [H][W][C] FP32 slices (2x2 box average applied l times, computed
+ * as one 2^l x 2^l average): x device [P][H][W][C] -> y device [P][H/2^l][W/2^l][C].
+ * Sec. 3.2 "Hierarchical PSV construction". */
+rl_status reallife_downsample_f32(const float* x, int P, int H, int W, int C, int level, float* y,
+                                  cudaStream_t stream);
+
+/* Selection on an MPI `m` (at whatever resolution it has): A_d = alpha_d prod_{j>d}
+ * (1 - alpha_j) in FP32 at the reference view (Eq. eq_gradient), keep the k largest per
+ * pixel, ties to the lower d (Sec. 3.3).  S device [k][H][W] uint8 (ascending), mask
+ * device [H][W] uint64; either may be NULL. */
+rl_status reallife_select(const rl_mpi* m, int k, uint8_t* S, uint64_t* mask, cudaStream_t stream);
+
+/* Same selection from caller-supplied FP32 keys `keys` device [D][H][W]. */
+rl_status reallife_select_keys(const float* keys, int D, int H, int W, int k, uint8_t* S, uint64_t* mask,
+                               cudaStream_t stream);
+
+/* Photometric loss of N views of `m` against `images` (both at m's resolution) and its
+ * gradient (warp + composite + loss + exact adjoint, Sec. 3.1/3.3):
+ *   mask == NULL: dense G device [D][H][W][4] FP32;
+ *   mask != NULL: compact G device [k][H][W][4] FP32, slot j of pixel p holding the
+ *                 j-th kept plane of p in ascending order (mask device [H][W] uint64).
+ *   loss_out: device float[1] or NULL.  G is overwritten.
+ *   ws: device workspace, at least reallife_workspace_bytes(N, D, H, W, k or D, dtype). */
+rl_status reallife_loss_grad(const rl_mpi* m, const float* images, const rl_camera* src, int N,
+                             const uint64_t* mask, int k, float* G, float* loss_out, void* ws, size_t ws_bytes,
+                             cudaStream_t stream);
+
+/* Masked update (restore operator R(., S) of Sec. 3.3 followed by nearest-neighbour
+ * upsampling to full resolution): for every full-resolution pixel (y, x) and j < k,
+ *   d = S[j][y>>level][x>>level];
+ *   M[d][y][x] <- clamp01 ? clamp(M - lambda G[j][y>>level][x>>level], 0, 1) : M - lambda G.
+ * S device [k][H_l][W_l] uint8, G device [k][H_l][W_l][4] FP32. */
+rl_status reallife_sparse_update(rl_mpi* m, const uint8_t* S, const float* G, int k, int level, float lambda,
+                                 int clamp01, cudaStream_t stream);
+
+/* Backward of warp + composite (the differentiable forward is reallife_render with the
+ * source cameras): given dL/dC device [N][H][W][3], write dL/dM device [D][H][W][4]
+ * FP32 (dense, overwritten).  Transmittance is recomputed, not stored. */
+rl_status reallife_render_backward(const rl_mpi* m, const rl_camera* views, int N, const float* grad_out,
+                                   float* grad_mpi, cudaStream_t stream);
+
+/* Diagnostic: warp offsets of view `view`: out device [D][H][W][2] FP32 holding
+ * p - q, where p is the reference pixel sampled for plane d at the view's pixel q
+ * (Eq. eq_homo inverted); NaN where the plane is not met in front of the view. */
+rl_status reallife_warp_offsets(const rl_mpi* m, const rl_camera* view, float* out, cudaStream_t stream);
+
+/* ------------------------------------------------------------------ utilities */
+
+/* Host-side kernel tracing: when enabled, every kernel launch of this library is
+ * bracketed by CUDA events on its stream and counted per kernel name. */
+rl_status reallife_trace_enable(int on);
+/* Synchronises the recorded events and reports, for up to `max` kernel names: name,
+ * launch count and summed device milliseconds.  Resets the counters. */
+typedef struct {
+    char name[48];
+    long long launches;
+    double total_ms;
+} rl_trace_entry;
+rl_status reallife_trace_read(rl_trace_entry* out, int max, int* n_out);
+
+const char* reallife_strerror(rl_status s);
+/* Message of the most recent failure on the calling thread ("" if none). */
+const char* reallife_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* REALLIFE_H */

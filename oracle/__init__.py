@@ -58,6 +58,8 @@ def _load():
             lib.orc_view_to_ref.argtypes = [cam, cam, d, d, d, dp, dp]
             lib.orc_view_to_ref.restype = i
             lib.orc_render.argtypes = [dp, i, i, i, d, d, cam, cam, dp]
+            ip = P(ctypes.c_int)
+            lib.orc_render_pixels.argtypes = [dp, i, i, i, d, d, cam, cam, i, ip, ip, dp]
             lib.orc_vjp.argtypes = [dp, i, i, i, d, d, cam, cam, i, dp, dp]
             lib.orc_loss_grad.argtypes = [dp, i, i, i, d, d, cam, dp, cam, i, dp, dp]
             lib.orc_loss_grad.restype = d
@@ -124,6 +126,18 @@ def render(M, near: float, far: float, ref, view) -> np.ndarray:
     D, H, W, _ = M.shape
     out = np.empty((H, W, 3))
     _load().orc_render(_ptr(M), D, H, W, near, far, ctypes.byref(_cam(ref)), ctypes.byref(_cam(view)), _ptr(out))
+    return out
+
+
+def render_pixels(M, near: float, far: float, ref, view, xs, ys) -> np.ndarray:
+    """Eq. (eq_render) at the listed view pixels only -> ``[n][3]``."""
+    M = _f64(M)
+    D, H, W, _ = M.shape
+    xs = np.ascontiguousarray(xs, dtype=np.int32)
+    ys = np.ascontiguousarray(ys, dtype=np.int32)
+    out = np.empty((len(xs), 3))
+    _load().orc_render_pixels(_ptr(M), D, H, W, near, far, ctypes.byref(_cam(ref)), ctypes.byref(_cam(view)),
+                              len(xs), _ptr(xs, ctypes.c_int), _ptr(ys, ctypes.c_int), _ptr(out))
     return out
 
 

@@ -144,29 +144,38 @@ static void sample_plane(const double* M, int d, int H, int W, int valid, double
     }
 }
 
-/*
- * Render one view of size H x W (same size as the MPI): Eq. (eq_render) with the over
- * operator of Eq. (eq_over).  out[y][x][3].
- */
+/* Composite of one view pixel (u, v): Eq. (eq_render) with the over operator of Eq. (eq_over). */
+static void render_pixel(const double* M, int D, int H, int W, const double* rho, const orc_camera* ref,
+                         const orc_camera* view, double u, double v, double C[3]) {
+    C[0] = C[1] = C[2] = 0.0;
+    /* sum_d c_d alpha_d prod_{j>d}(1-alpha_j), accumulated from the nearest plane */
+    double T = 1.0;
+    for (int d = D - 1; d >= 0; --d) {
+        double px, py;
+        int ok = orc_view_to_ref(ref, view, 1.0 / rho[d], u, v, &px, &py);
+        sample_t s;
+        sample_plane(M, d, H, W, ok, px, py, &s);
+        for (int c = 0; c < 3; ++c) C[c] += s.m[c] * s.m[3] * T;
+        T *= (1.0 - s.m[3]);
+    }
+}
+
+/* Render one view of size H x W (same size as the MPI): out[y][x][3]. */
 void orc_render(const double* M, int D, int H, int W, double near_, double far_, const orc_camera* ref,
                 const orc_camera* view, double* out) {
     double* rho = (double*)malloc(sizeof(double) * D);
     orc_plane_inverse_depths(D, near_, far_, rho);
     for (int y = 0; y < H; ++y)
-        for (int x = 0; x < W; ++x) {
-            double C[3] = {0, 0, 0};
-            /* sum_d c_d alpha_d prod_{j>d}(1-alpha_j), accumulated from the nearest plane */
-            double T = 1.0;
-            for (int d = D - 1; d >= 0; --d) {
-                double px, py;
-                int ok = orc_view_to_ref(ref, view, 1.0 / rho[d], x, y, &px, &py);
-                sample_t s;
-                sample_plane(M, d, H, W, ok, px, py, &s);
-                for (int c = 0; c < 3; ++c) C[c] += s.m[c] * s.m[3] * T;
-                T *= (1.0 - s.m[3]);
-            }
-            for (int c = 0; c < 3; ++c) out[((size_t)y * W + x) * 3 + c] = C[c];
-        }
+        for (int x = 0; x < W; ++x) render_pixel(M, D, H, W, rho, ref, view, x, y, out + ((size_t)y * W + x) * 3);
+    free(rho);
+}
+
+/* Render only the n view pixels (xs[j], ys[j]): out[n][3]. */
+void orc_render_pixels(const double* M, int D, int H, int W, double near_, double far_, const orc_camera* ref,
+                       const orc_camera* view, int n, const int* xs, const int* ys, double* out) {
+    double* rho = (double*)malloc(sizeof(double) * D);
+    orc_plane_inverse_depths(D, near_, far_, rho);
+    for (int j = 0; j < n; ++j) render_pixel(M, D, H, W, rho, ref, view, xs[j], ys[j], out + (size_t)j * 3);
     free(rho);
 }
 

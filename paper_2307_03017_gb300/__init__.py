@@ -1,0 +1,263 @@
+"""Python binding of libreallife: the GB300 (sm_103a) RealLiFe hot path.
+
+Argument marshalling only.  Every step (warp, composite, loss, adjoint, selection,
+update, rendering) runs in the CUDA kernels behind the C ABI of ``include/reallife.h``;
+the functions here carry the same names as the C entry points, take CUDA tensors
+(PyTorch supplies device memory and streams) and host cameras, and raise
+``RealLifeError`` when the library reports a failure.  There is no CPU fallback:
+importing works without a GPU, but every call needs the built library and a CUDA
+device.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+import torch
+
+from . import _lib
+
+__all__ = [
+    "RealLifeError", "Mpi", "make_mpi", "plane_inverse_depths",
+    "reallife_workspace_bytes", "reallife_render", "reallife_hsgd_step", "reallife_refine",
+    "reallife_downsample_f32", "reallife_select", "reallife_select_keys", "reallife_loss_grad",
+    "reallife_sparse_update", "reallife_render_backward", "reallife_warp_offsets",
+    "reallife_trace_enable", "reallife_trace_read", "reallife_strerror", "workspace", "library_path",
+]
+
+RealLifeError = _lib.RealLifeError
+F32, BF16 = 0, 1
+_DT = {torch.float32: F32, torch.bfloat16: BF16}
+
+
+def library_path() -> str:
+    return _lib.path()
+
+
+def plane_inverse_depths(D: int, near: float, far: float) -> np.ndarray:
+    """Inverse depths of the planes (d = 0 farthest), uniform between 1/far and 1/near."""
+    if D == 1:
+        return np.array([1.0 / far])
+    return 1.0 / far + np.arange(D) / (D - 1) * (1.0 / near - 1.0 / far)
+
+
+class Mpi:
+    """A device MPI ``[D][H][W][4]`` (float32 or bfloat16) in the frustum of ``ref``."""
+
+    def __init__(self, data: torch.Tensor, near: float, far: float, ref):
+        if data.dim() != 4 or data.shape[-1] != 4:
+            raise ValueError("MPI tensor must be [D][H][W][4]")
+        if data.dtype not in _DT:
+            raise ValueError("MPI dtype must be float32 or bfloat16")
+        if not data.is_cuda or not data.is_contiguous():
+            raise ValueError("MPI tensor must be a contiguous CUDA tensor")
+        self.data = data
+        self.near = float(near)
+        self.far = float(far)
+        self.ref = ref
+
+    @property
+    def D(self):
+        return self.data.shape[0]
+
+    @property
+    def H(self):
+        return self.data.shape[1]
+
+    @property
+    def W(self):
+        return self.data.shape[2]
+
+    def c_struct(self) -> _lib.RlMpi:
+        s = _lib.RlMpi()
+        s.D, s.H, s.W = self.D, self.H, self.W
+        s.near_, s.far_ = self.near, self.far
+        s.dtype = _DT[self.data.dtype]
+        s.data = ctypes.c_void_p(self.data.data_ptr())
+        s.ref = _lib.camera(self.ref)
+        return s
+
+
+def make_mpi(data: torch.Tensor, near: float, far: float, ref) -> Mpi:
+    return Mpi(data, near, far, ref)
+
+
+def _stream(stream) -> ctypes.c_void_p:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+
+
+def _ptr(t: torch.Tensor | None) -> ctypes.c_void_p | None:
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _check_f32(t: torch.Tensor, shape, name):
+    if t.dtype != torch.float32 or tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} must be float32 {tuple(shape)}, got {t.dtype} {tuple(t.shape)}")
+
+
+def _params(k, lam, clamp, level) -> _lib.RlHsgdParams:
+    p = _lib.RlHsgdParams()
+    p.k, p.lambda_, p.clamp01, p.level = int(k), float(lam), int(bool(clamp)), int(level)
+    return p
+
+
+# ------------------------------------------------------------------ entry points
+
+def reallife_workspace_bytes(N: int, D: int, H: int, W: int, k: int, dtype=torch.float32) -> int:
+    return int(_lib.lib().reallife_workspace_bytes(N, D, H, W, k, _DT[dtype]))
+
+
+def workspace(N: int, D: int, H: int, W: int, k: int, dtype=torch.float32, device="cuda") -> torch.Tensor:
+    """A caller-owned workspace tensor (uint8, 256-byte aligned) for hsgd_step / refine."""
+    n = reallife_workspace_bytes(N, D, H, W, k, dtype)
+    return torch.empty(n, dtype=torch.uint8, device=device)
+
+
+def reallife_render(m: Mpi, cams, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """Novel views of the MPI for every camera in ``cams``: ``[T][H][W][3]`` float32."""
+    T = len(cams)
+    if out is None:
+        out = torch.empty((T, m.H, m.W, 3), dtype=torch.float32, device=m.data.device)
+    _check_f32(out, (T, m.H, m.W, 3), "out")
+    ms = m.c_struct()
+    _lib.check("reallife_render", _lib.lib().reallife_render(ctypes.byref(ms), _lib.cameras(cams), T,
+                                                            _ptr(out), _stream(stream)))
+    return out
+
+
+def reallife_hsgd_step(m: Mpi, images: torch.Tensor, src, k: int, lam: float = 1.0, clamp: bool = True,
+                       level: int = 0, loss_out: torch.Tensor | None = None, S_out: torch.Tensor | None = None,
+                       ws: torch.Tensor | None = None, stream=None):
+    """One HSGD iteration on ``m`` in place; returns (loss_out, S_out)."""
+    N = len(src)
+    _check_f32(images, (N, m.H, m.W, 3), "images")
+    if ws is None:
+        ws = workspace(N, m.D, m.H, m.W, k, m.data.dtype, m.data.device)
+    ms = m.c_struct()
+    p = _params(k, lam, clamp, level)
+    _lib.check("reallife_hsgd_step", _lib.lib().reallife_hsgd_step(
+        ctypes.byref(ms), _ptr(images), _lib.cameras(src), N, ctypes.byref(p), _ptr(loss_out), _ptr(S_out),
+        _ptr(ws), ws.numel(), _stream(stream)))
+    return loss_out, S_out
+
+
+def reallife_refine(m: Mpi, images: torch.Tensor, src, k: int, schedule=(2, 1, 0), lam: float = 1.0,
+                    clamp: bool = True, loss_per_iter: torch.Tensor | None = None, ws: torch.Tensor | None = None,
+                    stream=None):
+    """HSGD refinement of ``m`` in place over the level schedule; returns ``loss_per_iter``."""
+    N = len(src)
+    _check_f32(images, (N, m.H, m.W, 3), "images")
+    if ws is None:
+        ws = workspace(N, m.D, m.H, m.W, k, m.data.dtype, m.data.device)
+    sched = (ctypes.c_int * len(schedule))(*[int(s) for s in schedule])
+    ms = m.c_struct()
+    p = _params(k, lam, clamp, 0)
+    _lib.check("reallife_refine", _lib.lib().reallife_refine(
+        ctypes.byref(ms), _ptr(images), _lib.cameras(src), N, ctypes.byref(p), sched, len(schedule),
+        _ptr(loss_per_iter), _ptr(ws), ws.numel(), _stream(stream)))
+    return loss_per_iter
+
+
+def reallife_downsample_f32(x: torch.Tensor, level: int, out: torch.Tensor | None = None, stream=None):
+    """Down^l of ``x[P][H][W][C]`` float32 (2^l x 2^l box average)."""
+    P, H, W, C = x.shape
+    if out is None:
+        out = torch.empty((P, H >> level, W >> level, C), dtype=torch.float32, device=x.device)
+    _lib.check("reallife_downsample_f32", _lib.lib().reallife_downsample_f32(
+        _ptr(x), P, H, W, C, level, _ptr(out), _stream(stream)))
+    return out
+
+
+def reallife_select(m: Mpi, k: int, S: torch.Tensor | None = None, mask: torch.Tensor | None = None, stream=None):
+    """Top-k planes per pixel by the reference-view alpha weight: (S uint8 [k][H][W], mask int64 [H][W])."""
+    dev = m.data.device
+    if S is None:
+        S = torch.empty((k, m.H, m.W), dtype=torch.uint8, device=dev)
+    if mask is None:
+        mask = torch.empty((m.H, m.W), dtype=torch.int64, device=dev)
+    ms = m.c_struct()
+    _lib.check("reallife_select", _lib.lib().reallife_select(ctypes.byref(ms), k, _ptr(S), _ptr(mask),
+                                                            _stream(stream)))
+    return S, mask
+
+
+def reallife_select_keys(keys: torch.Tensor, k: int, stream=None):
+    """Top-k of caller-supplied float32 keys ``[D][H][W]``: (S, mask)."""
+    D, H, W = keys.shape
+    if keys.dtype != torch.float32:
+        raise ValueError("keys must be float32")
+    S = torch.empty((k, H, W), dtype=torch.uint8, device=keys.device)
+    mask = torch.empty((H, W), dtype=torch.int64, device=keys.device)
+    _lib.check("reallife_select_keys", _lib.lib().reallife_select_keys(_ptr(keys), D, H, W, k, _ptr(S), _ptr(mask),
+                                                                      _stream(stream)))
+    return S, mask
+
+
+def reallife_loss_grad(m: Mpi, images: torch.Tensor, src, mask: torch.Tensor | None = None, k: int | None = None,
+                       stream=None):
+    """Photometric loss and its gradient at the MPI's resolution: (loss [1], G).
+
+    Dense ``G [D][H][W][4]`` when ``mask`` is None, else compact ``G [k][H][W][4]``."""
+    N = len(src)
+    _check_f32(images, (N, m.H, m.W, 3), "images")
+    slots = m.D if mask is None else int(k)
+    G = torch.empty((slots, m.H, m.W, 4), dtype=torch.float32, device=m.data.device)
+    loss = torch.empty(1, dtype=torch.float32, device=m.data.device)
+    ws = workspace(N, m.D, m.H, m.W, 1, m.data.dtype, m.data.device)
+    ms = m.c_struct()
+    _lib.check("reallife_loss_grad", _lib.lib().reallife_loss_grad(
+        ctypes.byref(ms), _ptr(images), _lib.cameras(src), N, _ptr(mask), slots, _ptr(G), _ptr(loss), _ptr(ws),
+        ws.numel(), _stream(stream)))
+    return loss, G
+
+
+def reallife_sparse_update(m: Mpi, S: torch.Tensor, G: torch.Tensor, k: int, level: int, lam: float,
+                           clamp: bool = True, stream=None):
+    ms = m.c_struct()
+    _lib.check("reallife_sparse_update", _lib.lib().reallife_sparse_update(
+        ctypes.byref(ms), _ptr(S), _ptr(G), k, level, float(lam), int(bool(clamp)), _stream(stream)))
+
+
+def reallife_render_backward(m: Mpi, cams, grad_out: torch.Tensor, grad_mpi: torch.Tensor | None = None,
+                             stream=None) -> torch.Tensor:
+    """dL/dM (float32 ``[D][H][W][4]``) given dL/dC of the views ``grad_out [N][H][W][3]``."""
+    N = len(cams)
+    _check_f32(grad_out, (N, m.H, m.W, 3), "grad_out")
+    if grad_mpi is None:
+        grad_mpi = torch.empty((m.D, m.H, m.W, 4), dtype=torch.float32, device=m.data.device)
+    ms = m.c_struct()
+    _lib.check("reallife_render_backward", _lib.lib().reallife_render_backward(
+        ctypes.byref(ms), _lib.cameras(cams), N, _ptr(grad_out), _ptr(grad_mpi), _stream(stream)))
+    return grad_mpi
+
+
+def reallife_warp_offsets(m: Mpi, cam, stream=None) -> torch.Tensor:
+    out = torch.empty((m.D, m.H, m.W, 2), dtype=torch.float32, device=m.data.device)
+    ms = m.c_struct()
+    _lib.check("reallife_warp_offsets", _lib.lib().reallife_warp_offsets(
+        ctypes.byref(ms), _lib.cameras([cam]), _ptr(out), _stream(stream)))
+    return out
+
+
+def reallife_trace_enable(on: bool = True):
+    _lib.check("reallife_trace_enable", _lib.lib().reallife_trace_enable(int(bool(on))))
+
+
+def reallife_trace_read() -> dict:
+    """{kernel name: (launches, total device ms)} since the last read (synchronises)."""
+    arr = (_lib.RlTraceEntry * 64)()
+    n = ctypes.c_int()
+    _lib.check("reallife_trace_read", _lib.lib().reallife_trace_read(arr, 64, ctypes.byref(n)))
+    return {arr[i].name.decode(): (int(arr[i].launches), float(arr[i].total_ms)) for i in range(min(n.value, 64))}
+
+
+def reallife_strerror(status: int) -> str:
+    return _lib.lib().reallife_strerror(status).decode()

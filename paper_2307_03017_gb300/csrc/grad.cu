@@ -1,0 +1,184 @@
+// grad.cu -- fused warp + composite + photometric residual + exact adjoint (one launch for
+// all source views), the render backward used by autograd, and the loss reduction.
+//
+// Per view pixel q (one thread), with T_d = prod_{j>d}(1 - alpha_j) (Eq. eq_over):
+//   pass 1, d = D-1 .. 0:  m_d = bilinear(M[d], p_d(q)); T_d -> shared memory;
+//                           C += T_d alpha_d c_d; T *= (1 - alpha_d)
+//   residual:               r = (C - I(q)) / N  (loss mode; L = 1/(2N) sum |C - I|^2)
+//                           or r = dL/dC given by the caller (backward mode)
+//   pass 2, d = 0 .. D-1:  dL/dc_d = T_d alpha_d r;  dL/dalpha_d = T_d <c_d - B_d, r>,
+//                           B_d the composite of the planes below d (B_0 = 0,
+//                           B_{d+1} = c_d alpha_d + (1 - alpha_d) B_d);
+//                           the bilinear transpose adds w_tap * dL/dm_d to the 4 taps.
+// Sparse mode adds only into voxels kept by the selection mask (Sec. 3.3), at slot
+// popcount(mask & ((1 << d) - 1)) of the compact gradient.  No division by (1 - alpha).
+#include "rl_internal.h"
+
+namespace {
+
+constexpr int kGradBX = 32, kGradBY = 4, kGradThreads = kGradBX * kGradBY;
+
+template <bool SPARSE>
+__device__ __forceinline__ void scatter_tap(float* __restrict__ G, const uint64_t* __restrict__ mask, int d, int H,
+                                            int W, int x, int y, float wt, float4 g) {
+    if ((unsigned)x >= (unsigned)W || (unsigned)y >= (unsigned)H || wt == 0.f) return;
+    const size_t pix = (size_t)y * W + x;
+    int slot = d;
+    if (SPARSE) {
+        const uint64_t mk = __ldg(mask + pix);
+        if (!((mk >> d) & 1ull)) return;
+        slot = __popcll(mk & ((1ull << d) - 1ull));
+    }
+    float4* dst = reinterpret_cast<float4*>(G + ((size_t)slot * H * W + pix) * 4);
+    atomicAdd(dst, make_float4(wt * g.x, wt * g.y, wt * g.z, wt * g.w));
+}
+
+template <typename Tm, bool SPARSE, bool LOSS>
+__global__ void __launch_bounds__(kGradThreads)
+k_grad(const Tm* __restrict__ M, int D, int H, int W, const __grid_constant__ RLViews views,
+       const float* __restrict__ images, int img_level, const float* __restrict__ grad_out,
+       const uint64_t* __restrict__ mask, float* __restrict__ G, float inv_n, float* __restrict__ partials) {
+    extern __shared__ float sT[];  // [D][kGradThreads]
+    const int tid = threadIdx.y * kGradBX + threadIdx.x;
+    const int qx = blockIdx.x * kGradBX + threadIdx.x;
+    const int qy = blockIdx.y * kGradBY + threadIdx.y;
+    const int view = blockIdx.z;
+    float lsum = 0.f;
+    if (qx < W && qy < H) {
+        const RLWarp w = rl_warp_coeffs(views.v[view], (float)qx, (float)qy);
+        const size_t plane = (size_t)H * W * 4;
+        float T = 1.f, c0 = 0.f, c1 = 0.f, c2 = 0.f;
+        for (int d = D - 1; d >= 0; --d) {
+            const RLTaps t = rl_taps(w, views.rho[d], qx, qy);
+            const float4 m = rl_sample(M + d * plane, H, W, t);
+            sT[d * kGradThreads + tid] = T;
+            const float a = T * m.w;
+            c0 = fmaf(a, m.x, c0);
+            c1 = fmaf(a, m.y, c1);
+            c2 = fmaf(a, m.z, c2);
+            T = T * (1.f - m.w);
+        }
+        float r0, r1, r2;
+        if (LOSS) {
+            // source image at this level: mean of the 2^l x 2^l full-resolution block
+            const int s = 1 << img_level;
+            const int Wf = W << img_level, Hf = H << img_level;
+            const float* img = images + (size_t)view * Hf * Wf * 3;
+            float i0 = 0.f, i1 = 0.f, i2 = 0.f;
+            for (int yy = 0; yy < s; ++yy)
+                for (int xx = 0; xx < s; ++xx) {
+                    const float* px = img + ((size_t)(qy * s + yy) * Wf + (qx * s + xx)) * 3;
+                    i0 += __ldg(px);
+                    i1 += __ldg(px + 1);
+                    i2 += __ldg(px + 2);
+                }
+            const float inv_area = 1.f / (float)(s * s);
+            const float e0 = c0 - i0 * inv_area, e1 = c1 - i1 * inv_area, e2 = c2 - i2 * inv_area;
+            lsum = fmaf(e0, e0, fmaf(e1, e1, e2 * e2));
+            r0 = e0 * inv_n;
+            r1 = e1 * inv_n;
+            r2 = e2 * inv_n;
+        } else {
+            const float* go = grad_out + (((size_t)view * H + qy) * W + qx) * 3;
+            r0 = __ldg(go);
+            r1 = __ldg(go + 1);
+            r2 = __ldg(go + 2);
+        }
+        float b0 = 0.f, b1 = 0.f, b2 = 0.f;
+        for (int d = 0; d < D; ++d) {
+            const RLTaps t = rl_taps(w, views.rho[d], qx, qy);
+            const float4 m = rl_sample(M + d * plane, H, W, t);
+            const float Td = sT[d * kGradThreads + tid];
+            if (t.ok && Td != 0.f) {
+                const float gc = Td * m.w;
+                float4 g;
+                g.x = gc * r0;
+                g.y = gc * r1;
+                g.z = gc * r2;
+                g.w = Td * fmaf(m.x - b0, r0, fmaf(m.y - b1, r1, (m.z - b2) * r2));
+                const float w00 = (1.f - t.fx) * (1.f - t.fy), w10 = t.fx * (1.f - t.fy);
+                const float w01 = (1.f - t.fx) * t.fy, w11 = t.fx * t.fy;
+                scatter_tap<SPARSE>(G, mask, d, H, W, t.x0, t.y0, w00, g);
+                scatter_tap<SPARSE>(G, mask, d, H, W, t.x0 + 1, t.y0, w10, g);
+                scatter_tap<SPARSE>(G, mask, d, H, W, t.x0, t.y0 + 1, w01, g);
+                scatter_tap<SPARSE>(G, mask, d, H, W, t.x0 + 1, t.y0 + 1, w11, g);
+            }
+            const float om = 1.f - m.w;
+            b0 = fmaf(m.x, m.w, om * b0);
+            b1 = fmaf(m.y, m.w, om * b1);
+            b2 = fmaf(m.z, m.w, om * b2);
+        }
+    }
+    if (LOSS) {
+        __shared__ float red[kGradThreads / 32];
+        lsum = rl_warp_sum(lsum);
+        if ((tid & 31) == 0) red[tid >> 5] = lsum;
+        __syncthreads();
+        if (tid == 0) {
+            float s = 0.f;
+            for (int j = 0; j < kGradThreads / 32; ++j) s += red[j];
+            partials[blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z)] = s;
+        }
+    }
+}
+
+// Deterministic sum of the per-block partials (fixed order), times `scale`.
+__global__ void __launch_bounds__(1024) k_loss_reduce(const float* __restrict__ partials, int n, float scale,
+                                                     float* __restrict__ out) {
+    __shared__ float red[32];
+    float s = 0.f;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) s += partials[i];
+    s = rl_warp_sum(s);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        float v = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.f;
+        v = rl_warp_sum(v);
+        if (threadIdx.x == 0) out[0] = v * scale;
+    }
+}
+
+template <typename Tm, bool SPARSE, bool LOSS>
+void launch_grad_t(const void* M, int D, int H, int W, const RLViews& views, const float* images, int img_level,
+                   const float* grad_out, const uint64_t* mask, float* G, float inv_n, float* partials, dim3 grid,
+                   size_t smem, cudaStream_t s) {
+    auto kern = k_grad<Tm, SPARSE, LOSS>;
+    if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    kern<<<grid, dim3(kGradBX, kGradBY), smem, s>>>((const Tm*)M, D, H, W, views, images, img_level, grad_out, mask, G,
+                                                    inv_n, partials);
+}
+
+}  // namespace
+
+size_t rl_grad_num_blocks(int H, int W, int N) {
+    return (size_t)((W + kGradBX - 1) / kGradBX) * ((H + kGradBY - 1) / kGradBY) * N;
+}
+
+rl_status rl_launch_grad(const void* M, rl_dtype dt, int D, int H, int W, const RLViews& views, bool mode_loss,
+                         const float* images, int img_level, const float* grad_out, const uint64_t* mask, float* G,
+                         float inv_n, float* partials, int* nblocks, cudaStream_t s) {
+    dim3 grid((W + kGradBX - 1) / kGradBX, (H + kGradBY - 1) / kGradBY, views.n);
+    const size_t smem = (size_t)D * kGradThreads * sizeof(float);
+    if (nblocks) *nblocks = (int)(grid.x * grid.y * grid.z);
+    const bool sparse = mask != nullptr;
+    const char* name = dt == RL_F32 ? (sparse ? "grad_sparse_f32" : "grad_dense_f32")
+                                    : (sparse ? "grad_sparse_bf16" : "grad_dense_bf16");
+    RLTraceScope ts(name, s);
+#define RL_GRAD_CASE(TM, SP, LS) \
+    launch_grad_t<TM, SP, LS>(M, D, H, W, views, images, img_level, grad_out, mask, G, inv_n, partials, grid, smem, s)
+    if (dt == RL_F32) {
+        if (sparse) { if (mode_loss) RL_GRAD_CASE(float, true, true); else RL_GRAD_CASE(float, true, false); }
+        else        { if (mode_loss) RL_GRAD_CASE(float, false, true); else RL_GRAD_CASE(float, false, false); }
+    } else {
+        if (sparse) { if (mode_loss) RL_GRAD_CASE(__nv_bfloat16, true, true); else RL_GRAD_CASE(__nv_bfloat16, true, false); }
+        else        { if (mode_loss) RL_GRAD_CASE(__nv_bfloat16, false, true); else RL_GRAD_CASE(__nv_bfloat16, false, false); }
+    }
+#undef RL_GRAD_CASE
+    return rl_check_launch("grad");
+}
+
+rl_status rl_launch_loss_reduce(const float* partials, int n, float scale, float* out, cudaStream_t s) {
+    RLTraceScope ts("loss_reduce", s);
+    k_loss_reduce<<<1, 1024, 0, s>>>(partials, n, scale, out);
+    return rl_check_launch("loss_reduce");
+}

@@ -1,0 +1,458 @@
+// reallife_api.cu -- the C ABI of libreallife (include/reallife.h): host-side validation,
+// camera geometry in FP64, workspace layout, kernel sequencing and launch tracing.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "rl_internal.h"
+
+// ------------------------------------------------------------------ errors
+
+static thread_local char g_err[512] = "";
+
+rl_status rl_fail(rl_status st, const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+    return st;
+}
+
+rl_status rl_check_launch(const char* what) {
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return rl_fail(RL_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+    return RL_OK;
+}
+
+extern "C" const char* reallife_strerror(rl_status s) {
+    switch (s) {
+        case RL_OK: return "ok";
+        case RL_EINVAL: return "invalid argument";
+        case RL_ENOMEM: return "workspace too small";
+        case RL_ECUDA: return "CUDA error";
+        case RL_ETIMEOUT: return "device wait timed out";
+        case RL_ENOTIMPL: return "not implemented";
+    }
+    return "unknown status";
+}
+
+extern "C" const char* reallife_last_error(void) { return g_err; }
+
+// ------------------------------------------------------------------ tracing
+
+namespace {
+struct TracePending {
+    int name;
+    cudaEvent_t a, b;
+};
+std::mutex g_tmu;
+bool g_trace_on = false;
+std::vector<TracePending> g_pending;
+std::vector<cudaEvent_t> g_free_events;
+std::vector<std::string> g_names;
+std::vector<long long> g_counts;
+
+cudaEvent_t take_event() {
+    if (!g_free_events.empty()) {
+        cudaEvent_t e = g_free_events.back();
+        g_free_events.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+int name_index(const char* name) {
+    for (size_t i = 0; i < g_names.size(); ++i)
+        if (g_names[i] == name) return (int)i;
+    g_names.emplace_back(name);
+    g_counts.push_back(0);
+    return (int)g_names.size() - 1;
+}
+}  // namespace
+
+int rl_trace_begin(const char* name, cudaStream_t s) {
+    std::lock_guard<std::mutex> lk(g_tmu);
+    if (!g_trace_on) return -1;
+    TracePending p;
+    p.name = name_index(name);
+    g_counts[p.name] += 1;
+    p.a = take_event();
+    p.b = take_event();
+    cudaEventRecord(p.a, s);
+    g_pending.push_back(p);
+    return (int)g_pending.size() - 1;
+}
+
+void rl_trace_end(int token, cudaStream_t s) {
+    if (token < 0) return;
+    std::lock_guard<std::mutex> lk(g_tmu);
+    if (token < (int)g_pending.size()) cudaEventRecord(g_pending[token].b, s);
+}
+
+extern "C" rl_status reallife_trace_enable(int on) {
+    std::lock_guard<std::mutex> lk(g_tmu);
+    g_trace_on = on != 0;
+    return RL_OK;
+}
+
+extern "C" rl_status reallife_trace_read(rl_trace_entry* out, int max, int* n_out) {
+    std::lock_guard<std::mutex> lk(g_tmu);
+    std::vector<double> ms(g_names.size(), 0.0);
+    rl_status st = RL_OK;
+    for (const TracePending& p : g_pending) {
+        float t = 0.f;
+        if (cudaEventSynchronize(p.b) != cudaSuccess || cudaEventElapsedTime(&t, p.a, p.b) != cudaSuccess)
+            st = rl_fail(RL_ECUDA, "trace: %s", cudaGetErrorString(cudaGetLastError()));
+        ms[p.name] += t;
+        g_free_events.push_back(p.a);
+        g_free_events.push_back(p.b);
+    }
+    g_pending.clear();
+    int n = 0;
+    for (size_t i = 0; i < g_names.size(); ++i) {
+        if (g_counts[i] == 0) continue;
+        if (out && n < max) {
+            std::memset(out[n].name, 0, sizeof(out[n].name));
+            std::strncpy(out[n].name, g_names[i].c_str(), sizeof(out[n].name) - 1);
+            out[n].launches = g_counts[i];
+            out[n].total_ms = ms[i];
+        }
+        ++n;
+        g_counts[i] = 0;
+    }
+    if (n_out) *n_out = n;
+    return st;
+}
+
+// ------------------------------------------------------------------ geometry
+
+namespace {
+
+bool finite_all(const double* v, int n) {
+    for (int i = 0; i < n; ++i)
+        if (!std::isfinite(v[i])) return false;
+    return true;
+}
+
+// Zero-skew pinhole with last row (0,0,1), finite pose, R orthonormal to 1e-6.
+bool camera_ok(const rl_camera& c) {
+    if (!finite_all(c.K, 9) || !finite_all(c.R, 9) || !finite_all(c.t, 3)) return false;
+    if (c.K[1] != 0.0 || c.K[3] != 0.0 || c.K[6] != 0.0 || c.K[7] != 0.0 || c.K[8] != 1.0) return false;
+    if (!(c.K[0] > 0.0) || !(c.K[4] > 0.0)) return false;
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) {
+            double s = 0.0;
+            for (int j = 0; j < 3; ++j) s += c.R[a * 3 + j] * c.R[b * 3 + j];
+            if (std::fabs(s - (a == b ? 1.0 : 0.0)) > 1e-6) return false;
+        }
+    return true;
+}
+
+rl_camera camera_at_level(const rl_camera& c, int level) {
+    rl_camera o = c;
+    const double s = std::ldexp(1.0, -level);
+    o.K[0] = c.K[0] * s;
+    o.K[4] = c.K[4] * s;
+    o.K[2] = (c.K[2] + 0.5) * s - 0.5;
+    o.K[5] = (c.K[5] + 0.5) * s - 0.5;
+    return o;
+}
+
+// Relative pose of `view` w.r.t. the reference camera (Eq. eq_homo's R_i R_r^{-1} and
+// t_i - R_i R_r^{-1} t_r), reduced to the per-pixel warp parameters of rl_common.cuh.
+RLViewParam view_param(const rl_camera& ref, const rl_camera& view) {
+    double Rrel[9];  // R_v R_r^T
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) {
+            double s = 0.0;
+            for (int j = 0; j < 3; ++j) s += view.R[a * 3 + j] * ref.R[b * 3 + j];
+            Rrel[a * 3 + b] = s;
+        }
+    RLViewParam P;
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) P.E[a * 3 + b] = (float)(Rrel[b * 3 + a] - (a == b ? 1.0 : 0.0));
+    // centre of the view in the reference frame: -R_rel^T t_v + t_r
+    for (int a = 0; a < 3; ++a) {
+        double s = 0.0;
+        for (int j = 0; j < 3; ++j) s += Rrel[j * 3 + a] * view.t[j];
+        P.C[a] = (float)(ref.t[a] - s);
+    }
+    P.inv_fxv = (float)(1.0 / view.K[0]);
+    P.inv_fyv = (float)(1.0 / view.K[4]);
+    P.cxv = (float)view.K[2];
+    P.cyv = (float)view.K[5];
+    P.fxr = (float)ref.K[0];
+    P.fyr = (float)ref.K[4];
+    P.dcx = (float)(ref.K[2] - view.K[2]);
+    P.dcy = (float)(ref.K[5] - view.K[5]);
+    P.dfx = (float)(ref.K[0] - view.K[0]);
+    P.dfy = (float)(ref.K[4] - view.K[4]);
+    return P;
+}
+
+void fill_rho(RLViews& v, int D, double near_, double far_) {
+    for (int d = 0; d < RL_DEV_MAX_PLANES; ++d) v.rho[d] = 0.f;
+    for (int d = 0; d < D; ++d) {
+        const double r = (D == 1) ? 1.0 / far_ : 1.0 / far_ + ((double)d / (double)(D - 1)) * (1.0 / near_ - 1.0 / far_);
+        v.rho[d] = (float)r;
+    }
+}
+
+rl_status check_mpi(const rl_mpi* m) {
+    if (!m) return rl_fail(RL_EINVAL, "mpi is NULL");
+    if (m->D < 1 || m->D > RL_MAX_PLANES) return rl_fail(RL_EINVAL, "D=%d outside [1,%d]", m->D, RL_MAX_PLANES);
+    if (m->H < 1 || m->W < 1) return rl_fail(RL_EINVAL, "H=%d W=%d must be positive", m->H, m->W);
+    if ((long long)m->H * m->W > (1ll << 30)) return rl_fail(RL_EINVAL, "H*W too large");
+    if (m->dtype != RL_F32 && m->dtype != RL_BF16) return rl_fail(RL_EINVAL, "unknown dtype %d", (int)m->dtype);
+    if (!m->data) return rl_fail(RL_EINVAL, "mpi data is NULL");
+    if (((uintptr_t)m->data & 15) != 0) return rl_fail(RL_EINVAL, "mpi data must be 16-byte aligned");
+    if (!(m->near_ > 0.0) || !(m->far_ > m->near_) || !std::isfinite(m->far_))
+        return rl_fail(RL_EINVAL, "need 0 < near < far < inf (near=%g far=%g)", m->near_, m->far_);
+    if (!camera_ok(m->ref)) return rl_fail(RL_EINVAL, "reference camera invalid (zero-skew K, orthonormal R)");
+    return RL_OK;
+}
+
+rl_status make_views(const rl_mpi* m, const rl_camera* cams, int n, int level, RLViews& v) {
+    if (!cams) return rl_fail(RL_EINVAL, "camera array is NULL");
+    if (n < 1 || n > RL_DEV_MAX_VIEWS) return rl_fail(RL_EINVAL, "%d views outside [1,%d]", n, RL_DEV_MAX_VIEWS);
+    std::memset(&v, 0, sizeof(v));
+    v.n = n;
+    fill_rho(v, m->D, m->near_, m->far_);
+    const rl_camera ref = camera_at_level(m->ref, level);
+    for (int i = 0; i < n; ++i) {
+        if (!camera_ok(cams[i])) return rl_fail(RL_EINVAL, "camera %d invalid (zero-skew K, orthonormal R)", i);
+        v.v[i] = view_param(ref, camera_at_level(cams[i], level));
+    }
+    return RL_OK;
+}
+
+size_t elt_size(rl_dtype dt) { return dt == RL_F32 ? 4 : 2; }
+
+size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
+
+struct WsLayout {
+    size_t Ml, S, mask, G, partials, total;
+};
+
+// One workspace serves every level of a schedule: level 0 has the largest selection and
+// gradient buffers, level 1 the largest downsampled MPI.
+WsLayout ws_layout(int N, int D, int H, int W, int k, rl_dtype dt) {
+    WsLayout L;
+    size_t off = 0;
+    L.Ml = off;
+    if (H % 2 == 0 && W % 2 == 0) off += align_up((size_t)D * (H / 2) * (W / 2) * 4 * elt_size(dt));
+    L.S = off;
+    off += align_up((size_t)k * H * W);
+    L.mask = off;
+    off += align_up((size_t)H * W * 8);
+    L.G = off;
+    off += align_up((size_t)k * H * W * 16);
+    L.partials = off;
+    off += align_up(rl_grad_num_blocks(H, W, N) * sizeof(float));
+    L.total = off;
+    return L;
+}
+
+rl_status check_hsgd(const rl_mpi* m, const float* images, const rl_camera* src, int N, const rl_hsgd_params* p,
+                     int level, void* ws, size_t ws_bytes) {
+    rl_status st = check_mpi(m);
+    if (st) return st;
+    if (!p) return rl_fail(RL_EINVAL, "params is NULL");
+    if (p->k < 1 || p->k > m->D) return rl_fail(RL_EINVAL, "k=%d outside [1, D=%d]", p->k, m->D);
+    if (!std::isfinite(p->lambda)) return rl_fail(RL_EINVAL, "lambda not finite");
+    if (level < 0 || level > 10 || (m->H % (1 << level)) || (m->W % (1 << level)))
+        return rl_fail(RL_EINVAL, "level %d: H=%d and W=%d must be divisible by 2^level", level, m->H, m->W);
+    if (!images) return rl_fail(RL_EINVAL, "images is NULL");
+    if (N < 1 || N > RL_MAX_VIEWS) return rl_fail(RL_EINVAL, "N=%d outside [1,%d]", N, RL_MAX_VIEWS);
+    if (!src) return rl_fail(RL_EINVAL, "source cameras NULL");
+    for (int i = 0; i < N; ++i)
+        if (!camera_ok(src[i])) return rl_fail(RL_EINVAL, "source camera %d invalid", i);
+    if (!ws) return rl_fail(RL_EINVAL, "workspace is NULL");
+    const size_t need = ws_layout(N, m->D, m->H, m->W, p->k, m->dtype).total;
+    if (ws_bytes < need) return rl_fail(RL_ENOMEM, "workspace %zu bytes < %zu needed", ws_bytes, need);
+    if (((uintptr_t)ws & 255) != 0) return rl_fail(RL_EINVAL, "workspace must be 256-byte aligned");
+    return RL_OK;
+}
+
+// Enqueue one HSGD iteration (arguments already validated).
+rl_status enqueue_hsgd(rl_mpi* m, const float* images, const rl_camera* src, int N, int k, float lambda, int clamp01,
+                       int level, float* loss_out, uint8_t* S_out, void* ws, cudaStream_t s) {
+    const WsLayout L = ws_layout(N, m->D, m->H, m->W, k, m->dtype);
+    char* base = (char*)ws;
+    const int h = m->H >> level, w = m->W >> level;
+    void* Ml = level == 0 ? m->data : (void*)(base + L.Ml);
+    uint8_t* S = S_out ? S_out : (uint8_t*)(base + L.S);
+    uint64_t* mask = (uint64_t*)(base + L.mask);
+    float* G = (float*)(base + L.G);
+    float* partials = (float*)(base + L.partials);
+    RLViews views;
+    rl_status st = make_views(m, src, N, level, views);
+    if (st) return st;
+    st = rl_launch_select(m->data, m->dtype, nullptr, m->D, m->H, m->W, level, level ? Ml : nullptr, k, S, mask, G, s);
+    if (st) return st;
+    int nb = 0;
+    st = rl_launch_grad(Ml, m->dtype, m->D, h, w, views, true, images, level, nullptr, mask, G, 1.0f / (float)N,
+                        partials, &nb, s);
+    if (st) return st;
+    if (loss_out) {
+        st = rl_launch_loss_reduce(partials, nb, 0.5f / (float)N, loss_out, s);
+        if (st) return st;
+    }
+    return rl_launch_update(m->data, m->dtype, m->D, m->H, m->W, level, S, G, k, lambda, clamp01, s);
+}
+
+__global__ void k_zero(float4* __restrict__ p, size_t n4) {
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += (size_t)gridDim.x * blockDim.x)
+        p[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+}
+
+rl_status launch_zero(float* p, size_t nfloats, cudaStream_t s) {
+    RLTraceScope ts("zero_fill", s);
+    const size_t n4 = nfloats / 4;  // callers pass multiples of 4 floats
+    const unsigned blocks = (unsigned)std::min<size_t>((n4 + 255) / 256, 152 * 16);
+    if (n4) k_zero<<<blocks ? blocks : 1, 256, 0, s>>>((float4*)p, n4);
+    return rl_check_launch("zero_fill");
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ C ABI
+
+extern "C" size_t reallife_workspace_bytes(int N, int D, int H, int W, int k, rl_dtype dtype) {
+    if (N < 1 || D < 1 || H < 1 || W < 1 || k < 1) return 0;
+    return ws_layout(N, D, H, W, k, dtype).total;
+}
+
+extern "C" rl_status reallife_render(const rl_mpi* m, const rl_camera* tgt, int T, float* out, cudaStream_t stream) {
+    rl_status st = check_mpi(m);
+    if (st) return st;
+    if (!tgt || T < 1) return rl_fail(RL_EINVAL, "need T >= 1 target cameras");
+    if (!out) return rl_fail(RL_EINVAL, "out is NULL");
+    for (int i = 0; i < T; ++i)
+        if (!camera_ok(tgt[i])) return rl_fail(RL_EINVAL, "target camera %d invalid", i);
+    for (int i0 = 0; i0 < T; i0 += RL_DEV_MAX_VIEWS) {
+        const int n = std::min(RL_DEV_MAX_VIEWS, T - i0);
+        RLViews views;
+        st = make_views(m, tgt + i0, n, 0, views);
+        if (st) return st;
+        st = rl_launch_render(m->data, m->dtype, m->D, m->H, m->W, views, out + (size_t)i0 * m->H * m->W * 3, stream);
+        if (st) return st;
+    }
+    return RL_OK;
+}
+
+extern "C" rl_status reallife_hsgd_step(rl_mpi* m, const float* images, const rl_camera* src, int N,
+                                        const rl_hsgd_params* p, float* loss_out, uint8_t* S_out, void* ws,
+                                        size_t ws_bytes, cudaStream_t stream) {
+    rl_status st = check_hsgd(m, images, src, N, p, p ? p->level : 0, ws, ws_bytes);
+    if (st) return st;
+    return enqueue_hsgd(m, images, src, N, p->k, p->lambda, p->clamp01, p->level, loss_out, S_out, ws, stream);
+}
+
+extern "C" rl_status reallife_refine(rl_mpi* m, const float* images, const rl_camera* src, int N,
+                                     const rl_hsgd_params* p, const int* schedule, int iters, float* loss_per_iter,
+                                     void* ws, size_t ws_bytes, cudaStream_t stream) {
+    if (!schedule || iters < 1) return rl_fail(RL_EINVAL, "need a schedule of >= 1 levels");
+    for (int it = 0; it < iters; ++it) {
+        rl_status st = check_hsgd(m, images, src, N, p, schedule[it], ws, ws_bytes);
+        if (st) return st;
+    }
+    for (int it = 0; it < iters; ++it) {
+        rl_status st = enqueue_hsgd(m, images, src, N, p->k, p->lambda, p->clamp01, schedule[it],
+                                    loss_per_iter ? loss_per_iter + it : nullptr, nullptr, ws, stream);
+        if (st) return st;
+    }
+    return RL_OK;
+}
+
+extern "C" rl_status reallife_downsample_f32(const float* x, int P, int H, int W, int C, int level, float* y,
+                                             cudaStream_t stream) {
+    if (!x || !y || P < 1 || H < 1 || W < 1 || C < 1 || level < 0 || level > 10 || (H % (1 << level)) ||
+        (W % (1 << level)))
+        return rl_fail(RL_EINVAL, "downsample: bad arguments (H, W must be divisible by 2^level)");
+    return rl_launch_downsample_f32(x, P, H, W, C, level, y, stream);
+}
+
+extern "C" rl_status reallife_select(const rl_mpi* m, int k, uint8_t* S, uint64_t* mask, cudaStream_t stream) {
+    rl_status st = check_mpi(m);
+    if (st) return st;
+    if (k < 1 || k > m->D) return rl_fail(RL_EINVAL, "k=%d outside [1, D=%d]", k, m->D);
+    if (!S && !mask) return rl_fail(RL_EINVAL, "select: no output");
+    return rl_launch_select(m->data, m->dtype, nullptr, m->D, m->H, m->W, 0, nullptr, k, S, mask, nullptr, stream);
+}
+
+extern "C" rl_status reallife_select_keys(const float* keys, int D, int H, int W, int k, uint8_t* S, uint64_t* mask,
+                                          cudaStream_t stream) {
+    if (!keys || D < 1 || D > RL_MAX_PLANES || H < 1 || W < 1 || k < 1 || k > D || (!S && !mask))
+        return rl_fail(RL_EINVAL, "select_keys: bad arguments");
+    return rl_launch_select(nullptr, RL_F32, keys, D, H, W, 0, nullptr, k, S, mask, nullptr, stream);
+}
+
+extern "C" rl_status reallife_loss_grad(const rl_mpi* m, const float* images, const rl_camera* src, int N,
+                                        const uint64_t* mask, int k, float* G, float* loss_out, void* ws,
+                                        size_t ws_bytes, cudaStream_t stream) {
+    rl_status st = check_mpi(m);
+    if (st) return st;
+    if (!images || !G) return rl_fail(RL_EINVAL, "loss_grad: images and G must be non-NULL");
+    if (((uintptr_t)G & 15) != 0) return rl_fail(RL_EINVAL, "G must be 16-byte aligned");
+    if (mask && (k < 1 || k > m->D)) return rl_fail(RL_EINVAL, "k=%d outside [1, D=%d]", k, m->D);
+    if (!ws) return rl_fail(RL_EINVAL, "workspace is NULL");
+    RLViews views;
+    st = make_views(m, src, N, 0, views);
+    if (st) return st;
+    const size_t need = align_up(rl_grad_num_blocks(m->H, m->W, N) * sizeof(float));
+    if (ws_bytes < need) return rl_fail(RL_ENOMEM, "workspace %zu bytes < %zu needed", ws_bytes, need);
+    const int slots = mask ? k : m->D;
+    st = launch_zero(G, (size_t)slots * m->H * m->W * 4, stream);
+    if (st) return st;
+    int nb = 0;
+    st = rl_launch_grad(m->data, m->dtype, m->D, m->H, m->W, views, true, images, 0, nullptr, mask, G,
+                        1.0f / (float)N, (float*)ws, &nb, stream);
+    if (st) return st;
+    if (loss_out) return rl_launch_loss_reduce((float*)ws, nb, 0.5f / (float)N, loss_out, stream);
+    return RL_OK;
+}
+
+extern "C" rl_status reallife_sparse_update(rl_mpi* m, const uint8_t* S, const float* G, int k, int level,
+                                            float lambda, int clamp01, cudaStream_t stream) {
+    rl_status st = check_mpi(m);
+    if (st) return st;
+    if (!S || !G) return rl_fail(RL_EINVAL, "sparse_update: S and G must be non-NULL");
+    if (((uintptr_t)G & 15) != 0) return rl_fail(RL_EINVAL, "G must be 16-byte aligned");
+    if (k < 1 || k > m->D) return rl_fail(RL_EINVAL, "k=%d outside [1, D=%d]", k, m->D);
+    if (level < 0 || level > 10 || (m->H % (1 << level)) || (m->W % (1 << level)))
+        return rl_fail(RL_EINVAL, "level %d incompatible with H=%d W=%d", level, m->H, m->W);
+    if (!std::isfinite(lambda)) return rl_fail(RL_EINVAL, "lambda not finite");
+    return rl_launch_update(m->data, m->dtype, m->D, m->H, m->W, level, S, G, k, lambda, clamp01, stream);
+}
+
+extern "C" rl_status reallife_render_backward(const rl_mpi* m, const rl_camera* views_in, int N, const float* grad_out,
+                                              float* grad_mpi, cudaStream_t stream) {
+    rl_status st = check_mpi(m);
+    if (st) return st;
+    if (!grad_out || !grad_mpi) return rl_fail(RL_EINVAL, "render_backward: NULL buffer");
+    if (((uintptr_t)grad_mpi & 15) != 0) return rl_fail(RL_EINVAL, "grad_mpi must be 16-byte aligned");
+    RLViews views;
+    st = make_views(m, views_in, N, 0, views);
+    if (st) return st;
+    st = launch_zero(grad_mpi, (size_t)m->D * m->H * m->W * 4, stream);
+    if (st) return st;
+    return rl_launch_grad(m->data, m->dtype, m->D, m->H, m->W, views, false, nullptr, 0, grad_out, nullptr, grad_mpi,
+                          1.0f, nullptr, nullptr, stream);
+}
+
+extern "C" rl_status reallife_warp_offsets(const rl_mpi* m, const rl_camera* view, float* out, cudaStream_t stream) {
+    rl_status st = check_mpi(m);
+    if (st) return st;
+    if (!out) return rl_fail(RL_EINVAL, "out is NULL");
+    RLViews views;
+    st = make_views(m, view, 1, 0, views);
+    if (st) return st;
+    return rl_launch_warp_offsets(m->D, m->H, m->W, views, out, stream);
+}

@@ -1,0 +1,151 @@
+// rl_common.cuh -- device-side building blocks shared by the RealLiFe kernels (sm_103a).
+//
+// Warp geometry.  For a view camera v and the reference camera r, let R_rel = R_v R_r^T and
+// C the view's centre in the reference frame.  The ray of view pixel q = (u, v) has
+// reference-frame direction dir = R_rel^T K_v^{-1} (u, v, 1); it meets the fronto-parallel
+// plane z = 1/rho at the reference pixel
+//     p = q + a(q) + rho * b(q),
+//     a_x = (cx_r - cx_v) + (fx_r - fx_v) m_x + fx_r (dir_x/dir_z - m_x),
+//     b_x = fx_r (C_x - C_z dir_x/dir_z),         (same for y)
+// with m = K_v^{-1} q.  This is the inverse of the plane-induced homography of Eq. (eq_homo)
+// written per pixel: exact, linear in inverse depth, and evaluated as small offsets from q
+// so that FP32 keeps ~1e-6 px of accuracy at 2k-pixel coordinates.  The plane is met in
+// front of the view iff dir_z > 0 and 1 - rho C_z > 0.
+#pragma once
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#define RL_DEV_MAX_PLANES 64
+#define RL_DEV_MAX_VIEWS 16
+
+struct RLViewParam {
+    float E[9];          // R_rel^T - I (row-major)
+    float C[3];          // view centre in the reference frame
+    float inv_fxv, inv_fyv, cxv, cyv;
+    float fxr, fyr;      // reference focal lengths
+    float dcx, dcy;      // cx_r - cx_v, cy_r - cy_v
+    float dfx, dfy;      // fx_r - fx_v, fy_r - fy_v
+};
+
+// Views and plane inverse depths of one launch, passed by value as a kernel parameter.
+struct RLViews {
+    int n;
+    float rho[RL_DEV_MAX_PLANES];
+    RLViewParam v[RL_DEV_MAX_VIEWS];
+};
+
+// Per-pixel warp coefficients of one view.
+struct RLWarp {
+    float ax, ay, bx, by, cz;
+    bool dir_ok;
+};
+
+__device__ __forceinline__ RLWarp rl_warp_coeffs(const RLViewParam& P, float u, float v) {
+    RLWarp w;
+    float mx = (u - P.cxv) * P.inv_fxv;
+    float my = (v - P.cyv) * P.inv_fyv;
+    float ex = fmaf(P.E[0], mx, fmaf(P.E[1], my, P.E[2]));
+    float ey = fmaf(P.E[3], mx, fmaf(P.E[4], my, P.E[5]));
+    float ez = fmaf(P.E[6], mx, fmaf(P.E[7], my, P.E[8]));
+    float dz = 1.0f + ez;
+    float inv_dz = 1.0f / dz;
+    // r - m = (e - m e_z) / dir_z : small, computed without cancellation
+    float rmx = fmaf(-mx, ez, ex) * inv_dz;
+    float rmy = fmaf(-my, ez, ey) * inv_dz;
+    float rx = mx + rmx, ry = my + rmy;
+    w.ax = P.dcx + fmaf(P.dfx, mx, P.fxr * rmx);
+    w.ay = P.dcy + fmaf(P.dfy, my, P.fyr * rmy);
+    w.bx = P.fxr * fmaf(-P.C[2], rx, P.C[0]);
+    w.by = P.fyr * fmaf(-P.C[2], ry, P.C[1]);
+    w.cz = P.C[2];
+    w.dir_ok = dz > 0.0f;
+    return w;
+}
+
+// Bilinear footprint of one sample: top-left tap (x0, y0) and fractional offsets.
+struct RLTaps {
+    int x0, y0;
+    float fx, fy;
+    bool ok;  // plane met in front of the view
+};
+
+__device__ __forceinline__ RLTaps rl_taps(const RLWarp& w, float rho, int qx, int qy) {
+    RLTaps t;
+    float dx = fmaf(rho, w.bx, w.ax);
+    float dy = fmaf(rho, w.by, w.ay);
+    float flx = floorf(dx), fly = floorf(dy);
+    t.fx = dx - flx;  // exact
+    t.fy = dy - fly;
+    t.x0 = qx + (int)flx;
+    t.y0 = qy + (int)fly;
+    t.ok = w.dir_ok && (fmaf(-rho, w.cz, 1.0f) > 0.0f) && fabsf(dx) < 1.0e7f && fabsf(dy) < 1.0e7f;
+    return t;
+}
+
+// ---------------------------------------------------------------- storage types
+
+template <typename T> struct RLStore;
+
+template <> struct RLStore<float> {
+    static __device__ __forceinline__ float4 load4(const float* p) { return __ldg(reinterpret_cast<const float4*>(p)); }
+    static __device__ __forceinline__ float4 load4_nc(const float* p) { return *reinterpret_cast<const float4*>(p); }
+    static __device__ __forceinline__ void store4(float* p, float4 v) { *reinterpret_cast<float4*>(p) = v; }
+    static __device__ __forceinline__ float load1(const float* p) { return __ldg(p); }
+    static __device__ __forceinline__ float round1(float v) { return v; }
+};
+
+template <> struct RLStore<__nv_bfloat16> {
+    static __device__ __forceinline__ float4 cvt(uint2 r) {
+        float4 o;
+        o.x = __uint_as_float(r.x << 16);
+        o.y = __uint_as_float(r.x & 0xffff0000u);
+        o.z = __uint_as_float(r.y << 16);
+        o.w = __uint_as_float(r.y & 0xffff0000u);
+        return o;
+    }
+    static __device__ __forceinline__ float4 load4(const __nv_bfloat16* p) {
+        return cvt(__ldg(reinterpret_cast<const uint2*>(p)));
+    }
+    static __device__ __forceinline__ float4 load4_nc(const __nv_bfloat16* p) {
+        return cvt(*reinterpret_cast<const uint2*>(p));
+    }
+    static __device__ __forceinline__ void store4(__nv_bfloat16* p, float4 v) {
+        __nv_bfloat162 lo = __floats2bfloat162_rn(v.x, v.y);  // round to nearest even
+        __nv_bfloat162 hi = __floats2bfloat162_rn(v.z, v.w);
+        uint2 r;
+        r.x = *reinterpret_cast<uint32_t*>(&lo);
+        r.y = *reinterpret_cast<uint32_t*>(&hi);
+        *reinterpret_cast<uint2*>(p) = r;
+    }
+    static __device__ __forceinline__ float load1(const __nv_bfloat16* p) { return __bfloat162float(*p); }
+    // the value a store of v would hold
+    static __device__ __forceinline__ float round1(float v) { return __bfloat162float(__float2bfloat16_rn(v)); }
+};
+
+// Bilinear sample (zero padding per tap) of plane `plane` (base pointer of [H][W][4]).
+template <typename Tm>
+__device__ __forceinline__ float4 rl_sample(const Tm* __restrict__ plane, int H, int W, const RLTaps& t) {
+    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (!t.ok) return acc;
+    const float w00 = (1.f - t.fx) * (1.f - t.fy), w10 = t.fx * (1.f - t.fy);
+    const float w01 = (1.f - t.fx) * t.fy, w11 = t.fx * t.fy;
+    const bool x0in = (unsigned)t.x0 < (unsigned)W, x1in = (unsigned)(t.x0 + 1) < (unsigned)W;
+    const bool y0in = (unsigned)t.y0 < (unsigned)H, y1in = (unsigned)(t.y0 + 1) < (unsigned)H;
+    const size_t r0 = (size_t)t.y0 * W, r1 = r0 + W;
+    if (y0in) {
+        if (x0in) { float4 v = RLStore<Tm>::load4(plane + (r0 + t.x0) * 4); acc.x = fmaf(w00, v.x, acc.x); acc.y = fmaf(w00, v.y, acc.y); acc.z = fmaf(w00, v.z, acc.z); acc.w = fmaf(w00, v.w, acc.w); }
+        if (x1in) { float4 v = RLStore<Tm>::load4(plane + (r0 + t.x0 + 1) * 4); acc.x = fmaf(w10, v.x, acc.x); acc.y = fmaf(w10, v.y, acc.y); acc.z = fmaf(w10, v.z, acc.z); acc.w = fmaf(w10, v.w, acc.w); }
+    }
+    if (y1in) {
+        if (x0in) { float4 v = RLStore<Tm>::load4(plane + (r1 + t.x0) * 4); acc.x = fmaf(w01, v.x, acc.x); acc.y = fmaf(w01, v.y, acc.y); acc.z = fmaf(w01, v.z, acc.z); acc.w = fmaf(w01, v.w, acc.w); }
+        if (x1in) { float4 v = RLStore<Tm>::load4(plane + (r1 + t.x0 + 1) * 4); acc.x = fmaf(w11, v.x, acc.x); acc.y = fmaf(w11, v.y, acc.y); acc.z = fmaf(w11, v.z, acc.z); acc.w = fmaf(w11, v.w, acc.w); }
+    }
+    return acc;
+}
+
+__device__ __forceinline__ float rl_warp_sum(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}

@@ -85,7 +85,7 @@ typedef struct {
     int level;
 } rl_hsgd_params;
 
-/* Upper bounds checked on the host. */
+/* Upper bounds checked on the host (also D*H*W < 2^29 voxels). */
 #define RL_MAX_PLANES 64
 #define RL_MAX_VIEWS 16
 
@@ -151,7 +151,8 @@ rl_status reallife_select_keys(const float* keys, int D, int H, int W, int k, ui
  *   mask != NULL: compact G device [k][H][W][4] FP32, slot j of pixel p holding the
  *                 j-th kept plane of p in ascending order (mask device [H][W] uint64).
  *   loss_out: device float[1] or NULL.  G is overwritten.
- *   ws: device workspace, at least reallife_workspace_bytes(N, D, H, W, k or D, dtype). */
+ *   ws: device workspace (256-byte aligned), at least reallife_workspace_bytes(N, D, H, W,
+ *       1, dtype) bytes; RL_ENOMEM when smaller. */
 rl_status reallife_loss_grad(const rl_mpi* m, const float* images, const rl_camera* src, int N,
                              const uint64_t* mask, int k, float* G, float* loss_out, void* ws, size_t ws_bytes,
                              cudaStream_t stream);
@@ -176,6 +177,24 @@ rl_status reallife_render_backward(const rl_mpi* m, const rl_camera* views, int 
 rl_status reallife_warp_offsets(const rl_mpi* m, const rl_camera* view, float* out, cudaStream_t stream);
 
 /* ------------------------------------------------------------------ utilities */
+
+/* Kernel family for the warp kernels (render, gradient):
+ *   0 (default) automatic: plane-parallel for launches of fewer than 2^19 pixel-views,
+ *     per-pixel gather otherwise;
+ *   1 TMA-staged plane windows wherever the MPI's row pitch is a multiple of 16 bytes
+ *     (always for FP32; even W for BF16), plane-parallel elsewhere;
+ *   2 per-pixel gather (one thread per view pixel walks all planes);
+ *   3 plane-parallel (warps own chunks of planes; chunks combined through the
+ *     associativity of the over operator).
+ * All compute the same values up to FP32 rounding of the accumulation order.
+ * Process-wide; RL_EINVAL for other values. */
+rl_status reallife_set_kernel_path(int path);
+
+/* Device-side status: synchronises the device and reports the status word that kernels
+ * set when a bounded wait (about one second) gives up; *flags_out receives its bits
+ * (1 = timeout).  Returns RL_ETIMEOUT when the timeout bit is set, RL_OK otherwise;
+ * clear != 0 resets the word.  Results of launches that timed out are invalid. */
+rl_status reallife_device_status(int clear, unsigned int* flags_out);
 
 /* Host-side kernel tracing: when enabled, every kernel launch of this library is
  * bracketed by CUDA events on its stream and counted per kernel name. */

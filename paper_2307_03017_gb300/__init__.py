@@ -23,6 +23,7 @@ __all__ = [
     "reallife_downsample_f32", "reallife_select", "reallife_select_keys", "reallife_loss_grad",
     "reallife_sparse_update", "reallife_render_backward", "reallife_warp_offsets",
     "reallife_trace_enable", "reallife_trace_read", "reallife_strerror", "workspace", "library_path",
+    "reallife_set_kernel_path", "reallife_device_status",
 ]
 
 RealLifeError = _lib.RealLifeError
@@ -261,3 +262,15 @@ def reallife_trace_read() -> dict:
 
 def reallife_strerror(status: int) -> str:
     return _lib.lib().reallife_strerror(status).decode()
+
+
+def reallife_set_kernel_path(path: int):
+    """0: automatic (default); 1: TMA-staged windows; 2: per-pixel gather; 3: plane-parallel."""
+    _lib.check("reallife_set_kernel_path", _lib.lib().reallife_set_kernel_path(int(path)))
+
+
+def reallife_device_status(clear: bool = True) -> int:
+    """Synchronise the device and return the device status bits (raises on a timeout)."""
+    flags = ctypes.c_uint()
+    _lib.check("reallife_device_status", _lib.lib().reallife_device_status(int(bool(clear)), ctypes.byref(flags)))
+    return int(flags.value)

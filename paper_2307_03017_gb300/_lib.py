@@ -17,7 +17,8 @@ EXPORTS = [
     "reallife_workspace_bytes", "reallife_render", "reallife_hsgd_step", "reallife_refine",
     "reallife_downsample_f32", "reallife_select", "reallife_select_keys", "reallife_loss_grad",
     "reallife_sparse_update", "reallife_render_backward", "reallife_warp_offsets", "reallife_trace_enable",
-    "reallife_trace_read", "reallife_strerror", "reallife_last_error",
+    "reallife_trace_read", "reallife_strerror", "reallife_last_error", "reallife_set_kernel_path",
+    "reallife_device_status",
 ]
 
 
@@ -82,6 +83,8 @@ def _declare(lib):
         "reallife_trace_enable": (c_int, [c_int]),
         "reallife_trace_read": (c_int, [ctypes.POINTER(RlTraceEntry), c_int, ctypes.POINTER(c_int)]),
         "reallife_strerror": (ctypes.c_char_p, [c_int]),
+        "reallife_set_kernel_path": (c_int, [c_int]),
+        "reallife_device_status": (c_int, [c_int, ctypes.POINTER(ctypes.c_uint)]),
         "reallife_last_error": (ctypes.c_char_p, []),
     }
     for name, (res, args) in sig.items():

@@ -10,8 +10,9 @@
 //                           B_d the composite of the planes below d (B_0 = 0,
 //                           B_{d+1} = c_d alpha_d + (1 - alpha_d) B_d);
 //                           the bilinear transpose adds w_tap * dL/dm_d to the 4 taps.
-// Sparse mode adds only into voxels kept by the selection mask (Sec. 3.3), at slot
-// popcount(mask & ((1 << d) - 1)) of the compact gradient.  No division by (1 - alpha).
+// Sparse mode adds only into voxels kept by the selection (Sec. 3.3): the slot map
+// slots[d][y][x] gives the compact slot of a kept voxel (its rank among the kept planes of
+// the pixel) or RL_SLOT_NONE.  No division by (1 - alpha).
 #include "rl_internal.h"
 
 namespace {
@@ -19,38 +20,68 @@ namespace {
 constexpr int kGradBX = 32, kGradBY = 4, kGradThreads = kGradBX * kGradBY;
 
 template <bool SPARSE>
-__device__ __forceinline__ void scatter_tap(float* __restrict__ G, const uint64_t* __restrict__ mask, int d, int H,
-                                            int W, int x, int y, float wt, float4 g) {
-    if ((unsigned)x >= (unsigned)W || (unsigned)y >= (unsigned)H || wt == 0.f) return;
-    const size_t pix = (size_t)y * W + x;
-    int slot = d;
-    if (SPARSE) {
-        const uint64_t mk = __ldg(mask + pix);
-        if (!((mk >> d) & 1ull)) return;
-        slot = __popcll(mk & ((1ull << d) - 1ull));
+__device__ __forceinline__ void scatter_tap(float* __restrict__ G, const uint8_t* __restrict__ slots_d, int d,
+                                            unsigned hw, int H, int W, int x, int y, float wt, float4 g) {
+    if ((unsigned)x >= (unsigned)W || (unsigned)y >= (unsigned)H) return;
+    const unsigned pix = (unsigned)(y * W + x);
+    const unsigned slot = SPARSE ? (unsigned)__ldg(slots_d + pix) : (unsigned)d;
+    if (SPARSE && slot == RL_SLOT_NONE) return;
+    atomicAdd(reinterpret_cast<float4*>(G) + (slot * hw + pix), make_float4(wt * g.x, wt * g.y, wt * g.z, wt * g.w));
+}
+
+// Bilinear transpose of one sample's gradient g onto its four taps.
+template <bool SPARSE>
+__device__ __forceinline__ void scatter4(float* __restrict__ G, const uint8_t* __restrict__ slots_d, int d,
+                                         unsigned hw, int H, int W, const RLTaps& t, float4 g) {
+    const float w00 = (1.f - t.fx) * (1.f - t.fy), w10 = t.fx * (1.f - t.fy);
+    const float w01 = (1.f - t.fx) * t.fy, w11 = t.fx * t.fy;
+    if ((unsigned)t.x0 < (unsigned)(W - 1) && (unsigned)t.y0 < (unsigned)(H - 1)) {
+        const unsigned p = (unsigned)(t.y0 * W + t.x0);
+        unsigned s00 = d, s10 = d, s01 = d, s11 = d;
+        if (SPARSE) {
+            s00 = __ldg(slots_d + p);
+            s10 = __ldg(slots_d + p + 1);
+            s01 = __ldg(slots_d + p + W);
+            s11 = __ldg(slots_d + p + W + 1);
+        }
+        float4* G4 = reinterpret_cast<float4*>(G);
+        if (!SPARSE || s00 != RL_SLOT_NONE)
+            atomicAdd(G4 + (s00 * hw + p), make_float4(w00 * g.x, w00 * g.y, w00 * g.z, w00 * g.w));
+        if (!SPARSE || s10 != RL_SLOT_NONE)
+            atomicAdd(G4 + (s10 * hw + p + 1), make_float4(w10 * g.x, w10 * g.y, w10 * g.z, w10 * g.w));
+        if (!SPARSE || s01 != RL_SLOT_NONE)
+            atomicAdd(G4 + (s01 * hw + p + W), make_float4(w01 * g.x, w01 * g.y, w01 * g.z, w01 * g.w));
+        if (!SPARSE || s11 != RL_SLOT_NONE)
+            atomicAdd(G4 + (s11 * hw + p + W + 1), make_float4(w11 * g.x, w11 * g.y, w11 * g.z, w11 * g.w));
+        return;
     }
-    float4* dst = reinterpret_cast<float4*>(G + ((size_t)slot * H * W + pix) * 4);
-    atomicAdd(dst, make_float4(wt * g.x, wt * g.y, wt * g.z, wt * g.w));
+    scatter_tap<SPARSE>(G, slots_d, d, hw, H, W, t.x0, t.y0, w00, g);
+    scatter_tap<SPARSE>(G, slots_d, d, hw, H, W, t.x0 + 1, t.y0, w10, g);
+    scatter_tap<SPARSE>(G, slots_d, d, hw, H, W, t.x0, t.y0 + 1, w01, g);
+    scatter_tap<SPARSE>(G, slots_d, d, hw, H, W, t.x0 + 1, t.y0 + 1, w11, g);
 }
 
 template <typename Tm, bool SPARSE, bool LOSS>
 __global__ void __launch_bounds__(kGradThreads)
-k_grad(const Tm* __restrict__ M, int D, int H, int W, const __grid_constant__ RLViews views,
+k_grad(const Tm* __restrict__ M, int D, int H, int W, const __grid_constant__ RLViews views, int tiles_x,
        const float* __restrict__ images, int img_level, const float* __restrict__ grad_out,
-       const uint64_t* __restrict__ mask, float* __restrict__ G, float inv_n, float* __restrict__ partials) {
+       const uint8_t* __restrict__ slots, float* __restrict__ G, float inv_n, float* __restrict__ partials) {
     extern __shared__ float sT[];  // [D][kGradThreads]
+    // view-fastest block order: the N views of a tile run together and share M through L2
     const int tid = threadIdx.y * kGradBX + threadIdx.x;
-    const int qx = blockIdx.x * kGradBX + threadIdx.x;
-    const int qy = blockIdx.y * kGradBY + threadIdx.y;
-    const int view = blockIdx.z;
+    const int view = blockIdx.x % views.n;
+    const int tile = blockIdx.x / views.n;
+    const int qx = (tile % tiles_x) * kGradBX + threadIdx.x;
+    const int qy = (tile / tiles_x) * kGradBY + threadIdx.y;
     float lsum = 0.f;
     if (qx < W && qy < H) {
         const RLWarp w = rl_warp_coeffs(views.v[view], (float)qx, (float)qy);
         const size_t plane = (size_t)H * W * 4;
         float T = 1.f, c0 = 0.f, c1 = 0.f, c2 = 0.f;
+#pragma unroll 2
         for (int d = D - 1; d >= 0; --d) {
             const RLTaps t = rl_taps(w, views.rho[d], qx, qy);
-            const float4 m = rl_sample(M + d * plane, H, W, t);
+            const float4 m = rl_sample_fast(M + d * plane, H, W, t);
             sT[d * kGradThreads + tid] = T;
             const float a = T * m.w;
             c0 = fmaf(a, m.x, c0);
@@ -85,9 +116,11 @@ k_grad(const Tm* __restrict__ M, int D, int H, int W, const __grid_constant__ RL
             r2 = __ldg(go + 2);
         }
         float b0 = 0.f, b1 = 0.f, b2 = 0.f;
+        const unsigned hw = (unsigned)(H * W);
+#pragma unroll 2
         for (int d = 0; d < D; ++d) {
             const RLTaps t = rl_taps(w, views.rho[d], qx, qy);
-            const float4 m = rl_sample(M + d * plane, H, W, t);
+            const float4 m = rl_sample_fast(M + d * plane, H, W, t);
             const float Td = sT[d * kGradThreads + tid];
             if (t.ok && Td != 0.f) {
                 const float gc = Td * m.w;
@@ -96,12 +129,7 @@ k_grad(const Tm* __restrict__ M, int D, int H, int W, const __grid_constant__ RL
                 g.y = gc * r1;
                 g.z = gc * r2;
                 g.w = Td * fmaf(m.x - b0, r0, fmaf(m.y - b1, r1, (m.z - b2) * r2));
-                const float w00 = (1.f - t.fx) * (1.f - t.fy), w10 = t.fx * (1.f - t.fy);
-                const float w01 = (1.f - t.fx) * t.fy, w11 = t.fx * t.fy;
-                scatter_tap<SPARSE>(G, mask, d, H, W, t.x0, t.y0, w00, g);
-                scatter_tap<SPARSE>(G, mask, d, H, W, t.x0 + 1, t.y0, w10, g);
-                scatter_tap<SPARSE>(G, mask, d, H, W, t.x0, t.y0 + 1, w01, g);
-                scatter_tap<SPARSE>(G, mask, d, H, W, t.x0 + 1, t.y0 + 1, w11, g);
+                scatter4<SPARSE>(G, SPARSE ? slots + (size_t)d * hw : nullptr, d, hw, H, W, t, g);
             }
             const float om = 1.f - m.w;
             b0 = fmaf(m.x, m.w, om * b0);
@@ -117,7 +145,7 @@ k_grad(const Tm* __restrict__ M, int D, int H, int W, const __grid_constant__ RL
         if (tid == 0) {
             float s = 0.f;
             for (int j = 0; j < kGradThreads / 32; ++j) s += red[j];
-            partials[blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z)] = s;
+            partials[blockIdx.x] = s;
         }
     }
 }
@@ -140,32 +168,46 @@ __global__ void __launch_bounds__(1024) k_loss_reduce(const float* __restrict__ 
 
 template <typename Tm, bool SPARSE, bool LOSS>
 void launch_grad_t(const void* M, int D, int H, int W, const RLViews& views, const float* images, int img_level,
-                   const float* grad_out, const uint64_t* mask, float* G, float inv_n, float* partials, dim3 grid,
-                   size_t smem, cudaStream_t s) {
+                   const float* grad_out, const uint8_t* slots, float* G, float inv_n, float* partials, int tiles_x,
+                   unsigned grid, size_t smem, cudaStream_t s) {
     auto kern = k_grad<Tm, SPARSE, LOSS>;
     if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    kern<<<grid, dim3(kGradBX, kGradBY), smem, s>>>((const Tm*)M, D, H, W, views, images, img_level, grad_out, mask, G,
-                                                    inv_n, partials);
+    kern<<<grid, dim3(kGradBX, kGradBY), smem, s>>>((const Tm*)M, D, H, W, views, tiles_x, images, img_level, grad_out,
+                                                    slots, G, inv_n, partials);
 }
 
 }  // namespace
 
 size_t rl_grad_num_blocks(int H, int W, int N) {
-    return (size_t)((W + kGradBX - 1) / kGradBX) * ((H + kGradBY - 1) / kGradBY) * N;
+    const size_t own = (size_t)((W + kGradBX - 1) / kGradBX) * ((H + kGradBY - 1) / kGradBY) * N;
+    const size_t a = rl_grad_pp_num_blocks(H, W, N), b = rl_grad_tma_num_blocks(H, W, N);
+    return own > a ? (own > b ? own : b) : (a > b ? a : b);
 }
 
 rl_status rl_launch_grad(const void* M, rl_dtype dt, int D, int H, int W, const RLViews& views, bool mode_loss,
-                         const float* images, int img_level, const float* grad_out, const uint64_t* mask, float* G,
+                         const float* images, int img_level, const float* grad_out, const uint8_t* slots, float* G,
                          float inv_n, float* partials, int* nblocks, cudaStream_t s) {
-    dim3 grid((W + kGradBX - 1) / kGradBX, (H + kGradBY - 1) / kGradBY, views.n);
+    const int path = rl_kernel_path(H, W, views.n);
+    if (path == 1) {
+        CUtensorMap map;
+        if (rl_encode_mpi_tmap(&map, M, dt, D, H, W))
+            return rl_launch_grad_tma(map, M, dt, D, H, W, views, mode_loss, images, img_level, grad_out, slots, G,
+                                      inv_n, partials, nblocks, s);
+    }
+    if (path != 2)
+        return rl_launch_grad_pp(M, dt, D, H, W, views, mode_loss, images, img_level, grad_out, slots, G, inv_n,
+                                 partials, nblocks, s);
+    const int tiles_x = (W + kGradBX - 1) / kGradBX, tiles_y = (H + kGradBY - 1) / kGradBY;
+    const unsigned grid = (unsigned)(tiles_x * tiles_y * views.n);
     const size_t smem = (size_t)D * kGradThreads * sizeof(float);
-    if (nblocks) *nblocks = (int)(grid.x * grid.y * grid.z);
-    const bool sparse = mask != nullptr;
+    if (nblocks) *nblocks = (int)grid;
+    const bool sparse = slots != nullptr;
     const char* name = dt == RL_F32 ? (sparse ? "grad_sparse_f32" : "grad_dense_f32")
                                     : (sparse ? "grad_sparse_bf16" : "grad_dense_bf16");
     RLTraceScope ts(name, s);
 #define RL_GRAD_CASE(TM, SP, LS) \
-    launch_grad_t<TM, SP, LS>(M, D, H, W, views, images, img_level, grad_out, mask, G, inv_n, partials, grid, smem, s)
+    launch_grad_t<TM, SP, LS>(M, D, H, W, views, images, img_level, grad_out, slots, G, inv_n, partials, tiles_x, \
+                              grid, smem, s)
     if (dt == RL_F32) {
         if (sparse) { if (mode_loss) RL_GRAD_CASE(float, true, true); else RL_GRAD_CASE(float, true, false); }
         else        { if (mode_loss) RL_GRAD_CASE(float, false, true); else RL_GRAD_CASE(float, false, false); }

@@ -1,0 +1,354 @@
+// pp.cu -- plane-parallel warp kernels: novel-view rendering (Eq. eq_render, eq_over) and
+// the fused warp + composite + residual + exact adjoint of one HSGD iteration.
+//
+// Layout.  A block is kGroups warps over the same 32 view pixels (a 16 x 2 tile); warp g
+// owns planes [g C, g C + C), C = ceil(D / kGroups) <= 8, so a warp's loads of one plane
+// are 32 neighbouring voxels.  Each thread samples its C planes once and keeps them in
+// registers, nearest first forming its chunk's composite Cc_g = sum c_d alpha_d T_d^loc
+// and transmittance Tc_g = prod (1 - alpha_d).  The over operator is associative, so the
+// chunks combine exactly:
+//   T before chunk g (everything nearer):  Tb_g = prod_{g' > g} Tc_g'
+//   pixel colour:                          C = sum_g Tb_g Cc_g
+//   composite of everything farther:       Bb_g = f_{g-1}(... f_0(0)), f_g(x) = Cc_g + Tc_g x
+// (shared-memory exchange of the per-chunk (Cc, Tc)).  The adjoint of plane d then uses
+// T_d = Tb_g T_d^loc and the running below-composite B_d (B_{d+1} = c_d alpha_d + (1 -
+// alpha_d) B_d, starting from Bb_g) -- no division by (1 - alpha), no second gather.
+// Bilinear weights are applied with packed FP32x2 FMAs (same rounding as scalar FMAs).
+#include "rl_internal.h"
+
+namespace {
+
+constexpr int kGroups = 8;                 // warps (plane chunks) per block
+constexpr int kTX = 16, kTY = 2, kPix = 32;  // pixels per block, one per lane
+constexpr int kThreads = kGroups * kPix;
+
+__device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
+
+// Bilinear sample; interior samples use packed FMAs, border samples the checked path.
+template <typename Tm>
+__device__ __forceinline__ float4 sample_pp(const Tm* __restrict__ plane, int H, int W, const RLTaps& t) {
+    if (t.ok && (unsigned)t.x0 < (unsigned)(W - 1) && (unsigned)t.y0 < (unsigned)(H - 1)) {
+        const Tm* p = plane + (unsigned)(t.y0 * W + t.x0) * 4u;
+        const float4 v00 = RLStore<Tm>::load4(p), v10 = RLStore<Tm>::load4(p + 4);
+        const float4 v01 = RLStore<Tm>::load4(p + 4 * W), v11 = RLStore<Tm>::load4(p + 4 * W + 4);
+        const float w00 = (1.f - t.fx) * (1.f - t.fy), w10 = t.fx * (1.f - t.fy);
+        const float w01 = (1.f - t.fx) * t.fy, w11 = t.fx * t.fy;
+        float2 lo = __fmul2_rn(f2(w00, w00), f2(v00.x, v00.y));
+        float2 hi = __fmul2_rn(f2(w00, w00), f2(v00.z, v00.w));
+        lo = __ffma2_rn(f2(w10, w10), f2(v10.x, v10.y), lo);
+        hi = __ffma2_rn(f2(w10, w10), f2(v10.z, v10.w), hi);
+        lo = __ffma2_rn(f2(w01, w01), f2(v01.x, v01.y), lo);
+        hi = __ffma2_rn(f2(w01, w01), f2(v01.z, v01.w), hi);
+        lo = __ffma2_rn(f2(w11, w11), f2(v11.x, v11.y), lo);
+        hi = __ffma2_rn(f2(w11, w11), f2(v11.z, v11.w), hi);
+        return make_float4(lo.x, lo.y, hi.x, hi.y);
+    }
+    return rl_sample(plane, H, W, t);
+}
+
+template <bool SPARSE>
+__device__ __forceinline__ void scatter_tap_pp(float4* __restrict__ G4, const uint8_t* __restrict__ slots_d,
+                                               unsigned d, unsigned hw, int H, int W, int x, int y, float wt,
+                                               float4 g) {
+    if ((unsigned)x >= (unsigned)W || (unsigned)y >= (unsigned)H) return;
+    const unsigned pix = (unsigned)(y * W + x);
+    const unsigned slot = SPARSE ? (unsigned)__ldg(slots_d + pix) : d;
+    if (SPARSE && slot == RL_SLOT_NONE) return;
+    atomicAdd(G4 + (slot * hw + pix), make_float4(wt * g.x, wt * g.y, wt * g.z, wt * g.w));
+}
+
+// Bilinear transpose of one sample's gradient onto its four taps (kept voxels only).
+template <bool SPARSE>
+__device__ __forceinline__ void scatter_pp(float* __restrict__ G, const uint8_t* __restrict__ slots_d, unsigned d,
+                                           unsigned hw, int H, int W, const RLTaps& t, float4 g) {
+    const float w00 = (1.f - t.fx) * (1.f - t.fy), w10 = t.fx * (1.f - t.fy);
+    const float w01 = (1.f - t.fx) * t.fy, w11 = t.fx * t.fy;
+    float4* G4 = reinterpret_cast<float4*>(G);
+    if ((unsigned)t.x0 < (unsigned)(W - 1) && (unsigned)t.y0 < (unsigned)(H - 1)) {
+        const unsigned p = (unsigned)(t.y0 * W + t.x0);
+        unsigned s00 = d, s10 = d, s01 = d, s11 = d;
+        if (SPARSE) {
+            s00 = __ldg(slots_d + p);
+            s10 = __ldg(slots_d + p + 1);
+            s01 = __ldg(slots_d + p + W);
+            s11 = __ldg(slots_d + p + W + 1);
+        }
+        const float2 gl = f2(g.x, g.y), gh = f2(g.z, g.w);
+        if (!SPARSE || s00 != RL_SLOT_NONE) {
+            const float2 a = __fmul2_rn(f2(w00, w00), gl), b = __fmul2_rn(f2(w00, w00), gh);
+            atomicAdd(G4 + (s00 * hw + p), make_float4(a.x, a.y, b.x, b.y));
+        }
+        if (!SPARSE || s10 != RL_SLOT_NONE) {
+            const float2 a = __fmul2_rn(f2(w10, w10), gl), b = __fmul2_rn(f2(w10, w10), gh);
+            atomicAdd(G4 + (s10 * hw + p + 1), make_float4(a.x, a.y, b.x, b.y));
+        }
+        if (!SPARSE || s01 != RL_SLOT_NONE) {
+            const float2 a = __fmul2_rn(f2(w01, w01), gl), b = __fmul2_rn(f2(w01, w01), gh);
+            atomicAdd(G4 + (s01 * hw + p + W), make_float4(a.x, a.y, b.x, b.y));
+        }
+        if (!SPARSE || s11 != RL_SLOT_NONE) {
+            const float2 a = __fmul2_rn(f2(w11, w11), gl), b = __fmul2_rn(f2(w11, w11), gh);
+            atomicAdd(G4 + (s11 * hw + p + W + 1), make_float4(a.x, a.y, b.x, b.y));
+        }
+        return;
+    }
+    scatter_tap_pp<SPARSE>(G4, slots_d, d, hw, H, W, t.x0, t.y0, w00, g);
+    scatter_tap_pp<SPARSE>(G4, slots_d, d, hw, H, W, t.x0 + 1, t.y0, w10, g);
+    scatter_tap_pp<SPARSE>(G4, slots_d, d, hw, H, W, t.x0, t.y0 + 1, w01, g);
+    scatter_tap_pp<SPARSE>(G4, slots_d, d, hw, H, W, t.x0 + 1, t.y0 + 1, w11, g);
+}
+
+struct PixelCoord {
+    int qx, qy, view, g, lane;
+    bool active;
+};
+
+__device__ __forceinline__ PixelCoord pixel_coord(int nviews, int tiles_x, int H, int W) {
+    PixelCoord c;
+    c.view = blockIdx.x % nviews;
+    const int tile = blockIdx.x / nviews;
+    c.g = threadIdx.x >> 5;
+    c.lane = threadIdx.x & 31;
+    c.qx = (tile % tiles_x) * kTX + (c.lane % kTX);
+    c.qy = (tile / tiles_x) * kTY + (c.lane / kTX);
+    c.active = c.qx < W && c.qy < H;
+    return c;
+}
+
+template <typename Tm, int C>
+__global__ void __launch_bounds__(kThreads)
+k_render_pp(const Tm* __restrict__ M, int D, int H, int W, const __grid_constant__ RLViews views, int tiles_x,
+            float* __restrict__ out) {
+    __shared__ float4 xch[kGroups][kPix];  // per chunk: (Cc.rgb, Tc)
+    const PixelCoord pc = pixel_coord(views.n, tiles_x, H, W);
+    const int qx = min(pc.qx, W - 1), qy = min(pc.qy, H - 1);
+    const RLWarp w = rl_warp_coeffs(views.v[pc.view], (float)qx, (float)qy);
+    const size_t plane = (size_t)H * W * 4;
+    float Tl = 1.f, c0 = 0.f, c1 = 0.f, c2 = 0.f;
+#pragma unroll
+    for (int i = C - 1; i >= 0; --i) {
+        const int d = pc.g * C + i;
+        if (d < D) {
+            const RLTaps t = rl_taps(w, views.rho[d], qx, qy);
+            const float4 m = sample_pp(M + d * plane, H, W, t);
+            const float a = Tl * m.w;
+            c0 = fmaf(a, m.x, c0);
+            c1 = fmaf(a, m.y, c1);
+            c2 = fmaf(a, m.z, c2);
+            Tl = Tl * (1.f - m.w);
+        }
+    }
+    xch[pc.g][pc.lane] = make_float4(c0, c1, c2, Tl);
+    __syncthreads();
+    if (pc.g == 0 && pc.active) {
+        float T = 1.f, o0 = 0.f, o1 = 0.f, o2 = 0.f;
+#pragma unroll
+        for (int g = kGroups - 1; g >= 0; --g) {
+            const float4 v = xch[g][pc.lane];
+            o0 = fmaf(T, v.x, o0);
+            o1 = fmaf(T, v.y, o1);
+            o2 = fmaf(T, v.z, o2);
+            T = T * v.w;
+        }
+        float* o = out + (((size_t)pc.view * H + pc.qy) * W + pc.qx) * 3;
+        o[0] = o0;
+        o[1] = o1;
+        o[2] = o2;
+    }
+}
+
+template <typename Tm, int C, bool SPARSE, bool LOSS>
+__global__ void __launch_bounds__(kThreads)
+k_grad_pp(const Tm* __restrict__ M, int D, int H, int W, const __grid_constant__ RLViews views, int tiles_x,
+          const float* __restrict__ images, int img_level, const float* __restrict__ grad_out,
+          const uint8_t* __restrict__ slots, float* __restrict__ G, float inv_n, float* __restrict__ partials) {
+    __shared__ float4 xch[kGroups][kPix];
+    __shared__ float red[kGroups];
+    const PixelCoord pc = pixel_coord(views.n, tiles_x, H, W);
+    const int qx = min(pc.qx, W - 1), qy = min(pc.qy, H - 1);
+    const RLWarp w = rl_warp_coeffs(views.v[pc.view], (float)qx, (float)qy);
+    const size_t plane = (size_t)H * W * 4;
+
+    // forward over this thread's chunk, nearest plane first; samples stay in registers
+    float4 m[C];
+    float Tloc[C];
+    float Tl = 1.f, c0 = 0.f, c1 = 0.f, c2 = 0.f;
+#pragma unroll
+    for (int i = C - 1; i >= 0; --i) {
+        const int d = pc.g * C + i;
+        m[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+        Tloc[i] = Tl;
+        if (d < D) {
+            const RLTaps t = rl_taps(w, views.rho[d], qx, qy);
+            m[i] = sample_pp(M + d * plane, H, W, t);
+            const float a = Tl * m[i].w;
+            c0 = fmaf(a, m[i].x, c0);
+            c1 = fmaf(a, m[i].y, c1);
+            c2 = fmaf(a, m[i].z, c2);
+            Tl = Tl * (1.f - m[i].w);
+        }
+    }
+    xch[pc.g][pc.lane] = make_float4(c0, c1, c2, Tl);
+    __syncthreads();
+    // combine the chunks: pixel colour, transmittance in front of this chunk and the
+    // composite of everything behind it
+    float Tb = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f;
+    {
+        float T = 1.f;
+#pragma unroll
+        for (int g = kGroups - 1; g >= 0; --g) {
+            const float4 v = xch[g][pc.lane];
+            if (g == pc.g) Tb = T;
+            C0 = fmaf(T, v.x, C0);
+            C1 = fmaf(T, v.y, C1);
+            C2 = fmaf(T, v.z, C2);
+            T = T * v.w;
+        }
+    }
+    float b0 = 0.f, b1 = 0.f, b2 = 0.f;
+    for (int g = 0; g < pc.g; ++g) {
+        const float4 v = xch[g][pc.lane];
+        b0 = fmaf(v.w, b0, v.x);
+        b1 = fmaf(v.w, b1, v.y);
+        b2 = fmaf(v.w, b2, v.z);
+    }
+    float r0 = 0.f, r1 = 0.f, r2 = 0.f, lsum = 0.f;
+    if (pc.active) {
+        if (LOSS) {
+            const int s = 1 << img_level;
+            const int Wf = W << img_level, Hf = H << img_level;
+            const float* img = images + (size_t)pc.view * Hf * Wf * 3;
+            float i0 = 0.f, i1 = 0.f, i2 = 0.f;
+            for (int yy = 0; yy < s; ++yy)
+                for (int xx = 0; xx < s; ++xx) {
+                    const float* px = img + ((size_t)(pc.qy * s + yy) * Wf + (pc.qx * s + xx)) * 3;
+                    i0 += __ldg(px);
+                    i1 += __ldg(px + 1);
+                    i2 += __ldg(px + 2);
+                }
+            const float inv_area = 1.f / (float)(s * s);
+            const float e0 = C0 - i0 * inv_area, e1 = C1 - i1 * inv_area, e2 = C2 - i2 * inv_area;
+            if (pc.g == 0) lsum = fmaf(e0, e0, fmaf(e1, e1, e2 * e2));
+            r0 = e0 * inv_n;
+            r1 = e1 * inv_n;
+            r2 = e2 * inv_n;
+        } else {
+            const float* go = grad_out + (((size_t)pc.view * H + pc.qy) * W + pc.qx) * 3;
+            r0 = __ldg(go);
+            r1 = __ldg(go + 1);
+            r2 = __ldg(go + 2);
+        }
+        // adjoint over the chunk, farthest plane first
+        const unsigned hw = (unsigned)(H * W);
+#pragma unroll
+        for (int i = 0; i < C; ++i) {
+            const int d = pc.g * C + i;
+            if (d < D) {
+                const float Td = Tb * Tloc[i];
+                const float4 mi = m[i];
+                if (Td != 0.f) {
+                    const RLTaps t = rl_taps(w, views.rho[d], pc.qx, pc.qy);
+                    if (t.ok) {
+                        const float gc = Td * mi.w;
+                        float4 g;
+                        g.x = gc * r0;
+                        g.y = gc * r1;
+                        g.z = gc * r2;
+                        g.w = Td * fmaf(mi.x - b0, r0, fmaf(mi.y - b1, r1, (mi.z - b2) * r2));
+                        scatter_pp<SPARSE>(G, SPARSE ? slots + (size_t)d * hw : nullptr, (unsigned)d, hw, H, W, t, g);
+                    }
+                }
+                const float om = 1.f - mi.w;
+                b0 = fmaf(mi.x, mi.w, om * b0);
+                b1 = fmaf(mi.y, mi.w, om * b1);
+                b2 = fmaf(mi.z, mi.w, om * b2);
+            }
+        }
+    }
+    if (LOSS) {
+        lsum = rl_warp_sum(lsum);
+        if (pc.lane == 0) red[pc.g] = lsum;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            float s = 0.f;
+            for (int i = 0; i < kGroups; ++i) s += red[i];
+            partials[blockIdx.x] = s;
+        }
+    }
+}
+
+int chunk_for(int D) {
+    const int c = (D + kGroups - 1) / kGroups;
+    return c <= 1 ? 1 : c <= 2 ? 2 : c <= 4 ? 4 : 8;
+}
+
+template <typename Tm, bool SPARSE, bool LOSS>
+void launch_grad_pp_t(int C, const void* M, int D, int H, int W, const RLViews& views, int tiles_x, unsigned grid,
+                      const float* images, int img_level, const float* grad_out, const uint8_t* slots, float* G,
+                      float inv_n, float* partials, cudaStream_t s) {
+#define RL_PP_ARGS (const Tm*)M, D, H, W, views, tiles_x, images, img_level, grad_out, slots, G, inv_n, partials
+    switch (C) {
+        case 1: k_grad_pp<Tm, 1, SPARSE, LOSS><<<grid, kThreads, 0, s>>>(RL_PP_ARGS); break;
+        case 2: k_grad_pp<Tm, 2, SPARSE, LOSS><<<grid, kThreads, 0, s>>>(RL_PP_ARGS); break;
+        case 4: k_grad_pp<Tm, 4, SPARSE, LOSS><<<grid, kThreads, 0, s>>>(RL_PP_ARGS); break;
+        default: k_grad_pp<Tm, 8, SPARSE, LOSS><<<grid, kThreads, 0, s>>>(RL_PP_ARGS); break;
+    }
+#undef RL_PP_ARGS
+}
+
+template <typename Tm>
+void launch_render_pp_t(int C, const void* M, int D, int H, int W, const RLViews& views, int tiles_x, unsigned grid,
+                        float* out, cudaStream_t s) {
+    switch (C) {
+        case 1: k_render_pp<Tm, 1><<<grid, kThreads, 0, s>>>((const Tm*)M, D, H, W, views, tiles_x, out); break;
+        case 2: k_render_pp<Tm, 2><<<grid, kThreads, 0, s>>>((const Tm*)M, D, H, W, views, tiles_x, out); break;
+        case 4: k_render_pp<Tm, 4><<<grid, kThreads, 0, s>>>((const Tm*)M, D, H, W, views, tiles_x, out); break;
+        default: k_render_pp<Tm, 8><<<grid, kThreads, 0, s>>>((const Tm*)M, D, H, W, views, tiles_x, out); break;
+    }
+}
+
+}  // namespace
+
+size_t rl_grad_pp_num_blocks(int H, int W, int N) {
+    return (size_t)((W + kTX - 1) / kTX) * ((H + kTY - 1) / kTY) * N;
+}
+
+rl_status rl_launch_grad_pp(const void* M, rl_dtype dt, int D, int H, int W, const RLViews& views, bool mode_loss,
+                            const float* images, int img_level, const float* grad_out, const uint8_t* slots, float* G,
+                            float inv_n, float* partials, int* nblocks, cudaStream_t s) {
+    const int tiles_x = (W + kTX - 1) / kTX;
+    const unsigned grid = (unsigned)rl_grad_pp_num_blocks(H, W, views.n);
+    if (nblocks) *nblocks = (int)grid;
+    const int C = chunk_for(D);
+    const bool sparse = slots != nullptr;
+    const char* name = dt == RL_F32 ? (sparse ? "grad_sparse_f32" : "grad_dense_f32")
+                                    : (sparse ? "grad_sparse_bf16" : "grad_dense_bf16");
+    RLTraceScope ts(name, s);
+#define RL_CASE(TM, SP, LS) \
+    launch_grad_pp_t<TM, SP, LS>(C, M, D, H, W, views, tiles_x, grid, images, img_level, grad_out, slots, G, inv_n, \
+                                 partials, s)
+    if (dt == RL_F32) {
+        if (sparse) { if (mode_loss) RL_CASE(float, true, true); else RL_CASE(float, true, false); }
+        else        { if (mode_loss) RL_CASE(float, false, true); else RL_CASE(float, false, false); }
+    } else {
+        if (sparse) { if (mode_loss) RL_CASE(__nv_bfloat16, true, true); else RL_CASE(__nv_bfloat16, true, false); }
+        else        { if (mode_loss) RL_CASE(__nv_bfloat16, false, true); else RL_CASE(__nv_bfloat16, false, false); }
+    }
+#undef RL_CASE
+    return rl_check_launch("grad_pp");
+}
+
+rl_status rl_launch_render_pp(const void* M, rl_dtype dt, int D, int H, int W, const RLViews& views, float* out,
+                              cudaStream_t s) {
+    const int tiles_x = (W + kTX - 1) / kTX;
+    const unsigned grid = (unsigned)rl_grad_pp_num_blocks(H, W, views.n);
+    const int C = chunk_for(D);
+    if (dt == RL_F32) {
+        RLTraceScope ts("render_f32", s);
+        launch_render_pp_t<float>(C, M, D, H, W, views, tiles_x, grid, out, s);
+    } else {
+        RLTraceScope ts("render_bf16", s);
+        launch_render_pp_t<__nv_bfloat16>(C, M, D, H, W, views, tiles_x, grid, out, s);
+    }
+    return rl_check_launch("render_pp");
+}

@@ -208,7 +208,8 @@ rl_status check_mpi(const rl_mpi* m) {
     if (!m) return rl_fail(RL_EINVAL, "mpi is NULL");
     if (m->D < 1 || m->D > RL_MAX_PLANES) return rl_fail(RL_EINVAL, "D=%d outside [1,%d]", m->D, RL_MAX_PLANES);
     if (m->H < 1 || m->W < 1) return rl_fail(RL_EINVAL, "H=%d W=%d must be positive", m->H, m->W);
-    if ((long long)m->H * m->W > (1ll << 30)) return rl_fail(RL_EINVAL, "H*W too large");
+    if ((long long)m->D * m->H * m->W >= (1ll << 29))
+        return rl_fail(RL_EINVAL, "D*H*W = %lld voxels exceeds the 2^29 limit", (long long)m->D * m->H * m->W);
     if (m->dtype != RL_F32 && m->dtype != RL_BF16) return rl_fail(RL_EINVAL, "unknown dtype %d", (int)m->dtype);
     if (!m->data) return rl_fail(RL_EINVAL, "mpi data is NULL");
     if (((uintptr_t)m->data & 15) != 0) return rl_fail(RL_EINVAL, "mpi data must be 16-byte aligned");
@@ -237,7 +238,7 @@ size_t elt_size(rl_dtype dt) { return dt == RL_F32 ? 4 : 2; }
 size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct WsLayout {
-    size_t Ml, S, mask, G, partials, total;
+    size_t Ml, S, slots, G, partials, total;
 };
 
 // One workspace serves every level of a schedule: level 0 has the largest selection and
@@ -249,8 +250,8 @@ WsLayout ws_layout(int N, int D, int H, int W, int k, rl_dtype dt) {
     if (H % 2 == 0 && W % 2 == 0) off += align_up((size_t)D * (H / 2) * (W / 2) * 4 * elt_size(dt));
     L.S = off;
     off += align_up((size_t)k * H * W);
-    L.mask = off;
-    off += align_up((size_t)H * W * 8);
+    L.slots = off;
+    off += align_up((size_t)D * H * W);
     L.G = off;
     off += align_up((size_t)k * H * W * 16);
     L.partials = off;
@@ -288,16 +289,20 @@ rl_status enqueue_hsgd(rl_mpi* m, const float* images, const rl_camera* src, int
     const int h = m->H >> level, w = m->W >> level;
     void* Ml = level == 0 ? m->data : (void*)(base + L.Ml);
     uint8_t* S = S_out ? S_out : (uint8_t*)(base + L.S);
-    uint64_t* mask = (uint64_t*)(base + L.mask);
+    uint8_t* slots = (uint8_t*)(base + L.slots);
     float* G = (float*)(base + L.G);
     float* partials = (float*)(base + L.partials);
     RLViews views;
     rl_status st = make_views(m, src, N, level, views);
     if (st) return st;
-    st = rl_launch_select(m->data, m->dtype, nullptr, m->D, m->H, m->W, level, level ? Ml : nullptr, k, S, mask, G, s);
+    if (level) {
+        st = rl_launch_pyramid(m->data, m->dtype, m->D, m->H, m->W, level, Ml, s);
+        if (st) return st;
+    }
+    st = rl_launch_select(Ml, m->dtype, nullptr, m->D, h, w, k, S, nullptr, slots, G, s);
     if (st) return st;
     int nb = 0;
-    st = rl_launch_grad(Ml, m->dtype, m->D, h, w, views, true, images, level, nullptr, mask, G, 1.0f / (float)N,
+    st = rl_launch_grad(Ml, m->dtype, m->D, h, w, views, true, images, level, nullptr, slots, G, 1.0f / (float)N,
                         partials, &nb, s);
     if (st) return st;
     if (loss_out) {
@@ -384,14 +389,14 @@ extern "C" rl_status reallife_select(const rl_mpi* m, int k, uint8_t* S, uint64_
     if (st) return st;
     if (k < 1 || k > m->D) return rl_fail(RL_EINVAL, "k=%d outside [1, D=%d]", k, m->D);
     if (!S && !mask) return rl_fail(RL_EINVAL, "select: no output");
-    return rl_launch_select(m->data, m->dtype, nullptr, m->D, m->H, m->W, 0, nullptr, k, S, mask, nullptr, stream);
+    return rl_launch_select(m->data, m->dtype, nullptr, m->D, m->H, m->W, k, S, mask, nullptr, nullptr, stream);
 }
 
 extern "C" rl_status reallife_select_keys(const float* keys, int D, int H, int W, int k, uint8_t* S, uint64_t* mask,
                                           cudaStream_t stream) {
     if (!keys || D < 1 || D > RL_MAX_PLANES || H < 1 || W < 1 || k < 1 || k > D || (!S && !mask))
         return rl_fail(RL_EINVAL, "select_keys: bad arguments");
-    return rl_launch_select(nullptr, RL_F32, keys, D, H, W, 0, nullptr, k, S, mask, nullptr, stream);
+    return rl_launch_select(nullptr, RL_F32, keys, D, H, W, k, S, mask, nullptr, nullptr, stream);
 }
 
 extern "C" rl_status reallife_loss_grad(const rl_mpi* m, const float* images, const rl_camera* src, int N,
@@ -406,13 +411,20 @@ extern "C" rl_status reallife_loss_grad(const rl_mpi* m, const float* images, co
     RLViews views;
     st = make_views(m, src, N, 0, views);
     if (st) return st;
-    const size_t need = align_up(rl_grad_num_blocks(m->H, m->W, N) * sizeof(float));
+    const size_t part = align_up(rl_grad_num_blocks(m->H, m->W, N) * sizeof(float));
+    const size_t need = part + (mask ? align_up((size_t)m->D * m->H * m->W) : 0);
     if (ws_bytes < need) return rl_fail(RL_ENOMEM, "workspace %zu bytes < %zu needed", ws_bytes, need);
-    const int slots = mask ? k : m->D;
-    st = launch_zero(G, (size_t)slots * m->H * m->W * 4, stream);
+    if (((uintptr_t)ws & 255) != 0) return rl_fail(RL_EINVAL, "workspace must be 256-byte aligned");
+    uint8_t* slots = mask ? (uint8_t*)ws + part : nullptr;
+    const int nslots = mask ? k : m->D;
+    st = launch_zero(G, (size_t)nslots * m->H * m->W * 4, stream);
     if (st) return st;
+    if (mask) {
+        st = rl_launch_mask_to_slots(mask, m->D, m->H * m->W, slots, stream);
+        if (st) return st;
+    }
     int nb = 0;
-    st = rl_launch_grad(m->data, m->dtype, m->D, m->H, m->W, views, true, images, 0, nullptr, mask, G,
+    st = rl_launch_grad(m->data, m->dtype, m->D, m->H, m->W, views, true, images, 0, nullptr, slots, G,
                         1.0f / (float)N, (float*)ws, &nb, stream);
     if (st) return st;
     if (loss_out) return rl_launch_loss_reduce((float*)ws, nb, 0.5f / (float)N, loss_out, stream);

@@ -10,19 +10,24 @@ namespace {
 
 constexpr int kRenderBX = 32, kRenderBY = 4;
 
+// Blocks are ordered view-fastest (block = tile * n_views + view) so that the views of a
+// tile, whose plane footprints overlap, run together and share the MPI through L2.
 template <typename Tm>
 __global__ void __launch_bounds__(kRenderBX* kRenderBY)
-k_render(const Tm* __restrict__ M, int D, int H, int W, const __grid_constant__ RLViews views, float* __restrict__ out) {
-    const int qx = blockIdx.x * kRenderBX + threadIdx.x;
-    const int qy = blockIdx.y * kRenderBY + threadIdx.y;
-    const int view = blockIdx.z;
+k_render(const Tm* __restrict__ M, int D, int H, int W, const __grid_constant__ RLViews views, int tiles_x,
+         float* __restrict__ out) {
+    const int view = blockIdx.x % views.n;
+    const int tile = blockIdx.x / views.n;
+    const int qx = (tile % tiles_x) * kRenderBX + threadIdx.x;
+    const int qy = (tile / tiles_x) * kRenderBY + threadIdx.y;
     if (qx >= W || qy >= H) return;
     const RLWarp w = rl_warp_coeffs(views.v[view], (float)qx, (float)qy);
     const size_t plane = (size_t)H * W * 4;
     float T = 1.f, c0 = 0.f, c1 = 0.f, c2 = 0.f;
+#pragma unroll 2
     for (int d = D - 1; d >= 0; --d) {
         const RLTaps t = rl_taps(w, views.rho[d], qx, qy);
-        const float4 m = rl_sample(M + d * plane, H, W, t);
+        const float4 m = rl_sample_fast(M + d * plane, H, W, t);
         const float a = T * m.w;
         c0 = fmaf(a, m.x, c0);
         c1 = fmaf(a, m.y, c1);
@@ -54,14 +59,21 @@ __global__ void k_warp_offsets(int D, int H, int W, const __grid_constant__ RLVi
 
 rl_status rl_launch_render(const void* M, rl_dtype dt, int D, int H, int W, const RLViews& views, float* out,
                            cudaStream_t s) {
+    const int path = rl_kernel_path(H, W, views.n);
+    if (path == 1) {
+        CUtensorMap map;
+        if (rl_encode_mpi_tmap(&map, M, dt, D, H, W)) return rl_launch_render_tma(map, M, dt, D, H, W, views, out, s);
+    }
+    if (path != 2) return rl_launch_render_pp(M, dt, D, H, W, views, out, s);
     dim3 block(kRenderBX, kRenderBY);
-    dim3 grid((W + kRenderBX - 1) / kRenderBX, (H + kRenderBY - 1) / kRenderBY, views.n);
+    const int tiles_x = (W + kRenderBX - 1) / kRenderBX, tiles_y = (H + kRenderBY - 1) / kRenderBY;
+    const unsigned grid = (unsigned)(tiles_x * tiles_y * views.n);
     if (dt == RL_F32) {
         RLTraceScope ts("render_f32", s);
-        k_render<float><<<grid, block, 0, s>>>((const float*)M, D, H, W, views, out);
+        k_render<float><<<grid, block, 0, s>>>((const float*)M, D, H, W, views, tiles_x, out);
     } else {
         RLTraceScope ts("render_bf16", s);
-        k_render<__nv_bfloat16><<<grid, block, 0, s>>>((const __nv_bfloat16*)M, D, H, W, views, out);
+        k_render<__nv_bfloat16><<<grid, block, 0, s>>>((const __nv_bfloat16*)M, D, H, W, views, tiles_x, out);
     }
     return rl_check_launch("render");
 }

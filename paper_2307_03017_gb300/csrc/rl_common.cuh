@@ -144,6 +144,29 @@ __device__ __forceinline__ float4 rl_sample(const Tm* __restrict__ plane, int H,
     return acc;
 }
 
+// Same sample as rl_sample; when all four taps are inside the plane (the common case) it
+// skips the per-tap checks and addresses the taps with 32-bit offsets (D*H*W*4 < 2^31).
+template <typename Tm>
+__device__ __forceinline__ float4 rl_sample_fast(const Tm* __restrict__ plane, int H, int W, const RLTaps& t) {
+    if (t.ok && (unsigned)t.x0 < (unsigned)(W - 1) && (unsigned)t.y0 < (unsigned)(H - 1)) {
+        const Tm* p = plane + (unsigned)(t.y0 * W + t.x0) * 4u;
+        const float4 v00 = RLStore<Tm>::load4(p), v10 = RLStore<Tm>::load4(p + 4);
+        const float4 v01 = RLStore<Tm>::load4(p + 4 * W), v11 = RLStore<Tm>::load4(p + 4 * W + 4);
+        const float w00 = (1.f - t.fx) * (1.f - t.fy), w10 = t.fx * (1.f - t.fy);
+        const float w01 = (1.f - t.fx) * t.fy, w11 = t.fx * t.fy;
+        float4 a;
+        a.x = fmaf(w11, v11.x, fmaf(w01, v01.x, fmaf(w10, v10.x, w00 * v00.x)));
+        a.y = fmaf(w11, v11.y, fmaf(w01, v01.y, fmaf(w10, v10.y, w00 * v00.y)));
+        a.z = fmaf(w11, v11.z, fmaf(w01, v01.z, fmaf(w10, v10.z, w00 * v00.z)));
+        a.w = fmaf(w11, v11.w, fmaf(w01, v01.w, fmaf(w10, v10.w, w00 * v00.w)));
+        return a;
+    }
+    return rl_sample(plane, H, W, t);
+}
+
+// Slot-map value of a voxel that the selection did not keep.
+#define RL_SLOT_NONE 0xFF
+
 __device__ __forceinline__ float rl_warp_sum(float v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);

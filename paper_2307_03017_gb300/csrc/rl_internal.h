@@ -1,5 +1,6 @@
 // rl_internal.h -- host-side declarations shared by the translation units of libreallife.
 #pragma once
+#include <cuda.h>
 #include <cuda_runtime_api.h>
 #include <stddef.h>
 #include <stdint.h>
@@ -23,27 +24,60 @@ struct RLTraceScope {
     ~RLTraceScope() { rl_trace_end(tok, s); }
 };
 
+// Device status word (bit RL_DEVFLAG_TIMEOUT: a bounded wait gave up); address on the
+// current device, or NULL if it cannot be resolved.
+unsigned int* rl_device_status_ptr();
+// Warp-kernel family for a launch over H x W pixels of n views: 1 TMA-staged windows
+// where the layout allows (plane-parallel otherwise), 2 per-pixel gather, 3 plane-parallel.
+// The automatic setting picks plane-parallel for launches of fewer than 2^19 pixel-views
+// (coarse pyramid levels, small requests), where per-pixel threads are too few to hide
+// gather latency, and per-pixel gather otherwise.
+int rl_kernel_path(int H, int W, int nviews);
+// TMA descriptor of an MPI [D][H][W][4] with the staging window box; false when the
+// layout cannot be described (row pitch not a multiple of 16 bytes, misaligned base).
+bool rl_encode_mpi_tmap(CUtensorMap* map, const void* M, rl_dtype dt, int D, int H, int W);
+
 // ----------------------------------------------------------------- launchers
 // All take device pointers and enqueue on `s`; arguments are validated by the caller.
 
 rl_status rl_launch_render(const void* M, rl_dtype dt, int D, int H, int W, const RLViews& views, float* out,
                            cudaStream_t s);
+rl_status rl_launch_render_tma(const CUtensorMap& tmap, const void* M, rl_dtype dt, int D, int H, int W,
+                               const RLViews& views, float* out, cudaStream_t s);
 rl_status rl_launch_warp_offsets(int D, int H, int W, const RLViews& views, float* out, cudaStream_t s);
 
 // Fused warp + composite + residual + adjoint.  mode_loss: residual from images (full-res
-// images at level img_level, averaged on the fly) else from grad_out.  mask != NULL:
-// compact gradient [k][H][W][4]; else dense [D][H][W][4].  partials: one float per block
+// images at level img_level, averaged on the fly) else from grad_out.  slots != NULL
+// (slot map [D][H][W], RL_SLOT_NONE where not kept): compact gradient [k][H][W][4]; else
+// dense [D][H][W][4].  partials: one float per block
 // (loss mode); returns the number of blocks through *nblocks.
 rl_status rl_launch_grad(const void* M, rl_dtype dt, int D, int H, int W, const RLViews& views, bool mode_loss,
-                         const float* images, int img_level, const float* grad_out, const uint64_t* mask, float* G,
+                         const float* images, int img_level, const float* grad_out, const uint8_t* slots, float* G,
                          float inv_n, float* partials, int* nblocks, cudaStream_t s);
+// Largest number of loss partials any gradient kernel family writes.
 size_t rl_grad_num_blocks(int H, int W, int N);
+rl_status rl_launch_grad_tma(const CUtensorMap& tmap, const void* M, rl_dtype dt, int D, int H, int W,
+                             const RLViews& views, bool mode_loss, const float* images, int img_level,
+                             const float* grad_out, const uint8_t* slots, float* G, float inv_n, float* partials,
+                             int* nblocks, cudaStream_t s);
+size_t rl_grad_tma_num_blocks(int H, int W, int N);
+rl_status rl_launch_grad_pp(const void* M, rl_dtype dt, int D, int H, int W, const RLViews& views, bool mode_loss,
+                            const float* images, int img_level, const float* grad_out, const uint8_t* slots, float* G,
+                            float inv_n, float* partials, int* nblocks, cudaStream_t s);
+size_t rl_grad_pp_num_blocks(int H, int W, int N);
+rl_status rl_launch_render_pp(const void* M, rl_dtype dt, int D, int H, int W, const RLViews& views, float* out,
+                              cudaStream_t s);
 rl_status rl_launch_loss_reduce(const float* partials, int n, float scale, float* out, cudaStream_t s);
 
-// Level-l downsample of the full MPI (optional output Ml) fused with top-k selection.
-// keys != NULL selects from keys [D][H][W] instead (M, level, Ml ignored).
-rl_status rl_launch_select(const void* M, rl_dtype dt, const float* keys, int D, int Hf, int Wf, int level,
-                           void* Ml, int k, uint8_t* S, uint64_t* mask, float* Gzero, cudaStream_t s);
+// Top-k selection on the MPI M [D][h][w][4] (or on keys [D][h][w] when keys != NULL).
+// Outputs (each optional): S [k][h][w], mask [h][w], slot map [D][h][w]; Gzero
+// [k][h][w][4] is zeroed.
+rl_status rl_launch_select(const void* M, rl_dtype dt, const float* keys, int D, int h, int w, int k, uint8_t* S,
+                           uint64_t* mask, uint8_t* slots, float* Gzero, cudaStream_t s);
+// Level-l MPI Ml [D][H>>l][W>>l][4] = Down^l(M).
+rl_status rl_launch_pyramid(const void* M, rl_dtype dt, int D, int H, int W, int level, void* Ml, cudaStream_t s);
+// Slot map [D][h][w] from a selection mask [h][w].
+rl_status rl_launch_mask_to_slots(const uint64_t* mask, int D, int hw, uint8_t* slots, cudaStream_t s);
 rl_status rl_launch_downsample_f32(const float* x, int P, int H, int W, int C, int level, float* y,
                                    cudaStream_t s);
 rl_status rl_launch_update(void* M, rl_dtype dt, int D, int H, int W, int level, const uint8_t* S, const float* G,

@@ -1,13 +1,16 @@
-// select.cu -- level pyramid of the MPI fused with the content-aligned top-k selection
-// (Sec. 3.3 "Gradient Sparsification"), image/tensor box downsampling.
+// select.cu -- level pyramid of the MPI, the content-aligned top-k selection (Sec. 3.3
+// "Gradient Sparsification") and image/tensor box downsampling.
 //
-// One thread per level-l pixel.  Walking the planes nearest first, it forms the level-l
-// voxel (mean of the 2^l x 2^l full-resolution voxels, stored to the level MPI), the
+// Pyramid: one thread per level-l voxel, the mean of its 2^l x 2^l full-resolution voxels
+// (Sec. 3.2, hierarchical downsampling), rounded to the storage type.
+//
+// Selection: one thread per pixel.  Walking the planes nearest first, it forms the
 // reference-view alpha weight A_d = alpha_d T_d (Eq. eq_gradient / eq_overA) with
 // T_d = prod_{j>d}(1 - alpha_j), and keeps the k largest keys under the order
 // (key descending, d ascending).  The kept planes become a 64-bit mask and the compact
-// index list S[j][p] in ascending depth order; the compact gradient slots of the pixel
-// are zeroed for the adjoint that follows.
+// index list S[j][p] in ascending depth order, and the slot map used by the adjoint
+// (slot j of plane S[j][p], RL_SLOT_NONE for the planes not kept); the compact gradient
+// slots of the pixel are zeroed for the adjoint that follows.
 //   k <= 8: a register-resident sorted list, one compare-exchange pass per plane.
 //   k  > 8: rank counting over the D keys (O(D^2) per pixel, kept in local memory).
 #include "rl_internal.h"
@@ -18,16 +21,12 @@ __device__ __forceinline__ bool beats(float a, int ia, float b, int ib) { return
 
 template <typename Tm, bool FROM_KEYS, int KMAX>
 __global__ void __launch_bounds__(128)
-k_select(const Tm* __restrict__ M, const float* __restrict__ keys, int D, int Hf, int Wf, int level,
-         Tm* __restrict__ Ml, int k, uint8_t* __restrict__ S, uint64_t* __restrict__ mask_out,
+k_select(const Tm* __restrict__ M, const float* __restrict__ keys, int D, int h, int w, int k,
+         uint8_t* __restrict__ S, uint64_t* __restrict__ mask_out, uint8_t* __restrict__ slots,
          float* __restrict__ Gzero) {
-    const int h = Hf >> level, w = Wf >> level;
     const long long hw = (long long)h * w;
     const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= hw) return;
-    const int py = (int)(p / w), px = (int)(p - (long long)py * w);
-    const int s = 1 << level;
-    const float inv_area = 1.f / (float)(s * s);
 
     constexpr bool SMALL = KMAX <= 8;
     float kv[SMALL ? KMAX : 1];
@@ -37,45 +36,45 @@ k_select(const Tm* __restrict__ M, const float* __restrict__ keys, int D, int Hf
 #pragma unroll
         for (int j = 0; j < KMAX; ++j) { kv[j] = -INFINITY; ki[j] = 255; }
     }
+    // keys are formed nearest plane first; the loads of 16 planes are issued together
+    constexpr int kBatch = 16;
     float T = 1.f;
-    for (int d = D - 1; d >= 0; --d) {
-        float key;
-        if constexpr (FROM_KEYS) {
-            key = __ldg(keys + (size_t)d * hw + p);
-        } else {
-            float alpha;
-            if (level == 0) {
-                alpha = RLStore<Tm>::load1(M + ((size_t)d * hw + p) * 4 + 3);
-            } else {
-                float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-                const Tm* base = M + ((size_t)d * Hf + (size_t)py * s) * Wf * 4;
-                for (int yy = 0; yy < s; ++yy)
-                    for (int xx = 0; xx < s; ++xx) {
-                        const float4 v = RLStore<Tm>::load4(base + ((size_t)yy * Wf + (size_t)px * s + xx) * 4);
-                        acc.x += v.x; acc.y += v.y; acc.z += v.z; acc.w += v.w;
-                    }
-                acc.x *= inv_area; acc.y *= inv_area; acc.z *= inv_area; acc.w *= inv_area;
-                Tm* dst = Ml + ((size_t)d * hw + p) * 4;
-                RLStore<Tm>::store4(dst, acc);
-                alpha = RLStore<Tm>::round1(acc.w);  // the stored value, which the adjoint will see
-            }
-            key = alpha * T;
-            T = T * (1.f - alpha);
-        }
-        if (!(key == key)) key = -INFINITY;  // NaN keys rank last
-        if constexpr (SMALL) {
-            float cv = key;
-            int ci = d;
+    for (int d0 = D - 1; d0 >= 0; d0 -= kBatch) {
+        float raw[kBatch];
 #pragma unroll
-            for (int j = 0; j < KMAX; ++j) {
-                if (j < k && beats(cv, ci, kv[j], ki[j])) {
-                    const float tv = kv[j]; const int ti = ki[j];
-                    kv[j] = cv; ki[j] = ci;
-                    cv = tv; ci = ti;
-                }
+        for (int u = 0; u < kBatch; ++u) {
+            const int d = d0 - u;
+            if constexpr (FROM_KEYS)
+                raw[u] = d >= 0 ? __ldg(keys + (size_t)d * hw + p) : 0.f;
+            else
+                raw[u] = d >= 0 ? RLStore<Tm>::load1(M + ((size_t)d * hw + p) * 4 + 3) : 0.f;
+        }
+#pragma unroll
+        for (int u = 0; u < kBatch; ++u) {
+            const int d = d0 - u;
+            if (d < 0) break;
+            float key;
+            if constexpr (FROM_KEYS) {
+                key = raw[u];
+            } else {
+                key = raw[u] * T;
+                T = T * (1.f - raw[u]);
             }
-        } else {
-            allk[d] = key;
+            if (!(key == key)) key = -INFINITY;  // NaN keys rank last
+            if constexpr (SMALL) {
+                float cv = key;
+                int ci = d;
+#pragma unroll
+                for (int j = 0; j < KMAX; ++j) {
+                    if (j < k && beats(cv, ci, kv[j], ki[j])) {
+                        const float tv = kv[j]; const int ti = ki[j];
+                        kv[j] = cv; ki[j] = ci;
+                        cv = tv; ci = ti;
+                    }
+                }
+            } else {
+                allk[d] = key;
+            }
         }
     }
     uint64_t mk = 0;
@@ -91,6 +90,14 @@ k_select(const Tm* __restrict__ M, const float* __restrict__ keys, int D, int Hf
         }
     }
     if (mask_out) mask_out[p] = mk;
+    if (slots) {
+        int j = 0;
+        for (int d = 0; d < D; ++d) {
+            const bool kept = (mk >> d) & 1ull;
+            slots[(size_t)d * hw + p] = kept ? (uint8_t)j : (uint8_t)RL_SLOT_NONE;
+            j += kept;
+        }
+    }
     uint64_t rem = mk;
     for (int j = 0; j < k; ++j) {
         const int d = __ffsll((long long)rem) - 1;
@@ -101,14 +108,50 @@ k_select(const Tm* __restrict__ M, const float* __restrict__ keys, int D, int Hf
 }
 
 template <typename Tm, bool FROM_KEYS>
-void launch_select_t(const void* M, const float* keys, int D, int Hf, int Wf, int level, void* Ml, int k,
-                     uint8_t* S, uint64_t* mask, float* Gzero, cudaStream_t s) {
-    const long long hw = (long long)(Hf >> level) * (Wf >> level);
+void launch_select_t(const void* M, const float* keys, int D, int h, int w, int k, uint8_t* S, uint64_t* mask,
+                     uint8_t* slots, float* Gzero, cudaStream_t s) {
+    const long long hw = (long long)h * w;
     const int blocks = (int)((hw + 127) / 128);
     if (k <= 8)
-        k_select<Tm, FROM_KEYS, 8><<<blocks, 128, 0, s>>>((const Tm*)M, keys, D, Hf, Wf, level, (Tm*)Ml, k, S, mask, Gzero);
+        k_select<Tm, FROM_KEYS, 8><<<blocks, 128, 0, s>>>((const Tm*)M, keys, D, h, w, k, S, mask, slots, Gzero);
     else
-        k_select<Tm, FROM_KEYS, 64><<<blocks, 128, 0, s>>>((const Tm*)M, keys, D, Hf, Wf, level, (Tm*)Ml, k, S, mask, Gzero);
+        k_select<Tm, FROM_KEYS, 64><<<blocks, 128, 0, s>>>((const Tm*)M, keys, D, h, w, k, S, mask, slots, Gzero);
+}
+
+template <typename Tm>
+__global__ void __launch_bounds__(256)
+k_pyramid(const Tm* __restrict__ M, int D, int H, int W, int level, Tm* __restrict__ Ml) {
+    const int h = H >> level, w = W >> level, s = 1 << level;
+    const long long n = (long long)D * h * w;
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int x = (int)(i % w);
+    const long long r = i / w;
+    const int y = (int)(r % h);
+    const int d = (int)(r / h);
+    const Tm* base = M + (((size_t)d * H + (size_t)y * s) * W + (size_t)x * s) * 4;
+    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int yy = 0; yy < s; ++yy)
+#pragma unroll 4
+        for (int xx = 0; xx < s; ++xx) {
+            const float4 v = RLStore<Tm>::load4(base + ((size_t)yy * W + xx) * 4);
+            acc.x += v.x; acc.y += v.y; acc.z += v.z; acc.w += v.w;
+        }
+    const float inv = 1.f / (float)(s * s);
+    acc.x *= inv; acc.y *= inv; acc.z *= inv; acc.w *= inv;
+    RLStore<Tm>::store4(Ml + (size_t)i * 4, acc);
+}
+
+__global__ void k_mask_to_slots(const uint64_t* __restrict__ mask, int D, int hw, uint8_t* __restrict__ slots) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= hw) return;
+    const uint64_t mk = mask[p];
+    int j = 0;
+    for (int d = 0; d < D; ++d) {
+        const bool kept = (mk >> d) & 1ull;
+        slots[(size_t)d * hw + p] = kept ? (uint8_t)j : (uint8_t)RL_SLOT_NONE;
+        j += kept;
+    }
 }
 
 __global__ void k_downsample_f32(const float* __restrict__ x, int P, int H, int W, int C, int level,
@@ -131,19 +174,39 @@ __global__ void k_downsample_f32(const float* __restrict__ x, int P, int H, int 
 
 }  // namespace
 
-rl_status rl_launch_select(const void* M, rl_dtype dt, const float* keys, int D, int Hf, int Wf, int level, void* Ml,
-                           int k, uint8_t* S, uint64_t* mask, float* Gzero, cudaStream_t s) {
+rl_status rl_launch_select(const void* M, rl_dtype dt, const float* keys, int D, int h, int w, int k, uint8_t* S,
+                           uint64_t* mask, uint8_t* slots, float* Gzero, cudaStream_t s) {
     if (keys) {
         RLTraceScope ts("select_keys", s);
-        launch_select_t<float, true>(nullptr, keys, D, Hf, Wf, 0, nullptr, k, S, mask, Gzero, s);
+        launch_select_t<float, true>(nullptr, keys, D, h, w, k, S, mask, slots, Gzero, s);
     } else if (dt == RL_F32) {
-        RLTraceScope ts(level ? "pyramid_select_f32" : "select_f32", s);
-        launch_select_t<float, false>(M, nullptr, D, Hf, Wf, level, Ml, k, S, mask, Gzero, s);
+        RLTraceScope ts("select_f32", s);
+        launch_select_t<float, false>(M, nullptr, D, h, w, k, S, mask, slots, Gzero, s);
     } else {
-        RLTraceScope ts(level ? "pyramid_select_bf16" : "select_bf16", s);
-        launch_select_t<__nv_bfloat16, false>(M, nullptr, D, Hf, Wf, level, Ml, k, S, mask, Gzero, s);
+        RLTraceScope ts("select_bf16", s);
+        launch_select_t<__nv_bfloat16, false>(M, nullptr, D, h, w, k, S, mask, slots, Gzero, s);
     }
     return rl_check_launch("select");
+}
+
+rl_status rl_launch_pyramid(const void* M, rl_dtype dt, int D, int H, int W, int level, void* Ml, cudaStream_t s) {
+    const long long n = (long long)D * (H >> level) * (W >> level);
+    const unsigned blocks = (unsigned)((n + 255) / 256);
+    if (dt == RL_F32) {
+        RLTraceScope ts("pyramid_f32", s);
+        k_pyramid<float><<<blocks, 256, 0, s>>>((const float*)M, D, H, W, level, (float*)Ml);
+    } else {
+        RLTraceScope ts("pyramid_bf16", s);
+        k_pyramid<__nv_bfloat16><<<blocks, 256, 0, s>>>((const __nv_bfloat16*)M, D, H, W, level,
+                                                        (__nv_bfloat16*)Ml);
+    }
+    return rl_check_launch("pyramid");
+}
+
+rl_status rl_launch_mask_to_slots(const uint64_t* mask, int D, int hw, uint8_t* slots, cudaStream_t s) {
+    RLTraceScope ts("mask_to_slots", s);
+    k_mask_to_slots<<<(hw + 255) / 256, 256, 0, s>>>(mask, D, hw, slots);
+    return rl_check_launch("mask_to_slots");
 }
 
 rl_status rl_launch_downsample_f32(const float* x, int P, int H, int W, int C, int level, float* y, cudaStream_t s) {

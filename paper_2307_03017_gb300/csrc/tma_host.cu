@@ -1,0 +1,90 @@
+// tma_host.cu -- host-side TMA descriptors, the device status word and the kernel-path
+// switch.
+#include <atomic>
+#include <mutex>
+
+#include <cudaTypedefs.h>
+
+#include "rl_internal.h"
+#include "rl_tma.cuh"
+
+// Set by kernels (atomicOr) when a bounded wait gives up; read by reallife_device_status.
+__device__ unsigned int g_rl_status_word;
+
+namespace {
+std::atomic<int> g_path{0};
+PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+std::once_flag g_encode_once;
+std::mutex g_status_mu;
+unsigned int* g_status_ptr[256] = {};
+
+PFN_cuTensorMapEncodeTiled_v12000 encoder() {
+    std::call_once(g_encode_once, [] {
+        void* fn = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+        else
+            cudaGetLastError();
+    });
+    return g_encode;
+}
+}  // namespace
+
+int rl_kernel_path(int H, int W, int nviews) {
+    const int p = g_path.load(std::memory_order_relaxed);
+    if (p != 0) return p;
+    return (long long)H * W * nviews < (1ll << 19) ? 3 : 2;
+}
+
+unsigned int* rl_device_status_ptr() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256) return nullptr;
+    std::lock_guard<std::mutex> lk(g_status_mu);
+    if (!g_status_ptr[dev]) {
+        void* p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_rl_status_word) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        g_status_ptr[dev] = static_cast<unsigned int*>(p);
+    }
+    return g_status_ptr[dev];
+}
+
+bool rl_encode_mpi_tmap(CUtensorMap* map, const void* M, rl_dtype dt, int D, int H, int W) {
+    const size_t elt = dt == RL_F32 ? 4 : 2;
+    if (((uintptr_t)M & 15) != 0 || ((size_t)W * 4 * elt) % 16 != 0) return false;
+    PFN_cuTensorMapEncodeTiled_v12000 fn = encoder();
+    if (!fn) return false;
+    const cuuint64_t dims[3] = {(cuuint64_t)W * 4, (cuuint64_t)H, (cuuint64_t)D};
+    const cuuint64_t strides[2] = {(cuuint64_t)W * 4 * elt, (cuuint64_t)W * 4 * elt * H};
+    const cuuint32_t box[3] = {(cuuint32_t)rltma::BW * 4, (cuuint32_t)rltma::BH, 1};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    const CUresult r = fn(map, dt == RL_F32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3,
+                          const_cast<void*>(M), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                          CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
+extern "C" rl_status reallife_set_kernel_path(int path) {
+    if (path < 0 || path > 3) return rl_fail(RL_EINVAL, "kernel path must be 0, 1, 2 or 3");
+    g_path.store(path);
+    return RL_OK;
+}
+
+extern "C" rl_status reallife_device_status(int clear, unsigned int* flags_out) {
+    unsigned int* p = rl_device_status_ptr();
+    if (!p) return rl_fail(RL_ECUDA, "device status word unavailable");
+    cudaError_t e = cudaDeviceSynchronize();
+    unsigned int v = 0;
+    if (e == cudaSuccess) e = cudaMemcpy(&v, p, sizeof(v), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && clear) e = cudaMemset(p, 0, sizeof(v));
+    if (e != cudaSuccess) return rl_fail(RL_ECUDA, "device status: %s", cudaGetErrorString(e));
+    if (flags_out) *flags_out = v;
+    if (v & RL_DEVFLAG_TIMEOUT) return rl_fail(RL_ETIMEOUT, "a device-side wait timed out (flags 0x%x)", v);
+    return RL_OK;
+}

@@ -25,7 +25,17 @@ TOL16 = 2e-2
 def rl():
     import paper_2307_03017_gb300 as rl
     rl._lib.lib()  # loud failure if the library is missing
-    return rl
+    rl.reallife_set_kernel_path(0)
+    yield rl
+    assert rl.reallife_device_status(clear=True) == 0  # no bounded wait gave up
+
+
+@pytest.fixture(params=[3, 1, 2], ids=["planepar", "tma", "gather"])
+def kernel_path(request, rl):
+    """Run a test with each warp-kernel family: plane-parallel, TMA-staged windows, per-pixel gather."""
+    rl.reallife_set_kernel_path(request.param)
+    yield request.param
+    rl.reallife_set_kernel_path(0)
 
 
 @pytest.fixture(scope="module")
@@ -79,7 +89,7 @@ def test_warp_offsets_match_ray_plane_intersection(rl, paper):
 # ---------------------------------------------------------------------- render
 
 @pytest.mark.parametrize("dtype", [torch.float32, torch.bfloat16])
-def test_render_matches_oracle_small(rl, small, dtype):
+def test_render_matches_oracle_small(rl, kernel_path, small, dtype):
     sc = small
     m = _mpi(rl, sc, dtype)
     Mq = m.data.float().cpu().numpy()  # the values the GPU stores (BF16-rounded when BF16)
@@ -90,7 +100,7 @@ def test_render_matches_oracle_small(rl, small, dtype):
         assert np.abs(out[j] - ref).max() <= TOL32
 
 
-def test_render_matches_oracle_paper_sampled(rl, paper):
+def test_render_matches_oracle_paper_sampled(rl, kernel_path, paper):
     """Full-size render (the benchmark's 9 views), checked on 3000 sampled pixels per view."""
     sc = paper
     m = _mpi(rl, sc)
@@ -103,7 +113,7 @@ def test_render_matches_oracle_paper_sampled(rl, paper):
         assert np.abs(out[j][ys, xs] - ref).max() <= TOL32
 
 
-def test_render_edge_cases(rl):
+def test_render_edge_cases(rl, kernel_path):
     # ragged tile tails (W % 32, H % 4 != 0), one plane, a view that sees mostly outside the MPI
     sc = sg.make_scene(5, 23, 37, 1, 2, n_layers=(1, 2), f=30.0, n_novel=3)
     m = _mpi(rl, sc)
@@ -157,7 +167,7 @@ def test_select_from_mpi_is_valid_topk(rl, paper):
 
 # -------------------------------------------------------------------- gradient
 
-def test_dense_gradient_and_loss_match_oracle(rl, small):
+def test_dense_gradient_and_loss_match_oracle(rl, kernel_path, small):
     sc = small
     m = _mpi(rl, sc)
     loss, G = rl.reallife_loss_grad(m, _dev(sc.images), sc.src)
@@ -166,7 +176,7 @@ def test_dense_gradient_and_loss_match_oracle(rl, small):
     assert np.abs(G.cpu().numpy() - g_o).max() <= TOL32
 
 
-def test_sparse_gradient_is_masked_dense_gradient(rl, small):
+def test_sparse_gradient_is_masked_dense_gradient(rl, kernel_path, small):
     sc = small
     m = _mpi(rl, sc)
     k = 3
@@ -178,7 +188,7 @@ def test_sparse_gradient_is_masked_dense_gradient(rl, small):
     assert np.abs(Gs.cpu().numpy() - want).max() <= TOL32
 
 
-def test_render_backward_matches_oracle_vjp(rl, small):
+def test_render_backward_matches_oracle_vjp(rl, kernel_path, small):
     sc = small
     m = _mpi(rl, sc)
     rng = np.random.default_rng(3)
@@ -192,7 +202,7 @@ def test_render_backward_matches_oracle_vjp(rl, small):
 
 @pytest.mark.parametrize("level", [0, 1, 2])
 @pytest.mark.parametrize("k", [1, 5, 8])
-def test_hsgd_step_matches_oracle_with_selection_pinned(rl, small, level, k):
+def test_hsgd_step_matches_oracle_with_selection_pinned(rl, kernel_path, small, level, k):
     sc = small
     m = _mpi(rl, sc)
     h, w = sc.H >> level, sc.W >> level
@@ -241,7 +251,7 @@ def _gpu_refine_steps(rl, sc, k, schedule, dtype=torch.float32):
     return m, M0, sels, losses
 
 
-def test_refine_small_matches_oracle(rl, small):
+def test_refine_small_matches_oracle(rl, kernel_path, small):
     sc = small
     m, M0, sels, losses = _gpu_refine_steps(rl, sc, 5, (2, 1, 0))
     M_o, L_o, _ = oracle.refine(M0, sc.near, sc.far, sc.ref, sc.src, sc.images, 5, (2, 1, 0), S_pins=sels)
@@ -259,7 +269,7 @@ def test_refine_call_equals_step_sequence(rl, small):
     np.testing.assert_allclose(lpi.cpu().numpy(), losses, rtol=1e-6)
 
 
-def test_refine_paper_size_matches_oracle(rl, paper):
+def test_refine_paper_size_matches_oracle(rl, kernel_path, paper):
     """The benchmark's workload (512x384, D=32, N=4, k=5, levels 2,1,0) at full size."""
     sc = paper
     m, M0, sels, losses = _gpu_refine_steps(rl, sc, 5, (2, 1, 0))
@@ -268,7 +278,7 @@ def test_refine_paper_size_matches_oracle(rl, paper):
     np.testing.assert_allclose(losses, L_o, rtol=1e-5)
 
 
-def test_refine_bf16_storage_within_tolerance(rl, small):
+def test_refine_bf16_storage_within_tolerance(rl, kernel_path, small):
     sc = small
     m, M0, sels, losses = _gpu_refine_steps(rl, sc, 5, (2, 1, 0), torch.bfloat16)
     M_o, L_o, _ = oracle.refine(M0, sc.near, sc.far, sc.ref, sc.src, sc.images, 5, (2, 1, 0), S_pins=sels)
@@ -287,8 +297,47 @@ def test_degenerate_one_plane_and_one_view(rl):
     assert np.abs(m.data.cpu().numpy() - M_o).max() <= TOL32
 
 
-def test_ragged_sizes_and_level_tails(rl):
+def test_ragged_sizes_and_level_tails(rl, kernel_path):
     sc = sg.make_scene(4, 20, 44, 5, 2, n_layers=(2, 3), f=40.0)  # W/4 = 11: ragged tiles at every level
     m, M0, sels, _ = _gpu_refine_steps(rl, sc, 2, (2, 1, 0))
     M_o, _, _ = oracle.refine(M0, sc.near, sc.far, sc.ref, sc.src, sc.images, 2, (2, 1, 0), S_pins=sels)
     assert np.abs(m.data.cpu().numpy() - M_o).max() <= TOL32
+
+
+def test_kernel_families_agree_on_extreme_warps(rl):
+    """Large rotations and translations push samples out of the staged windows (fallback loads)."""
+    rng = np.random.default_rng(7)
+    sc = sg.make_scene(6, 64, 96, 6, 3, n_layers=(2, 3), f=96.0)
+    cams = [sg.Camera(sc.ref.K, sg.random_rotation(rng, 25.0), rng.uniform(-0.6, 0.6, 3)) for _ in range(3)]
+    g_out = _dev(rng.normal(size=(3, sc.H, sc.W, 3)).astype(np.float32))
+    outs, grads = [], []
+    for path in (3, 1, 2):
+        rl.reallife_set_kernel_path(path)
+        m = _mpi(rl, sc)
+        outs.append(rl.reallife_render(m, cams).cpu().numpy())
+        grads.append(rl.reallife_render_backward(m, cams, g_out).cpu().numpy())
+    rl.reallife_set_kernel_path(0)
+    for j, cam in enumerate(cams):
+        assert np.abs(outs[0][j] - oracle.render(sc.coarse_mpi, sc.near, sc.far, sc.ref, cam)).max() <= TOL32
+    want = oracle.vjp(sc.coarse_mpi, sc.near, sc.far, sc.ref, cams, g_out.cpu().numpy())
+    for p in (1, 2):
+        assert np.abs(outs[0] - outs[p]).max() <= TOL32
+    for p in (0, 1, 2):
+        assert np.abs(grads[p] - want).max() <= 1e-4 * max(1.0, np.abs(want).max())
+
+
+@pytest.mark.parametrize("D", [16, 64])
+def test_bf16_odd_width_and_large_plane_counts(rl, D):
+    """BF16 MPIs with odd W cannot be described for TMA (gather kernels); D=64 fills the mask word."""
+    sc = sg.make_scene(8, 24, 45 if D == 16 else 48, D, 2, n_layers=(2, 3), f=45.0)
+    m = _mpi(rl, sc, torch.bfloat16)
+    Mq = m.data.float().cpu().numpy()
+    out = rl.reallife_render(m, sc.src).cpu().numpy()
+    for j, cam in enumerate(sc.src):
+        assert np.abs(out[j] - oracle.render(Mq, sc.near, sc.far, sc.ref, cam)).max() <= TOL32
+    S = torch.empty((9, sc.H, sc.W), dtype=torch.uint8, device="cuda")
+    loss = torch.empty(1, dtype=torch.float32, device="cuda")
+    rl.reallife_hsgd_step(m, _dev(sc.images), sc.src, 9, loss_out=loss, S_out=S)
+    M_o, L_o, _ = oracle.hsgd_step(Mq, sc.near, sc.far, sc.ref, sc.src, sc.images, 9, S_pin=S.cpu().numpy())
+    assert np.abs(m.data.float().cpu().numpy() - M_o).max() <= TOL16
+    assert abs(loss.item() - L_o) <= 1e-5 * L_o

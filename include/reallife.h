@@ -127,6 +127,28 @@ rl_status reallife_refine(rl_mpi* m, const float* images, const rl_camera* src, 
                           const int* schedule, int iters, float* loss_per_iter, void* ws, size_t ws_bytes,
                           cudaStream_t stream);
 
+/* HSGD iteration for callers that cannot allocate device memory (no counterpart in the
+ * paper; an interface for hosts such as plugins inside an application that owns the GPU
+ * heap and gives them no allocator, or frame loops that must not call cudaMalloc).  It
+ * computes exactly what reallife_hsgd_step computes, but takes no workspace: the
+ * library keeps a fixed scratch array of RL_NOALLOC_SCRATCH_BYTES in every GPU that
+ * loads it, held until the process exits, and this call allocates nothing.
+ *   - Arguments and outputs as reallife_hsgd_step.
+ *   - RL_ENOMEM (with a message) when the problem needs more scratch than the array
+ *     holds (reallife_workspace_bytes > RL_NOALLOC_SCRATCH_BYTES); e.g. 512x384, D=32,
+ *     N=4, k=5 needs 48 MB and fits, 1920x1080 D=64 does not.
+ *   - The first call on a device looks up the array's device address for that device
+ *     (cudaGetSymbolAddress) with the device current; make that first call before any
+ *     stream capture.
+ *   - All calls on a device share the one array, and it keeps what the last call left
+ *     in it (every value a call reads is written earlier in the same call).  Calls that
+ *     overlap on the GPU -- on different streams, or from different threads -- race on
+ *     it: order them.
+ *   - RL_EINVAL while kernel tracing is enabled (tracing creates CUDA events). */
+#define RL_NOALLOC_SCRATCH_BYTES (64u << 20)
+rl_status reallife_hsgd_step_noalloc(rl_mpi* m, const float* images, const rl_camera* src, int N,
+                                     const rl_hsgd_params* p, float* loss_out, uint8_t* S_out, cudaStream_t stream);
+
 /* -------------------------------------------------------- steps of the iteration */
 
 /* Down^l of P stacked [H][W][C] FP32 slices (2x2 box average applied l times, computed

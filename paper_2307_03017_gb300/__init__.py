@@ -23,7 +23,7 @@ __all__ = [
     "reallife_downsample_f32", "reallife_select", "reallife_select_keys", "reallife_loss_grad",
     "reallife_sparse_update", "reallife_render_backward", "reallife_warp_offsets",
     "reallife_trace_enable", "reallife_trace_read", "reallife_strerror", "workspace", "library_path",
-    "reallife_set_kernel_path", "reallife_device_status",
+    "reallife_set_kernel_path", "reallife_device_status", "reallife_hsgd_step_noalloc",
 ]
 
 RealLifeError = _lib.RealLifeError
@@ -147,6 +147,22 @@ def reallife_hsgd_step(m: Mpi, images: torch.Tensor, src, k: int, lam: float = 1
     _lib.check("reallife_hsgd_step", _lib.lib().reallife_hsgd_step(
         ctypes.byref(ms), _ptr(images), _lib.cameras(src), N, ctypes.byref(p), _ptr(loss_out), _ptr(S_out),
         _ptr(ws), ws.numel(), _stream(stream)))
+    return loss_out, S_out
+
+
+def reallife_hsgd_step_noalloc(m: Mpi, images: torch.Tensor, src, k: int, lam: float = 1.0, clamp: bool = True,
+                               level: int = 0, loss_out: torch.Tensor | None = None,
+                               S_out: torch.Tensor | None = None, stream=None):
+    """One HSGD iteration without a caller workspace (for callers that cannot allocate):
+    the library's fixed per-device scratch array is used instead.  Same results as
+    ``reallife_hsgd_step``; calls that overlap on the GPU race on the shared array."""
+    N = len(src)
+    _check_f32(images, (N, m.H, m.W, 3), "images")
+    ms = m.c_struct()
+    p = _params(k, lam, clamp, level)
+    _lib.check("reallife_hsgd_step_noalloc", _lib.lib().reallife_hsgd_step_noalloc(
+        ctypes.byref(ms), _ptr(images), _lib.cameras(src), N, ctypes.byref(p), _ptr(loss_out), _ptr(S_out),
+        _stream(stream)))
     return loss_out, S_out
 
 

@@ -18,7 +18,7 @@ EXPORTS = [
     "reallife_downsample_f32", "reallife_select", "reallife_select_keys", "reallife_loss_grad",
     "reallife_sparse_update", "reallife_render_backward", "reallife_warp_offsets", "reallife_trace_enable",
     "reallife_trace_read", "reallife_strerror", "reallife_last_error", "reallife_set_kernel_path",
-    "reallife_device_status",
+    "reallife_device_status", "reallife_hsgd_step_noalloc",
 ]
 
 
@@ -71,6 +71,7 @@ def _declare(lib):
         "reallife_workspace_bytes": (c_size_t, [c_int, c_int, c_int, c_int, c_int, c_int]),
         "reallife_render": (c_int, [mpi_p, cam_p, c_int, vp, vp]),
         "reallife_hsgd_step": (c_int, [mpi_p, vp, cam_p, c_int, par_p, vp, vp, vp, c_size_t, vp]),
+        "reallife_hsgd_step_noalloc": (c_int, [mpi_p, vp, cam_p, c_int, par_p, vp, vp, vp]),
         "reallife_refine": (c_int, [mpi_p, vp, cam_p, c_int, par_p, ctypes.POINTER(c_int), c_int, vp, vp, c_size_t,
                                     vp]),
         "reallife_downsample_f32": (c_int, [vp, c_int, c_int, c_int, c_int, c_int, vp, vp]),

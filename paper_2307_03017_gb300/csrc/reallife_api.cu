@@ -468,3 +468,65 @@ extern "C" rl_status reallife_warp_offsets(const rl_mpi* m, const rl_camera* vie
     if (st) return st;
     return rl_launch_warp_offsets(m->D, m->H, m->W, views, out, stream);
 }
+
+// ------------------------------------------------------ fixed-scratch HSGD step
+//
+// Some callers cannot allocate device memory at all: a plugin running inside a host
+// application that owns the GPU heap and hands its plugins no allocator, or a frame loop
+// that must not call cudaMalloc because the call can synchronise the device and stall
+// the frame.  reallife_hsgd_step_noalloc runs the same iteration as reallife_hsgd_step
+// without asking them for a workspace: its scratch is the array below, a fixed
+// RL_NOALLOC_SCRATCH_BYTES per device that every GPU loading this library keeps until
+// the process exits.  The array's name is only a host-side stand-in in host code, so its
+// device address is looked up with cudaGetSymbolAddress (once per device, on the first
+// call with that device current) and passed to the kernels.
+
+static __device__ __align__(256) unsigned char g_rl_noalloc_scratch[RL_NOALLOC_SCRATCH_BYTES];
+
+namespace {
+std::mutex g_noalloc_mu;
+void* g_noalloc_ptr[256] = {};
+
+rl_status noalloc_scratch(void** out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return rl_fail(RL_ECUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
+    if (dev < 0 || dev >= 256) return rl_fail(RL_ECUDA, "device ordinal %d out of range", dev);
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_rl_noalloc_scratch);
+        if (e != cudaSuccess || !p)
+            return rl_fail(RL_ECUDA, "cudaGetSymbolAddress of the fixed scratch: %s", cudaGetErrorString(e));
+        g_noalloc_ptr[dev] = p;
+    }
+    *out = g_noalloc_ptr[dev];
+    return RL_OK;
+}
+}  // namespace
+
+extern "C" rl_status reallife_hsgd_step_noalloc(rl_mpi* m, const float* images, const rl_camera* src, int N,
+                                                const rl_hsgd_params* p, float* loss_out, uint8_t* S_out,
+                                                cudaStream_t stream) {
+    rl_status st = check_mpi(m);
+    if (st) return st;
+    if (!p) return rl_fail(RL_EINVAL, "params is NULL");
+    if (p->k < 1 || p->k > m->D) return rl_fail(RL_EINVAL, "k=%d outside [1, D=%d]", p->k, m->D);
+    if (N < 1 || N > RL_MAX_VIEWS) return rl_fail(RL_EINVAL, "N=%d outside [1,%d]", N, RL_MAX_VIEWS);
+    const size_t need = ws_layout(N, m->D, m->H, m->W, p->k, m->dtype).total;
+    if (need > (size_t)RL_NOALLOC_SCRATCH_BYTES)
+        return rl_fail(RL_ENOMEM, "this problem needs %zu bytes of scratch; the fixed scratch holds %zu bytes", need,
+                       (size_t)RL_NOALLOC_SCRATCH_BYTES);
+    {
+        std::lock_guard<std::mutex> lk(g_tmu);
+        if (g_trace_on) return rl_fail(RL_EINVAL, "kernel tracing creates CUDA events; disable it for this call");
+    }
+    void* ws = nullptr;
+    st = noalloc_scratch(&ws);
+    if (st) return st;
+    st = check_hsgd(m, images, src, N, p, p->level, ws, (size_t)RL_NOALLOC_SCRATCH_BYTES);
+    if (st) return st;
+    // every part of the scratch this iteration reads is written earlier in the same
+    // iteration (level MPI, selection, slot map; the select kernel zeroes the gradient slots)
+    return enqueue_hsgd(m, images, src, N, p->k, p->lambda, p->clamp01, p->level, loss_out, S_out, ws, stream);
+}

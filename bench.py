@@ -41,7 +41,12 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", default="paper", choices=["paper", "paper_bf16", "display", "small"])
+    ap.add_argument("--workload", default="paper", choices=["paper", "paper_bf16", "display", "small", "serve"])
+    ap.add_argument("--requests", type=int, default=2000, help="serve: number of requests")
+    ap.add_argument("--rate", type=float, default=200.0, help="serve: Poisson arrival rate (requests/s)")
+    ap.add_argument("--slots", type=int, default=8, help="serve: concurrent request slots")
+    ap.add_argument("--arena-gb", type=float, default=24.0, help="serve: device memory arena (GB)")
+    ap.add_argument("--graphs", action="store_true", help="serve: replay captured CUDA graphs")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-clocks", action="store_true")
@@ -148,16 +153,26 @@ def k3_algorithmic_bytes(cfg, sc, level: int, elt: int) -> int:
     return (sc.D * h * w * 4 * elt + cfg["N"] * sc.H * sc.W * 3 * 4 + h * w * 8 + cfg["k"] * h * w * 16)
 
 
+RENDER_VIEWS_PER_LAUNCH = 16  # RL_MAX_VIEWS: target views per render launch
+
+
+def render_algorithmic_bytes(sc, elt: int, n_views: int) -> int:
+    """Minimal DRAM bytes of rendering n_views: the MPI read once per launch of up to 16
+    views (their blocks share it through L2) and every view's RGB output written once."""
+    Mb = sc.D * sc.H * sc.W * 4 * elt
+    launches = -(-n_views // RENDER_VIEWS_PER_LAUNCH)
+    return launches * Mb + n_views * sc.H * sc.W * 12
+
+
 def step_algorithmic_bytes(cfg, sc, elt: int) -> int:
     """Minimal DRAM bytes of one step: per level-l iteration read M (select / pyramid),
-    write M_l (l > 0), K3 traffic, read-modify-write the kept k/D of M; 9 renders read M
-    once each and write their RGB output."""
+    write M_l (l > 0), the fused kernel's traffic, read-modify-write the kept k/D of M;
+    then the renders."""
     Mb = sc.D * sc.H * sc.W * 4 * elt
     tot = 0
     for l in cfg["schedule"]:
         tot += Mb + (Mb >> (2 * l) if l else 0) + k3_algorithmic_bytes(cfg, sc, l, elt) + 2 * cfg["k"] * Mb // sc.D
-    tot += len(sc.novel) * (Mb + sc.H * sc.W * 12)
-    return tot
+    return tot + render_algorithmic_bytes(sc, elt, len(sc.novel))
 
 
 def run_ours(args, world, rank, local):
@@ -235,8 +250,7 @@ def run_ours(args, world, rank, local):
         per_step = sum(k3_algorithmic_bytes(cfg, sc, l, elt) for l in sched)
         alg_bytes = per_step * args.steps
     elif dom_name.startswith("render"):
-        Mb = sc.D * sc.H * sc.W * 4 * elt
-        alg_bytes = args.steps * len(sc.novel) * (Mb + sc.H * sc.W * 12)
+        alg_bytes = args.steps * render_algorithmic_bytes(sc, elt, len(sc.novel))
     else:
         alg_bytes = None
     achieved = alg_bytes / (dom_ms / 1e3) / 1e9 if alg_bytes else None
@@ -316,6 +330,83 @@ def run_e2e(args, rl, sc, cfg, dtype, dev, world, dist):
     return {"value": round(world * args.steps / (ms / 1e3), 3), "unit": UNIT,
             "h2d_bytes_per_step": int(h_M.numel() * h_M.element_size() + h_I.numel() * 4),
             "d2h_bytes_per_step": int(h_out.numel() * 4)}
+
+
+# ----------------------------------------------------------------------- serving
+
+SERVE_RES = [(192, 256), (384, 512), (576, 768), (768, 1024)]
+SERVE_D = [16, 32, 48, 64]
+
+
+def serve_scene_pool(seed: int = 7, n_views: int = 6):
+    """One seeded scene per (resolution, D) of the serving workload, with 6 source views
+    (requests with fewer views use the first N), coarse MPI BF16 in pinned host memory."""
+    import scenegen as sg
+    import torch
+    pool = {}
+    for (H, W) in SERVE_RES:
+        for D in SERVE_D:
+            sc = sg.make_scene(seed + len(pool), H, W, D, n_views, n_layers=(3, 8), novel="none")
+            M = torch.from_numpy(sc.coarse_mpi).to(torch.bfloat16).pin_memory()
+            I = torch.from_numpy(sc.images).pin_memory()
+            pool[(H, W, D)] = (sc, M, I)
+            sc.coarse_mpi = None  # host copy no longer needed
+    return pool
+
+
+def serve_requests_from_pool(pool, draws):
+    from paper_2307_03017_gb300.serve import Request
+    out = []
+    for r in draws:
+        sc, M, I = pool[(r["H"], r["W"], r["D"])]
+        N = r["N"]
+        out.append(Request(id=r["id"], arrival=r["arrival"], coarse=M, images=I[:N], ref=sc.ref, src=sc.src[:N],
+                           near=sc.near, far=sc.far, schedule=(2, 1, 0) if r["iters"] == 3 else (2, 0), k=5))
+    return out
+
+
+def run_serve(args, world, rank, local):
+    import torch
+    import scenegen as sg
+    from paper_2307_03017_gb300.serve import ServeEngine, latency_stats
+    torch.cuda.set_device(local)
+    t_gen = time.perf_counter()
+    pool = serve_scene_pool()
+    t_gen = time.perf_counter() - t_gen
+    draws = sg.serve_requests(args.requests, args.rate, seed=12345)
+    max_elems = max(M.numel() for (_, M, _) in pool.values())
+    eng = ServeEngine(int(args.arena_gb * (1 << 30)), max_slots=args.slots, graphs=args.graphs,
+                      max_result_elems=max_elems)
+    # warm-up: one request of every (resolution, D) so first-use costs stay out of the run
+    warm = serve_requests_from_pool(pool, [dict(id=-1, arrival=0.0, H=H, W=W, D=D, N=4, iters=3)
+                                           for (H, W) in SERVE_RES for D in SERVE_D])
+    eng.run(warm, realtime=False)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local) if not args.no_clocks else None
+    if clocks:
+        clocks.start()
+    done = eng.run(serve_requests_from_pool(pool, draws), realtime=True)
+    poisson = latency_stats(done)
+    closed = latency_stats(eng.run(serve_requests_from_pool(pool, draws[: max(1, args.requests // 4)]),
+                                   realtime=False))
+    clk = clocks.stop() if clocks else None
+    mean_px = float(np.mean([d["H"] * d["W"] for d in draws]))
+    return {
+        "metric": "p50/p99 serve latency and reconstructions/s (Poisson arrivals, BF16 MPIs)",
+        "value": round(poisson["p99_ms"], 3), "unit": "ms (p99 latency)", "higher_is_better": False,
+        "n_gpus": world, "p50_ms": round(poisson["p50_ms"], 3), "p99_ms": round(poisson["p99_ms"], 3),
+        "mean_ms": round(poisson["mean_ms"], 3), "max_ms": round(poisson["max_ms"], 3),
+        "queue_p50_ms": round(poisson["queue_p50_ms"], 3), "queue_p99_ms": round(poisson["queue_p99_ms"], 3),
+        "reconstructions_per_s": round(poisson["reconstructions_per_s"], 2),
+        "closed_loop_reconstructions_per_s": round(closed["reconstructions_per_s"], 2),
+        "dtype": "bf16", "data": "synthetic (seeded ray-cast layered scenes; no dataset)",
+        "config": {"workload": f"serve: {args.requests} requests, Poisson {args.rate}/s, res in {SERVE_RES}, "
+                               f"D in {SERVE_D}, N 2-6, 2-3 iterations, k=5, BF16",
+                   "slots": args.slots, "arena_gb": args.arena_gb, "graphs": bool(args.graphs),
+                   "latency": "arrival -> refined MPI and losses on the host (queueing, H2D, compute, D2H)",
+                   "mean_pixels": mean_px, "scene_pool_s": round(t_gen, 1)},
+        "graph_captures": eng.captures, "graph_replays": eng.replays, "clocks": clk,
+    }
 
 
 # ------------------------------------------------------------------- CPU oracle
@@ -420,6 +511,8 @@ def main():
     world, rank, local = dist_env()
     if args.impl == "reference":
         res = run_reference(args, world, rank)
+    elif args.workload == "serve":
+        res = run_serve(args, world, rank, local) if rank == 0 else None
     else:
         res = run_ours(args, world, rank, local)
         if res is not None and not args.no_cpu_baseline and world == 1:

@@ -51,6 +51,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-clocks", action="store_true")
     ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--kernel-path", type=int, default=0,
+                    help="warp-kernel family: 0 automatic, 1 TMA windows, 2 per-pixel gather, 3/4 plane-parallel")
     return ap.parse_args()
 
 
@@ -181,6 +183,7 @@ def run_ours(args, world, rank, local):
 
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
+    rl.reallife_set_kernel_path(args.kernel_path)
     dist = None
     if world > 1:
         import torch.distributed as dist
@@ -283,6 +286,7 @@ def run_ours(args, world, rank, local):
             "data": "synthetic (seeded ray-cast layered scenes; no dataset)",
             "config": {"workload": f"{args.workload}: {sc.W}x{sc.H} D={sc.D} N={N} k={k} levels={list(sched)} "
                                    f"+ {len(sc.novel)} novel views", "storage": cfg["dtype"],
+                       "kernel_path": args.kernel_path,
                        "l2": "flushed (512 MB write) before every timed step", "parallelism": f"replicas{world}"},
             "hbm_gbs_step": round(step_bytes / (total_ms / args.steps / 1e3) / 1e9, 1),
             "roofline": roofline, "kernels": kernels, "gpu_launches": int(launches),

@@ -207,7 +207,8 @@ rl_status reallife_warp_offsets(const rl_mpi* m, const rl_camera* view, float* o
  *     (always for FP32; even W for BF16), plane-parallel elsewhere;
  *   2 per-pixel gather (one thread per view pixel walks all planes);
  *   3 plane-parallel (warps own chunks of planes; chunks combined through the
- *     associativity of the over operator).
+ *     associativity of the over operator), 8 warps per block;
+ *   4 plane-parallel with 4 warps per block where D <= 32; 5 same as 3.
  * All compute the same values up to FP32 rounding of the accumulation order.
  * Process-wide; RL_EINVAL for other values. */
 rl_status reallife_set_kernel_path(int path);

@@ -69,10 +69,9 @@ k_grad(const Tm* __restrict__ M, int D, int H, int W, const __grid_constant__ RL
     extern __shared__ float sT[];  // [D][kGradThreads]
     // view-fastest block order: the N views of a tile run together and share M through L2
     const int tid = threadIdx.y * kGradBX + threadIdx.x;
-    const int view = blockIdx.x % views.n;
-    const int tile = blockIdx.x / views.n;
-    const int qx = (tile % tiles_x) * kGradBX + threadIdx.x;
-    const int qy = (tile / tiles_x) * kGradBY + threadIdx.y;
+    const int view = blockIdx.x;  // grid (views, tiles_x, tiles_y)
+    const int qx = blockIdx.y * kGradBX + threadIdx.x;
+    const int qy = blockIdx.z * kGradBY + threadIdx.y;
     float lsum = 0.f;
     if (qx < W && qy < H) {
         const RLWarp w = rl_warp_coeffs(views.v[view], (float)qx, (float)qy);
@@ -145,7 +144,7 @@ k_grad(const Tm* __restrict__ M, int D, int H, int W, const __grid_constant__ RL
         if (tid == 0) {
             float s = 0.f;
             for (int j = 0; j < kGradThreads / 32; ++j) s += red[j];
-            partials[blockIdx.x] = s;
+            partials[blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z)] = s;
         }
     }
 }
@@ -169,7 +168,7 @@ __global__ void __launch_bounds__(1024) k_loss_reduce(const float* __restrict__ 
 template <typename Tm, bool SPARSE, bool LOSS>
 void launch_grad_t(const void* M, int D, int H, int W, const RLViews& views, const float* images, int img_level,
                    const float* grad_out, const uint8_t* slots, float* G, float inv_n, float* partials, int tiles_x,
-                   unsigned grid, size_t smem, cudaStream_t s) {
+                   dim3 grid, size_t smem, cudaStream_t s) {
     auto kern = k_grad<Tm, SPARSE, LOSS>;
     if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     kern<<<grid, dim3(kGradBX, kGradBY), smem, s>>>((const Tm*)M, D, H, W, views, tiles_x, images, img_level, grad_out,
@@ -198,9 +197,9 @@ rl_status rl_launch_grad(const void* M, rl_dtype dt, int D, int H, int W, const 
         return rl_launch_grad_pp(M, dt, D, H, W, views, mode_loss, images, img_level, grad_out, slots, G, inv_n,
                                  partials, nblocks, s);
     const int tiles_x = (W + kGradBX - 1) / kGradBX, tiles_y = (H + kGradBY - 1) / kGradBY;
-    const unsigned grid = (unsigned)(tiles_x * tiles_y * views.n);
+    const dim3 grid((unsigned)views.n, (unsigned)tiles_x, (unsigned)tiles_y);
     const size_t smem = (size_t)D * kGradThreads * sizeof(float);
-    if (nblocks) *nblocks = (int)grid;
+    if (nblocks) *nblocks = (int)(grid.x * grid.y * grid.z);
     const bool sparse = slots != nullptr;
     const char* name = dt == RL_F32 ? (sparse ? "grad_sparse_f32" : "grad_dense_f32")
                                     : (sparse ? "grad_sparse_bf16" : "grad_dense_bf16");

@@ -1,8 +1,9 @@
 // pp.cu -- plane-parallel warp kernels: novel-view rendering (Eq. eq_render, eq_over) and
 // the fused warp + composite + residual + exact adjoint of one HSGD iteration.
 //
-// Layout.  A block is kGroups warps over the same 32 view pixels (a 16 x 2 tile); warp g
-// owns planes [g C, g C + C), C = ceil(D / kGroups) <= 8, so a warp's loads of one plane
+// Layout.  A block is kGroups (4 or 8) warps over the same 32 view pixels (a 16 x 2 tile; grid =
+// (views, tiles_x, tiles_y) so that the views of a tile run together); warp g
+// owns planes [g C, g C + C), C = ceil(D / kGroups) rounded up to 1, 2, 4 or 8, so a warp's loads of one plane
 // are 32 neighbouring voxels.  Each thread samples its C planes once and keeps them in
 // registers, nearest first forming its chunk's composite Cc_g = sum c_d alpha_d T_d^loc
 // and transmittance Tc_g = prod (1 - alpha_d).  The over operator is associative, so the
@@ -18,9 +19,7 @@
 
 namespace {
 
-constexpr int kGroups = 8;                 // warps (plane chunks) per block
 constexpr int kTX = 16, kTY = 2, kPix = 32;  // pixels per block, one per lane
-constexpr int kThreads = kGroups * kPix;
 
 __device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
 
@@ -103,24 +102,24 @@ struct PixelCoord {
     bool active;
 };
 
-__device__ __forceinline__ PixelCoord pixel_coord(int nviews, int tiles_x, int H, int W) {
+// grid (views, tiles_x, tiles_y): the views of a tile run together and share M in L2
+__device__ __forceinline__ PixelCoord pixel_coord(int H, int W) {
     PixelCoord c;
-    c.view = blockIdx.x % nviews;
-    const int tile = blockIdx.x / nviews;
+    c.view = blockIdx.x;
     c.g = threadIdx.x >> 5;
     c.lane = threadIdx.x & 31;
-    c.qx = (tile % tiles_x) * kTX + (c.lane % kTX);
-    c.qy = (tile / tiles_x) * kTY + (c.lane / kTX);
+    c.qx = blockIdx.y * kTX + (c.lane % kTX);
+    c.qy = blockIdx.z * kTY + (c.lane / kTX);
     c.active = c.qx < W && c.qy < H;
     return c;
 }
 
-template <typename Tm, int C>
-__global__ void __launch_bounds__(kThreads)
+template <typename Tm, int C, int kGroups>
+__global__ void __launch_bounds__(kGroups * kPix)
 k_render_pp(const Tm* __restrict__ M, int D, int H, int W, const __grid_constant__ RLViews views, int tiles_x,
             float* __restrict__ out) {
     __shared__ float4 xch[kGroups][kPix];  // per chunk: (Cc.rgb, Tc)
-    const PixelCoord pc = pixel_coord(views.n, tiles_x, H, W);
+    const PixelCoord pc = pixel_coord(H, W);
     const int qx = min(pc.qx, W - 1), qy = min(pc.qy, H - 1);
     const RLWarp w = rl_warp_coeffs(views.v[pc.view], (float)qx, (float)qy);
     const size_t plane = (size_t)H * W * 4;
@@ -157,14 +156,14 @@ k_render_pp(const Tm* __restrict__ M, int D, int H, int W, const __grid_constant
     }
 }
 
-template <typename Tm, int C, bool SPARSE, bool LOSS>
-__global__ void __launch_bounds__(kThreads)
+template <typename Tm, int C, int kGroups, bool SPARSE, bool LOSS>
+__global__ void __launch_bounds__(kGroups * kPix)
 k_grad_pp(const Tm* __restrict__ M, int D, int H, int W, const __grid_constant__ RLViews views, int tiles_x,
           const float* __restrict__ images, int img_level, const float* __restrict__ grad_out,
           const uint8_t* __restrict__ slots, float* __restrict__ G, float inv_n, float* __restrict__ partials) {
     __shared__ float4 xch[kGroups][kPix];
     __shared__ float red[kGroups];
-    const PixelCoord pc = pixel_coord(views.n, tiles_x, H, W);
+    const PixelCoord pc = pixel_coord(H, W);
     const int qx = min(pc.qx, W - 1), qy = min(pc.qy, H - 1);
     const RLWarp w = rl_warp_coeffs(views.v[pc.view], (float)qx, (float)qy);
     const size_t plane = (size_t)H * W * 4;
@@ -272,39 +271,70 @@ k_grad_pp(const Tm* __restrict__ M, int D, int H, int W, const __grid_constant__
         if (threadIdx.x == 0) {
             float s = 0.f;
             for (int i = 0; i < kGroups; ++i) s += red[i];
-            partials[blockIdx.x] = s;
+            partials[blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z)] = s;
         }
     }
 }
 
-int chunk_for(int D) {
-    const int c = (D + kGroups - 1) / kGroups;
+// planes per thread for D planes over G warps: the next of 1, 2, 4, 8 >= ceil(D / G)
+int chunk_for(int D, int G) {
+    const int c = (D + G - 1) / G;
     return c <= 1 ? 1 : c <= 2 ? 2 : c <= 4 ? 4 : 8;
 }
 
+// Warps per block: 8 (measured faster than 4 at D = 32 despite the chunk combination being
+// amortised over fewer planes); kernel path 4 forces 4 where D <= 32 (at most 8 planes per
+// thread).
+int groups_for(int D, int path) {
+    return (path == 4 && D <= 32) ? 4 : 8;
+}
+
 template <typename Tm, bool SPARSE, bool LOSS>
-void launch_grad_pp_t(int C, const void* M, int D, int H, int W, const RLViews& views, int tiles_x, unsigned grid,
-                      const float* images, int img_level, const float* grad_out, const uint8_t* slots, float* G,
+void launch_grad_pp_t(int G, int C, const void* M, int D, int H, int W, const RLViews& views, int tiles_x, dim3 grid,
+                      const float* images, int img_level, const float* grad_out, const uint8_t* slots, float* G_,
                       float inv_n, float* partials, cudaStream_t s) {
-#define RL_PP_ARGS (const Tm*)M, D, H, W, views, tiles_x, images, img_level, grad_out, slots, G, inv_n, partials
-    switch (C) {
-        case 1: k_grad_pp<Tm, 1, SPARSE, LOSS><<<grid, kThreads, 0, s>>>(RL_PP_ARGS); break;
-        case 2: k_grad_pp<Tm, 2, SPARSE, LOSS><<<grid, kThreads, 0, s>>>(RL_PP_ARGS); break;
-        case 4: k_grad_pp<Tm, 4, SPARSE, LOSS><<<grid, kThreads, 0, s>>>(RL_PP_ARGS); break;
-        default: k_grad_pp<Tm, 8, SPARSE, LOSS><<<grid, kThreads, 0, s>>>(RL_PP_ARGS); break;
+#define RL_PP_ARGS (const Tm*)M, D, H, W, views, tiles_x, images, img_level, grad_out, slots, G_, inv_n, partials
+#define RL_PP_LAUNCH(CC, GG) k_grad_pp<Tm, CC, GG, SPARSE, LOSS><<<grid, GG * kPix, 0, s>>>(RL_PP_ARGS)
+    if (G == 4) {
+        switch (C) {
+            case 1: RL_PP_LAUNCH(1, 4); break;
+            case 2: RL_PP_LAUNCH(2, 4); break;
+            case 4: RL_PP_LAUNCH(4, 4); break;
+            default: RL_PP_LAUNCH(8, 4); break;
+        }
+    } else {
+        switch (C) {
+            case 1: RL_PP_LAUNCH(1, 8); break;
+            case 2: RL_PP_LAUNCH(2, 8); break;
+            case 4: RL_PP_LAUNCH(4, 8); break;
+            default: RL_PP_LAUNCH(8, 8); break;
+        }
     }
+#undef RL_PP_LAUNCH
 #undef RL_PP_ARGS
 }
 
 template <typename Tm>
-void launch_render_pp_t(int C, const void* M, int D, int H, int W, const RLViews& views, int tiles_x, unsigned grid,
-                        float* out, cudaStream_t s) {
-    switch (C) {
-        case 1: k_render_pp<Tm, 1><<<grid, kThreads, 0, s>>>((const Tm*)M, D, H, W, views, tiles_x, out); break;
-        case 2: k_render_pp<Tm, 2><<<grid, kThreads, 0, s>>>((const Tm*)M, D, H, W, views, tiles_x, out); break;
-        case 4: k_render_pp<Tm, 4><<<grid, kThreads, 0, s>>>((const Tm*)M, D, H, W, views, tiles_x, out); break;
-        default: k_render_pp<Tm, 8><<<grid, kThreads, 0, s>>>((const Tm*)M, D, H, W, views, tiles_x, out); break;
+void launch_render_pp_t(int G, int C, const void* M, int D, int H, int W, const RLViews& views, int tiles_x,
+                        dim3 grid, float* out, cudaStream_t s) {
+#define RL_PP_LAUNCH(CC, GG) \
+    k_render_pp<Tm, CC, GG><<<grid, GG * kPix, 0, s>>>((const Tm*)M, D, H, W, views, tiles_x, out)
+    if (G == 4) {
+        switch (C) {
+            case 1: RL_PP_LAUNCH(1, 4); break;
+            case 2: RL_PP_LAUNCH(2, 4); break;
+            case 4: RL_PP_LAUNCH(4, 4); break;
+            default: RL_PP_LAUNCH(8, 4); break;
+        }
+    } else {
+        switch (C) {
+            case 1: RL_PP_LAUNCH(1, 8); break;
+            case 2: RL_PP_LAUNCH(2, 8); break;
+            case 4: RL_PP_LAUNCH(4, 8); break;
+            default: RL_PP_LAUNCH(8, 8); break;
+        }
     }
+#undef RL_PP_LAUNCH
 }
 
 }  // namespace
@@ -314,19 +344,20 @@ size_t rl_grad_pp_num_blocks(int H, int W, int N) {
 }
 
 rl_status rl_launch_grad_pp(const void* M, rl_dtype dt, int D, int H, int W, const RLViews& views, bool mode_loss,
-                            const float* images, int img_level, const float* grad_out, const uint8_t* slots, float* G,
-                            float inv_n, float* partials, int* nblocks, cudaStream_t s) {
+                            const float* images, int img_level, const float* grad_out, const uint8_t* slots,
+                            float* G_out, float inv_n, float* partials, int* nblocks, cudaStream_t s) {
     const int tiles_x = (W + kTX - 1) / kTX;
-    const unsigned grid = (unsigned)rl_grad_pp_num_blocks(H, W, views.n);
-    if (nblocks) *nblocks = (int)grid;
-    const int C = chunk_for(D);
+    const dim3 grid((unsigned)views.n, (unsigned)tiles_x, (unsigned)((H + kTY - 1) / kTY));
+    if (nblocks) *nblocks = (int)rl_grad_pp_num_blocks(H, W, views.n);
+    const int G = groups_for(D, rl_kernel_path_setting());
+    const int C = chunk_for(D, G);
     const bool sparse = slots != nullptr;
     const char* name = dt == RL_F32 ? (sparse ? "grad_sparse_f32" : "grad_dense_f32")
                                     : (sparse ? "grad_sparse_bf16" : "grad_dense_bf16");
     RLTraceScope ts(name, s);
 #define RL_CASE(TM, SP, LS) \
-    launch_grad_pp_t<TM, SP, LS>(C, M, D, H, W, views, tiles_x, grid, images, img_level, grad_out, slots, G, inv_n, \
-                                 partials, s)
+    launch_grad_pp_t<TM, SP, LS>(G, C, M, D, H, W, views, tiles_x, grid, images, img_level, grad_out, slots, G_out, \
+                                 inv_n, partials, s)
     if (dt == RL_F32) {
         if (sparse) { if (mode_loss) RL_CASE(float, true, true); else RL_CASE(float, true, false); }
         else        { if (mode_loss) RL_CASE(float, false, true); else RL_CASE(float, false, false); }
@@ -341,14 +372,15 @@ rl_status rl_launch_grad_pp(const void* M, rl_dtype dt, int D, int H, int W, con
 rl_status rl_launch_render_pp(const void* M, rl_dtype dt, int D, int H, int W, const RLViews& views, float* out,
                               cudaStream_t s) {
     const int tiles_x = (W + kTX - 1) / kTX;
-    const unsigned grid = (unsigned)rl_grad_pp_num_blocks(H, W, views.n);
-    const int C = chunk_for(D);
+    const dim3 grid((unsigned)views.n, (unsigned)tiles_x, (unsigned)((H + kTY - 1) / kTY));
+    const int G = groups_for(D, rl_kernel_path_setting());
+    const int C = chunk_for(D, G);
     if (dt == RL_F32) {
         RLTraceScope ts("render_f32", s);
-        launch_render_pp_t<float>(C, M, D, H, W, views, tiles_x, grid, out, s);
+        launch_render_pp_t<float>(G, C, M, D, H, W, views, tiles_x, grid, out, s);
     } else {
         RLTraceScope ts("render_bf16", s);
-        launch_render_pp_t<__nv_bfloat16>(C, M, D, H, W, views, tiles_x, grid, out, s);
+        launch_render_pp_t<__nv_bfloat16>(G, C, M, D, H, W, views, tiles_x, grid, out, s);
     }
     return rl_check_launch("render_pp");
 }

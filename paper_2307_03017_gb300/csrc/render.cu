@@ -10,16 +10,15 @@ namespace {
 
 constexpr int kRenderBX = 32, kRenderBY = 4;
 
-// Blocks are ordered view-fastest (block = tile * n_views + view) so that the views of a
-// tile, whose plane footprints overlap, run together and share the MPI through L2.
+// Blocks are ordered view-fastest (grid x = view) so that the views of a tile, whose plane
+// footprints overlap, run together and share the MPI through L2.
 template <typename Tm>
 __global__ void __launch_bounds__(kRenderBX* kRenderBY)
 k_render(const Tm* __restrict__ M, int D, int H, int W, const __grid_constant__ RLViews views, int tiles_x,
          float* __restrict__ out) {
-    const int view = blockIdx.x % views.n;
-    const int tile = blockIdx.x / views.n;
-    const int qx = (tile % tiles_x) * kRenderBX + threadIdx.x;
-    const int qy = (tile / tiles_x) * kRenderBY + threadIdx.y;
+    const int view = blockIdx.x;  // grid (views, tiles_x, tiles_y): views of a tile run together
+    const int qx = blockIdx.y * kRenderBX + threadIdx.x;
+    const int qy = blockIdx.z * kRenderBY + threadIdx.y;
     if (qx >= W || qy >= H) return;
     const RLWarp w = rl_warp_coeffs(views.v[view], (float)qx, (float)qy);
     const size_t plane = (size_t)H * W * 4;
@@ -67,7 +66,7 @@ rl_status rl_launch_render(const void* M, rl_dtype dt, int D, int H, int W, cons
     if (path != 2) return rl_launch_render_pp(M, dt, D, H, W, views, out, s);
     dim3 block(kRenderBX, kRenderBY);
     const int tiles_x = (W + kRenderBX - 1) / kRenderBX, tiles_y = (H + kRenderBY - 1) / kRenderBY;
-    const unsigned grid = (unsigned)(tiles_x * tiles_y * views.n);
+    const dim3 grid((unsigned)views.n, (unsigned)tiles_x, (unsigned)tiles_y);
     if (dt == RL_F32) {
         RLTraceScope ts("render_f32", s);
         k_render<float><<<grid, block, 0, s>>>((const float*)M, D, H, W, views, tiles_x, out);

@@ -154,12 +154,16 @@ __device__ __forceinline__ float4 rl_sample_fast(const Tm* __restrict__ plane, i
         const float4 v01 = RLStore<Tm>::load4(p + 4 * W), v11 = RLStore<Tm>::load4(p + 4 * W + 4);
         const float w00 = (1.f - t.fx) * (1.f - t.fy), w10 = t.fx * (1.f - t.fy);
         const float w01 = (1.f - t.fx) * t.fy, w11 = t.fx * t.fy;
-        float4 a;
-        a.x = fmaf(w11, v11.x, fmaf(w01, v01.x, fmaf(w10, v10.x, w00 * v00.x)));
-        a.y = fmaf(w11, v11.y, fmaf(w01, v01.y, fmaf(w10, v10.y, w00 * v00.y)));
-        a.z = fmaf(w11, v11.z, fmaf(w01, v01.z, fmaf(w10, v10.z, w00 * v00.z)));
-        a.w = fmaf(w11, v11.w, fmaf(w01, v01.w, fmaf(w10, v10.w, w00 * v00.w)));
-        return a;
+        // packed FP32x2 FMAs: each lane of a pair is rounded as a scalar fmaf would round it
+        float2 lo = __fmul2_rn(make_float2(w00, w00), make_float2(v00.x, v00.y));
+        float2 hi = __fmul2_rn(make_float2(w00, w00), make_float2(v00.z, v00.w));
+        lo = __ffma2_rn(make_float2(w10, w10), make_float2(v10.x, v10.y), lo);
+        hi = __ffma2_rn(make_float2(w10, w10), make_float2(v10.z, v10.w), hi);
+        lo = __ffma2_rn(make_float2(w01, w01), make_float2(v01.x, v01.y), lo);
+        hi = __ffma2_rn(make_float2(w01, w01), make_float2(v01.z, v01.w), hi);
+        lo = __ffma2_rn(make_float2(w11, w11), make_float2(v11.x, v11.y), lo);
+        hi = __ffma2_rn(make_float2(w11, w11), make_float2(v11.z, v11.w), hi);
+        return make_float4(lo.x, lo.y, hi.x, hi.y);
     }
     return rl_sample(plane, H, W, t);
 }

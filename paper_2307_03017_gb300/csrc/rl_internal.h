@@ -33,6 +33,8 @@ unsigned int* rl_device_status_ptr();
 // (coarse pyramid levels, small requests), where per-pixel threads are too few to hide
 // gather latency, and per-pixel gather otherwise.
 int rl_kernel_path(int H, int W, int nviews);
+// The raw process-wide setting of reallife_set_kernel_path (0 to 5).
+int rl_kernel_path_setting();
 // TMA descriptor of an MPI [D][H][W][4] with the staging window box; false when the
 // layout cannot be described (row pitch not a multiple of 16 bytes, misaligned base).
 bool rl_encode_mpi_tmap(CUtensorMap* map, const void* M, rl_dtype dt, int D, int H, int W);

@@ -35,6 +35,7 @@ PFN_cuTensorMapEncodeTiled_v12000 encoder() {
 
 int rl_kernel_path(int H, int W, int nviews) {
     const int p = g_path.load(std::memory_order_relaxed);
+    if (p >= 3) return 3;  // plane-parallel; the group count is read in pp.cu
     if (p != 0) return p;
     return (long long)H * W * nviews < (1ll << 19) ? 3 : 2;
 }
@@ -70,8 +71,10 @@ bool rl_encode_mpi_tmap(CUtensorMap* map, const void* M, rl_dtype dt, int D, int
     return r == CUDA_SUCCESS;
 }
 
+int rl_kernel_path_setting() { return g_path.load(std::memory_order_relaxed); }
+
 extern "C" rl_status reallife_set_kernel_path(int path) {
-    if (path < 0 || path > 3) return rl_fail(RL_EINVAL, "kernel path must be 0, 1, 2 or 3");
+    if (path < 0 || path > 5) return rl_fail(RL_EINVAL, "kernel path must be 0 to 5");
     g_path.store(path);
     return RL_OK;
 }

@@ -18,6 +18,9 @@
 namespace {
 
 constexpr int kGradBX = 32, kGradBY = 4, kGradThreads = kGradBX * kGradBY;
+#ifndef RL_GRAD_MIN_BLOCKS
+#define RL_GRAD_MIN_BLOCKS 10  // resident blocks per SM the register budget must allow (measured best)
+#endif
 
 template <bool SPARSE>
 __device__ __forceinline__ void scatter_tap(float* __restrict__ G, const uint8_t* __restrict__ slots_d, int d,
@@ -62,10 +65,11 @@ __device__ __forceinline__ void scatter4(float* __restrict__ G, const uint8_t* _
 }
 
 template <typename Tm, bool SPARSE, bool LOSS>
-__global__ void __launch_bounds__(kGradThreads)
+__global__ void __launch_bounds__(kGradThreads, RL_GRAD_MIN_BLOCKS)
 k_grad(const Tm* __restrict__ M, int D, int H, int W, const __grid_constant__ RLViews views, int tiles_x,
        const float* __restrict__ images, int img_level, const float* __restrict__ grad_out,
-       const uint8_t* __restrict__ slots, float* __restrict__ G, float inv_n, float* __restrict__ partials) {
+       const uint8_t* __restrict__ slots, float* __restrict__ G, float inv_n, float* __restrict__ partials,
+       float* __restrict__ loss_out, unsigned* __restrict__ counter, float loss_scale) {
     extern __shared__ float sT[];  // [D][kGradThreads]
     // view-fastest block order: the N views of a tile run together and share M through L2
     const int tid = threadIdx.y * kGradBX + threadIdx.x;
@@ -141,11 +145,12 @@ k_grad(const Tm* __restrict__ M, int D, int H, int W, const __grid_constant__ RL
         lsum = rl_warp_sum(lsum);
         if ((tid & 31) == 0) red[tid >> 5] = lsum;
         __syncthreads();
-        if (tid == 0) {
-            float s = 0.f;
-            for (int j = 0; j < kGradThreads / 32; ++j) s += red[j];
-            partials[blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z)] = s;
-        }
+        float blk = 0.f;
+        if (tid == 0)
+            for (int j = 0; j < kGradThreads / 32; ++j) blk += red[j];
+        __syncthreads();
+        rl_loss_epilogue(blk, partials, blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z),
+                         gridDim.x * gridDim.y * gridDim.z, loss_out, counter, loss_scale, tid, kGradThreads, red);
     }
 }
 
@@ -167,12 +172,12 @@ __global__ void __launch_bounds__(1024) k_loss_reduce(const float* __restrict__ 
 
 template <typename Tm, bool SPARSE, bool LOSS>
 void launch_grad_t(const void* M, int D, int H, int W, const RLViews& views, const float* images, int img_level,
-                   const float* grad_out, const uint8_t* slots, float* G, float inv_n, float* partials, int tiles_x,
-                   dim3 grid, size_t smem, cudaStream_t s) {
+                   const float* grad_out, const uint8_t* slots, float* G, float inv_n, float* partials, float* loss_out,
+                   unsigned* counter, float loss_scale, int tiles_x, dim3 grid, size_t smem, cudaStream_t s) {
     auto kern = k_grad<Tm, SPARSE, LOSS>;
     if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     kern<<<grid, dim3(kGradBX, kGradBY), smem, s>>>((const Tm*)M, D, H, W, views, tiles_x, images, img_level, grad_out,
-                                                    slots, G, inv_n, partials);
+                                                    slots, G, inv_n, partials, loss_out, counter, loss_scale);
 }
 
 }  // namespace
@@ -185,17 +190,18 @@ size_t rl_grad_num_blocks(int H, int W, int N) {
 
 rl_status rl_launch_grad(const void* M, rl_dtype dt, int D, int H, int W, const RLViews& views, bool mode_loss,
                          const float* images, int img_level, const float* grad_out, const uint8_t* slots, float* G,
-                         float inv_n, float* partials, int* nblocks, cudaStream_t s) {
+                         float inv_n, float* partials, int* nblocks, cudaStream_t s, float* loss_out,
+                         unsigned* counter, float loss_scale) {
     const int path = rl_kernel_path(H, W, views.n);
     if (path == 1) {
         CUtensorMap map;
         if (rl_encode_mpi_tmap(&map, M, dt, D, H, W))
             return rl_launch_grad_tma(map, M, dt, D, H, W, views, mode_loss, images, img_level, grad_out, slots, G,
-                                      inv_n, partials, nblocks, s);
+                                      inv_n, partials, nblocks, s, loss_out, counter, loss_scale);
     }
     if (path != 2)
         return rl_launch_grad_pp(M, dt, D, H, W, views, mode_loss, images, img_level, grad_out, slots, G, inv_n,
-                                 partials, nblocks, s);
+                                 partials, nblocks, s, loss_out, counter, loss_scale);
     const int tiles_x = (W + kGradBX - 1) / kGradBX, tiles_y = (H + kGradBY - 1) / kGradBY;
     const dim3 grid((unsigned)views.n, (unsigned)tiles_x, (unsigned)tiles_y);
     const size_t smem = (size_t)D * kGradThreads * sizeof(float);
@@ -205,8 +211,8 @@ rl_status rl_launch_grad(const void* M, rl_dtype dt, int D, int H, int W, const 
                                     : (sparse ? "grad_sparse_bf16" : "grad_dense_bf16");
     RLTraceScope ts(name, s);
 #define RL_GRAD_CASE(TM, SP, LS) \
-    launch_grad_t<TM, SP, LS>(M, D, H, W, views, images, img_level, grad_out, slots, G, inv_n, partials, tiles_x, \
-                              grid, smem, s)
+    launch_grad_t<TM, SP, LS>(M, D, H, W, views, images, img_level, grad_out, slots, G, inv_n, partials, loss_out, \
+                              counter, loss_scale, tiles_x, grid, smem, s)
     if (dt == RL_F32) {
         if (sparse) { if (mode_loss) RL_GRAD_CASE(float, true, true); else RL_GRAD_CASE(float, true, false); }
         else        { if (mode_loss) RL_GRAD_CASE(float, false, true); else RL_GRAD_CASE(float, false, false); }

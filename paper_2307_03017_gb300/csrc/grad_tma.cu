@@ -42,7 +42,8 @@ __global__ void __launch_bounds__(NT, 3)
 k_grad_tma(const __grid_constant__ CUtensorMap tmap, const Tm* __restrict__ M, int D, int H, int W,
            const __grid_constant__ RLViews views, int tiles_x, const float* __restrict__ images, int img_level,
            const float* __restrict__ grad_out, const uint8_t* __restrict__ slots, float* __restrict__ G, float inv_n,
-           float* __restrict__ partials, unsigned int* __restrict__ status) {
+           float* __restrict__ partials, unsigned int* __restrict__ status, float* __restrict__ loss_out,
+           unsigned* __restrict__ counter, float loss_scale) {
     extern __shared__ __align__(128) unsigned char smem[];
     Tm* stage0 = reinterpret_cast<Tm*>(smem);
     Tm* stage1 = reinterpret_cast<Tm*>(smem + stage_bytes<Tm>());
@@ -232,18 +233,18 @@ k_grad_tma(const __grid_constant__ CUtensorMap tmap, const Tm* __restrict__ M, i
         lsum = rl_warp_sum(lsum);
         if ((tid & 31) == 0) scratch[tid >> 5] = lsum;
         __syncthreads();
-        if (tid == 0) {
-            float s = 0.f;
-            for (int i = 0; i < NT / 32; ++i) s += scratch[i];
-            partials[blockIdx.x] = s;
-        }
+        float blk = 0.f;
+        if (tid == 0)
+            for (int i = 0; i < NT / 32; ++i) blk += scratch[i];
+        __syncthreads();
+        rl_loss_epilogue(blk, partials, blockIdx.x, gridDim.x, loss_out, counter, loss_scale, tid, NT, scratch);
     }
 }
 
 template <typename Tm, bool SPARSE, bool LOSS>
 void launch_t(const CUtensorMap& tmap, const void* M, int D, int H, int W, const RLViews& views, const float* images,
               int img_level, const float* grad_out, const uint8_t* slots, float* G, float inv_n, float* partials,
-              unsigned int* status, cudaStream_t s) {
+              unsigned int* status, float* loss_out, unsigned* counter, float loss_scale, cudaStream_t s) {
     auto kern = k_grad_tma<Tm, SPARSE, LOSS>;
     const size_t smem = grad_smem_bytes<Tm>(D);
     static size_t configured = 0;
@@ -254,7 +255,7 @@ void launch_t(const CUtensorMap& tmap, const void* M, int D, int H, int W, const
     const int tiles_x = (W + TX - 1) / TX, tiles_y = (H + TY - 1) / TY;
     const unsigned blocks = (unsigned)(tiles_x * tiles_y * views.n);
     kern<<<blocks, NT, smem, s>>>(tmap, (const Tm*)M, D, H, W, views, tiles_x, images, img_level, grad_out, slots, G,
-                                  inv_n, partials, status);
+                                  inv_n, partials, status, loss_out, counter, loss_scale);
 }
 
 }  // namespace
@@ -266,7 +267,7 @@ size_t rl_grad_tma_num_blocks(int H, int W, int N) {
 rl_status rl_launch_grad_tma(const CUtensorMap& tmap, const void* M, rl_dtype dt, int D, int H, int W,
                              const RLViews& views, bool mode_loss, const float* images, int img_level,
                              const float* grad_out, const uint8_t* slots, float* G, float inv_n, float* partials,
-                             int* nblocks, cudaStream_t s) {
+                             int* nblocks, cudaStream_t s, float* loss_out, unsigned* counter, float loss_scale) {
     unsigned int* status = rl_device_status_ptr();
     if (!status) return rl_fail(RL_ECUDA, "device status word unavailable");
     if (nblocks) *nblocks = (int)rl_grad_tma_num_blocks(H, W, views.n);
@@ -275,7 +276,8 @@ rl_status rl_launch_grad_tma(const CUtensorMap& tmap, const void* M, rl_dtype dt
                                     : (sparse ? "grad_sparse_bf16" : "grad_dense_bf16");
     RLTraceScope ts(name, s);
 #define RL_CASE(TM, SP, LS) \
-    launch_t<TM, SP, LS>(tmap, M, D, H, W, views, images, img_level, grad_out, slots, G, inv_n, partials, status, s)
+    launch_t<TM, SP, LS>(tmap, M, D, H, W, views, images, img_level, grad_out, slots, G, inv_n, partials, status, \
+                         loss_out, counter, loss_scale, s)
     if (dt == RL_F32) {
         if (sparse) { if (mode_loss) RL_CASE(float, true, true); else RL_CASE(float, true, false); }
         else        { if (mode_loss) RL_CASE(float, false, true); else RL_CASE(float, false, false); }

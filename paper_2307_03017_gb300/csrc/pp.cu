@@ -160,7 +160,8 @@ template <typename Tm, int C, int kGroups, bool SPARSE, bool LOSS>
 __global__ void __launch_bounds__(kGroups * kPix)
 k_grad_pp(const Tm* __restrict__ M, int D, int H, int W, const __grid_constant__ RLViews views, int tiles_x,
           const float* __restrict__ images, int img_level, const float* __restrict__ grad_out,
-          const uint8_t* __restrict__ slots, float* __restrict__ G, float inv_n, float* __restrict__ partials) {
+          const uint8_t* __restrict__ slots, float* __restrict__ G, float inv_n, float* __restrict__ partials,
+          float* __restrict__ loss_out, unsigned* __restrict__ counter, float loss_scale) {
     __shared__ float4 xch[kGroups][kPix];
     __shared__ float red[kGroups];
     const PixelCoord pc = pixel_coord(H, W);
@@ -268,11 +269,13 @@ k_grad_pp(const Tm* __restrict__ M, int D, int H, int W, const __grid_constant__
         lsum = rl_warp_sum(lsum);
         if (pc.lane == 0) red[pc.g] = lsum;
         __syncthreads();
-        if (threadIdx.x == 0) {
-            float s = 0.f;
-            for (int i = 0; i < kGroups; ++i) s += red[i];
-            partials[blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z)] = s;
-        }
+        float blk = 0.f;
+        if (threadIdx.x == 0)
+            for (int i = 0; i < kGroups; ++i) blk += red[i];
+        __syncthreads();
+        rl_loss_epilogue(blk, partials, blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z),
+                         gridDim.x * gridDim.y * gridDim.z, loss_out, counter, loss_scale, threadIdx.x,
+                         kGroups * kPix, red);
     }
 }
 
@@ -292,8 +295,10 @@ int groups_for(int D, int path) {
 template <typename Tm, bool SPARSE, bool LOSS>
 void launch_grad_pp_t(int G, int C, const void* M, int D, int H, int W, const RLViews& views, int tiles_x, dim3 grid,
                       const float* images, int img_level, const float* grad_out, const uint8_t* slots, float* G_,
-                      float inv_n, float* partials, cudaStream_t s) {
-#define RL_PP_ARGS (const Tm*)M, D, H, W, views, tiles_x, images, img_level, grad_out, slots, G_, inv_n, partials
+                      float inv_n, float* partials, float* loss_out, unsigned* counter, float loss_scale,
+                      cudaStream_t s) {
+#define RL_PP_ARGS (const Tm*)M, D, H, W, views, tiles_x, images, img_level, grad_out, slots, G_, inv_n, partials, \
+                   loss_out, counter, loss_scale
 #define RL_PP_LAUNCH(CC, GG) k_grad_pp<Tm, CC, GG, SPARSE, LOSS><<<grid, GG * kPix, 0, s>>>(RL_PP_ARGS)
     if (G == 4) {
         switch (C) {
@@ -345,7 +350,8 @@ size_t rl_grad_pp_num_blocks(int H, int W, int N) {
 
 rl_status rl_launch_grad_pp(const void* M, rl_dtype dt, int D, int H, int W, const RLViews& views, bool mode_loss,
                             const float* images, int img_level, const float* grad_out, const uint8_t* slots,
-                            float* G_out, float inv_n, float* partials, int* nblocks, cudaStream_t s) {
+                            float* G_out, float inv_n, float* partials, int* nblocks, cudaStream_t s,
+                            float* loss_out, unsigned* counter, float loss_scale) {
     const int tiles_x = (W + kTX - 1) / kTX;
     const dim3 grid((unsigned)views.n, (unsigned)tiles_x, (unsigned)((H + kTY - 1) / kTY));
     if (nblocks) *nblocks = (int)rl_grad_pp_num_blocks(H, W, views.n);
@@ -357,7 +363,7 @@ rl_status rl_launch_grad_pp(const void* M, rl_dtype dt, int D, int H, int W, con
     RLTraceScope ts(name, s);
 #define RL_CASE(TM, SP, LS) \
     launch_grad_pp_t<TM, SP, LS>(G, C, M, D, H, W, views, tiles_x, grid, images, img_level, grad_out, slots, G_out, \
-                                 inv_n, partials, s)
+                                 inv_n, partials, loss_out, counter, loss_scale, s)
     if (dt == RL_F32) {
         if (sparse) { if (mode_loss) RL_CASE(float, true, true); else RL_CASE(float, true, false); }
         else        { if (mode_loss) RL_CASE(float, false, true); else RL_CASE(float, false, false); }

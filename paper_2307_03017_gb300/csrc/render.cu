@@ -9,11 +9,14 @@
 namespace {
 
 constexpr int kRenderBX = 32, kRenderBY = 4;
+#ifndef RL_RENDER_MIN_BLOCKS
+#define RL_RENDER_MIN_BLOCKS 1  // no register cap: measured fastest
+#endif
 
 // Blocks are ordered view-fastest (grid x = view) so that the views of a tile, whose plane
 // footprints overlap, run together and share the MPI through L2.
 template <typename Tm>
-__global__ void __launch_bounds__(kRenderBX* kRenderBY)
+__global__ void __launch_bounds__(kRenderBX* kRenderBY, RL_RENDER_MIN_BLOCKS)
 k_render(const Tm* __restrict__ M, int D, int H, int W, const __grid_constant__ RLViews views, int tiles_x,
          float* __restrict__ out) {
     const int view = blockIdx.x;  // grid (views, tiles_x, tiles_y): views of a tile run together

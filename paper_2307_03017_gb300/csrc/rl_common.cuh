@@ -176,3 +176,36 @@ __device__ __forceinline__ float rl_warp_sum(float v) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     return v;
 }
+
+// Loss epilogue shared by the gradient kernels.  Thread `tid` 0 of every block passes the
+// block's partial sum `s`; it is stored at partials[bid].  When out != NULL the last block
+// to finish (counted on *counter, which must be 0 at launch and is reset to 0 here) adds
+// all nblocks partials in index order -- a fixed order, so the loss is deterministic -- and
+// writes out[0] = sum * scale.  `red` is shared scratch of nthreads / 32 floats.
+__device__ __forceinline__ void rl_loss_epilogue(float s, float* __restrict__ partials, unsigned bid, unsigned nblocks,
+                                                 float* __restrict__ out, unsigned* __restrict__ counter, float scale,
+                                                 int tid, int nthreads, float* red) {
+    __shared__ int rl_am_last;
+    if (tid == 0) {
+        partials[bid] = s;
+        rl_am_last = 0;
+        if (out) {
+            __threadfence();
+            rl_am_last = atomicAdd(counter, 1u) == nblocks - 1;
+        }
+    }
+    __syncthreads();
+    if (!rl_am_last) return;
+    __threadfence();
+    float acc = 0.f;
+    for (unsigned i = tid; i < nblocks; i += nthreads) acc += __ldcg(partials + i);
+    acc = rl_warp_sum(acc);
+    if ((tid & 31) == 0) red[tid >> 5] = acc;
+    __syncthreads();
+    if (tid == 0) {
+        float total = 0.f;
+        for (int wi = 0; wi < nthreads / 32; ++wi) total += red[wi];
+        out[0] = total * scale;
+        *counter = 0u;
+    }
+}

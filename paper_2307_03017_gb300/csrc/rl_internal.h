@@ -52,20 +52,24 @@ rl_status rl_launch_warp_offsets(int D, int H, int W, const RLViews& views, floa
 // images at level img_level, averaged on the fly) else from grad_out.  slots != NULL
 // (slot map [D][H][W], RL_SLOT_NONE where not kept): compact gradient [k][H][W][4]; else
 // dense [D][H][W][4].  partials: one float per block
-// (loss mode); returns the number of blocks through *nblocks.
+// (loss mode); returns the number of blocks through *nblocks.  With loss_out != NULL the
+// last block also writes loss_out[0] = loss_scale * (sum of the partials), counting blocks
+// on *counter (0 at launch, left at 0).
 rl_status rl_launch_grad(const void* M, rl_dtype dt, int D, int H, int W, const RLViews& views, bool mode_loss,
                          const float* images, int img_level, const float* grad_out, const uint8_t* slots, float* G,
-                         float inv_n, float* partials, int* nblocks, cudaStream_t s);
+                         float inv_n, float* partials, int* nblocks, cudaStream_t s, float* loss_out = nullptr,
+                         unsigned* counter = nullptr, float loss_scale = 0.f);
 // Largest number of loss partials any gradient kernel family writes.
 size_t rl_grad_num_blocks(int H, int W, int N);
 rl_status rl_launch_grad_tma(const CUtensorMap& tmap, const void* M, rl_dtype dt, int D, int H, int W,
                              const RLViews& views, bool mode_loss, const float* images, int img_level,
                              const float* grad_out, const uint8_t* slots, float* G, float inv_n, float* partials,
-                             int* nblocks, cudaStream_t s);
+                             int* nblocks, cudaStream_t s, float* loss_out, unsigned* counter, float loss_scale);
 size_t rl_grad_tma_num_blocks(int H, int W, int N);
 rl_status rl_launch_grad_pp(const void* M, rl_dtype dt, int D, int H, int W, const RLViews& views, bool mode_loss,
                             const float* images, int img_level, const float* grad_out, const uint8_t* slots, float* G,
-                            float inv_n, float* partials, int* nblocks, cudaStream_t s);
+                            float inv_n, float* partials, int* nblocks, cudaStream_t s, float* loss_out,
+                            unsigned* counter, float loss_scale);
 size_t rl_grad_pp_num_blocks(int H, int W, int N);
 rl_status rl_launch_render_pp(const void* M, rl_dtype dt, int D, int H, int W, const RLViews& views, float* out,
                               cudaStream_t s);
@@ -75,7 +79,8 @@ rl_status rl_launch_loss_reduce(const float* partials, int n, float scale, float
 // Outputs (each optional): S [k][h][w], mask [h][w], slot map [D][h][w]; Gzero
 // [k][h][w][4] is zeroed.
 rl_status rl_launch_select(const void* M, rl_dtype dt, const float* keys, int D, int h, int w, int k, uint8_t* S,
-                           uint64_t* mask, uint8_t* slots, float* Gzero, cudaStream_t s);
+                           uint64_t* mask, uint8_t* slots, float* Gzero, cudaStream_t s,
+                           unsigned* counter_zero = nullptr);
 // Level-l MPI Ml [D][H>>l][W>>l][4] = Down^l(M).
 rl_status rl_launch_pyramid(const void* M, rl_dtype dt, int D, int H, int W, int level, void* Ml, cudaStream_t s);
 // Slot map [D][h][w] from a selection mask [h][w].

@@ -23,9 +23,10 @@ template <typename Tm, bool FROM_KEYS, int KMAX>
 __global__ void __launch_bounds__(128)
 k_select(const Tm* __restrict__ M, const float* __restrict__ keys, int D, int h, int w, int k,
          uint8_t* __restrict__ S, uint64_t* __restrict__ mask_out, uint8_t* __restrict__ slots,
-         float* __restrict__ Gzero) {
+         float* __restrict__ Gzero, unsigned* __restrict__ counter_zero) {
     const long long hw = (long long)h * w;
     const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p == 0 && counter_zero) *counter_zero = 0u;  // block counter of the loss epilogue that follows
     if (p >= hw) return;
 
     constexpr bool SMALL = KMAX <= 8;
@@ -109,13 +110,15 @@ k_select(const Tm* __restrict__ M, const float* __restrict__ keys, int D, int h,
 
 template <typename Tm, bool FROM_KEYS>
 void launch_select_t(const void* M, const float* keys, int D, int h, int w, int k, uint8_t* S, uint64_t* mask,
-                     uint8_t* slots, float* Gzero, cudaStream_t s) {
+                     uint8_t* slots, float* Gzero, unsigned* counter_zero, cudaStream_t s) {
     const long long hw = (long long)h * w;
     const int blocks = (int)((hw + 127) / 128);
     if (k <= 8)
-        k_select<Tm, FROM_KEYS, 8><<<blocks, 128, 0, s>>>((const Tm*)M, keys, D, h, w, k, S, mask, slots, Gzero);
+        k_select<Tm, FROM_KEYS, 8><<<blocks, 128, 0, s>>>((const Tm*)M, keys, D, h, w, k, S, mask, slots, Gzero,
+                                                          counter_zero);
     else
-        k_select<Tm, FROM_KEYS, 64><<<blocks, 128, 0, s>>>((const Tm*)M, keys, D, h, w, k, S, mask, slots, Gzero);
+        k_select<Tm, FROM_KEYS, 64><<<blocks, 128, 0, s>>>((const Tm*)M, keys, D, h, w, k, S, mask, slots, Gzero,
+                                                           counter_zero);
 }
 
 template <typename Tm>
@@ -175,16 +178,16 @@ __global__ void k_downsample_f32(const float* __restrict__ x, int P, int H, int 
 }  // namespace
 
 rl_status rl_launch_select(const void* M, rl_dtype dt, const float* keys, int D, int h, int w, int k, uint8_t* S,
-                           uint64_t* mask, uint8_t* slots, float* Gzero, cudaStream_t s) {
+                           uint64_t* mask, uint8_t* slots, float* Gzero, cudaStream_t s, unsigned* counter_zero) {
     if (keys) {
         RLTraceScope ts("select_keys", s);
-        launch_select_t<float, true>(nullptr, keys, D, h, w, k, S, mask, slots, Gzero, s);
+        launch_select_t<float, true>(nullptr, keys, D, h, w, k, S, mask, slots, Gzero, counter_zero, s);
     } else if (dt == RL_F32) {
         RLTraceScope ts("select_f32", s);
-        launch_select_t<float, false>(M, nullptr, D, h, w, k, S, mask, slots, Gzero, s);
+        launch_select_t<float, false>(M, nullptr, D, h, w, k, S, mask, slots, Gzero, counter_zero, s);
     } else {
         RLTraceScope ts("select_bf16", s);
-        launch_select_t<__nv_bfloat16, false>(M, nullptr, D, h, w, k, S, mask, slots, Gzero, s);
+        launch_select_t<__nv_bfloat16, false>(M, nullptr, D, h, w, k, S, mask, slots, Gzero, counter_zero, s);
     }
     return rl_check_launch("select");
 }

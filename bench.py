@@ -48,6 +48,9 @@ def parse():
     ap.add_argument("--arena-gb", type=float, default=24.0, help="serve: device memory arena (GB)")
     ap.add_argument("--graphs", action="store_true", help="serve: replay captured CUDA graphs")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--graph", action="store_true", help="replay a captured CUDA graph of the step instead of "
+                    "launching its kernels directly (measured no faster: the tracer's event nodes cost what "
+                    "the launch gaps do)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-clocks", action="store_true")
     ap.add_argument("--seed", type=int, default=0)
@@ -207,10 +210,24 @@ def run_ours(args, world, rank, local):
         rl.reallife_refine(mpi, images, sc.src, k, sched, loss_per_iter=loss, ws=ws)
         rl.reallife_render(mpi, sc.novel, out=out)
 
-    for _ in range(args.warmup):
+    for _ in range(max(args.warmup, 1 if args.graph else 0)):  # kernels load before any capture
         M.copy_(M0)
         step()
     torch.cuda.synchronize()
+
+    graph = None
+    if args.graph:
+        # one step captured as a CUDA graph; the tracer puts event nodes around each kernel
+        rl.reallife_trace_enable(True)
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph):
+            step()
+        rl.reallife_trace_enable(False)
+        rl.reallife_trace_read()
+        M.copy_(M0)
+        graph.replay()  # first replay (untimed)
+        torch.cuda.synchronize()
+        rl.reallife_trace_read()
 
     clocks = ClockSampler(local) if not args.no_clocks else None
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
@@ -220,19 +237,32 @@ def run_ours(args, world, rank, local):
     torch.cuda.synchronize()
     if clocks:
         clocks.start()
-    rl.reallife_trace_enable(True)
+    trace = {}
+
+    def add_trace(tr):
+        for name, (n, ms) in tr.items():
+            c, t = trace.get(name, (0, 0.0))
+            trace[name] = (c + n, t + ms)
+
     rl.reallife_trace_read()  # reset counters
     for i in range(args.steps):
-        rl.reallife_trace_enable(False)  # reset + flush are not part of the step
-        M.copy_(M0)
+        M.copy_(M0)  # reset and L2 flush are not part of the step
         flush.fill_(i & 0xFF)
-        rl.reallife_trace_enable(True)
-        starts[i].record(stream)
-        step()
-        stops[i].record(stream)
+        if graph is not None:
+            starts[i].record(stream)
+            graph.replay()
+            stops[i].record(stream)
+            torch.cuda.synchronize()
+            add_trace(rl.reallife_trace_read())  # this replay's kernel durations
+        else:
+            rl.reallife_trace_enable(True)
+            starts[i].record(stream)
+            step()
+            stops[i].record(stream)
+            rl.reallife_trace_enable(False)
     torch.cuda.synchronize()
-    rl.reallife_trace_enable(False)
-    trace = rl.reallife_trace_read()
+    if graph is None:
+        add_trace(rl.reallife_trace_read())
     clk = clocks.stop() if clocks else None
     ms_steps = [a.elapsed_time(b) for a, b in zip(starts, stops)]
     total_ms = reduce_max(sum(ms_steps), dist, dev)
@@ -273,6 +303,11 @@ def run_ours(args, world, rank, local):
     step_bytes = step_algorithmic_bytes(cfg, sc, elt)
     kernels = {n: {"launches": c, "ms_per_step": round(t / args.steps, 4)} for n, (c, t) in sorted(trace.items())}
 
+    launch_mode = "direct" if graph is None else "CUDA graph replay of the step"
+    if graph is not None:
+        del graph
+        torch.cuda.synchronize()
+        rl.reallife_trace_release_captured()
     e2e = None
     if not args.no_e2e:
         e2e = run_e2e(args, rl, sc, cfg, dtype, dev, world, dist)
@@ -287,6 +322,7 @@ def run_ours(args, world, rank, local):
             "config": {"workload": f"{args.workload}: {sc.W}x{sc.H} D={sc.D} N={N} k={k} levels={list(sched)} "
                                    f"+ {len(sc.novel)} novel views", "storage": cfg["dtype"],
                        "kernel_path": args.kernel_path,
+                       "launch": launch_mode,
                        "l2": "flushed (512 MB write) before every timed step", "parallelism": f"replicas{world}"},
             "hbm_gbs_step": round(step_bytes / (total_ms / args.steps / 1e3) / 1e9, 1),
             "roofline": roofline, "kernels": kernels, "gpu_launches": int(launches),

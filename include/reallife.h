@@ -220,16 +220,21 @@ rl_status reallife_set_kernel_path(int path);
 rl_status reallife_device_status(int clear, unsigned int* flags_out);
 
 /* Host-side kernel tracing: when enabled, every kernel launch of this library is
- * bracketed by CUDA events on its stream and counted per kernel name. */
+ * bracketed by CUDA events on its stream and counted per kernel name.  Launches made
+ * while the stream is being captured into a CUDA graph are bracketed by external event
+ * nodes instead, which record on every replay of the graph. */
 rl_status reallife_trace_enable(int on);
 /* Synchronises the recorded events and reports, for up to `max` kernel names: name,
- * launch count and summed device milliseconds.  Resets the counters. */
+ * launch count and summed device milliseconds.  Resets the counters.  Captured launches
+ * contribute the durations of the most recent replay (read after every replay). */
 typedef struct {
     char name[48];
     long long launches;
     double total_ms;
 } rl_trace_entry;
 rl_status reallife_trace_read(rl_trace_entry* out, int max, int* n_out);
+/* Returns the events of captured launches to the tracer (call once their graphs are gone). */
+rl_status reallife_trace_release_captured(void);
 
 const char* reallife_strerror(rl_status s);
 /* Message of the most recent failure on the calling thread ("" if none). */

@@ -24,6 +24,7 @@ __all__ = [
     "reallife_sparse_update", "reallife_render_backward", "reallife_warp_offsets",
     "reallife_trace_enable", "reallife_trace_read", "reallife_strerror", "workspace", "library_path",
     "reallife_set_kernel_path", "reallife_device_status", "reallife_hsgd_step_noalloc",
+    "reallife_trace_release_captured",
 ]
 
 RealLifeError = _lib.RealLifeError
@@ -274,6 +275,11 @@ def reallife_trace_read() -> dict:
     n = ctypes.c_int()
     _lib.check("reallife_trace_read", _lib.lib().reallife_trace_read(arr, 64, ctypes.byref(n)))
     return {arr[i].name.decode(): (int(arr[i].launches), float(arr[i].total_ms)) for i in range(min(n.value, 64))}
+
+
+def reallife_trace_release_captured():
+    """Return the events of captured launches to the tracer (after their graphs are gone)."""
+    _lib.check("reallife_trace_release_captured", _lib.lib().reallife_trace_release_captured())
 
 
 def reallife_strerror(status: int) -> str:

@@ -18,7 +18,7 @@ EXPORTS = [
     "reallife_downsample_f32", "reallife_select", "reallife_select_keys", "reallife_loss_grad",
     "reallife_sparse_update", "reallife_render_backward", "reallife_warp_offsets", "reallife_trace_enable",
     "reallife_trace_read", "reallife_strerror", "reallife_last_error", "reallife_set_kernel_path",
-    "reallife_device_status", "reallife_hsgd_step_noalloc",
+    "reallife_device_status", "reallife_hsgd_step_noalloc", "reallife_trace_release_captured",
 ]
 
 
@@ -82,6 +82,7 @@ def _declare(lib):
         "reallife_render_backward": (c_int, [mpi_p, cam_p, c_int, vp, vp, vp]),
         "reallife_warp_offsets": (c_int, [mpi_p, cam_p, vp, vp]),
         "reallife_trace_enable": (c_int, [c_int]),
+        "reallife_trace_release_captured": (c_int, []),
         "reallife_trace_read": (c_int, [ctypes.POINTER(RlTraceEntry), c_int, ctypes.POINTER(c_int)]),
         "reallife_strerror": (ctypes.c_char_p, [c_int]),
         "reallife_set_kernel_path": (c_int, [c_int]),

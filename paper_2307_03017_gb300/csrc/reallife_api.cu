@@ -51,7 +51,8 @@ struct TracePending {
 };
 std::mutex g_tmu;
 bool g_trace_on = false;
-std::vector<TracePending> g_pending;
+std::vector<TracePending> g_pending;   // launches made outside stream capture, read once
+std::vector<TracePending> g_captured;  // launches captured into a graph, read after every replay
 std::vector<cudaEvent_t> g_free_events;
 std::vector<std::string> g_names;
 std::vector<long long> g_counts;
@@ -74,6 +75,17 @@ int name_index(const char* name) {
     g_counts.push_back(0);
     return (int)g_names.size() - 1;
 }
+
+bool capturing(cudaStream_t s) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return cs == cudaStreamCaptureStatusActive;
+}
+
+constexpr int kCapturedTag = 1 << 30;
 }  // namespace
 
 int rl_trace_begin(const char* name, cudaStream_t s) {
@@ -81,9 +93,15 @@ int rl_trace_begin(const char* name, cudaStream_t s) {
     if (!g_trace_on) return -1;
     TracePending p;
     p.name = name_index(name);
-    g_counts[p.name] += 1;
     p.a = take_event();
     p.b = take_event();
+    if (capturing(s)) {
+        // becomes an event-record node of the graph: it records on every replay
+        cudaEventRecordWithFlags(p.a, s, cudaEventRecordExternal);
+        g_captured.push_back(p);
+        return kCapturedTag | ((int)g_captured.size() - 1);
+    }
+    g_counts[p.name] += 1;
     cudaEventRecord(p.a, s);
     g_pending.push_back(p);
     return (int)g_pending.size() - 1;
@@ -92,7 +110,12 @@ int rl_trace_begin(const char* name, cudaStream_t s) {
 void rl_trace_end(int token, cudaStream_t s) {
     if (token < 0) return;
     std::lock_guard<std::mutex> lk(g_tmu);
-    if (token < (int)g_pending.size()) cudaEventRecord(g_pending[token].b, s);
+    if (token & kCapturedTag) {
+        const int i = token & ~kCapturedTag;
+        if (i < (int)g_captured.size()) cudaEventRecordWithFlags(g_captured[i].b, s, cudaEventRecordExternal);
+    } else if (token < (int)g_pending.size()) {
+        cudaEventRecord(g_pending[token].b, s);
+    }
 }
 
 extern "C" rl_status reallife_trace_enable(int on) {
@@ -114,6 +137,16 @@ extern "C" rl_status reallife_trace_read(rl_trace_entry* out, int max, int* n_ou
         g_free_events.push_back(p.b);
     }
     g_pending.clear();
+    // captured launches: the events hold the most recent replay's timestamps
+    for (const TracePending& p : g_captured) {
+        float t = 0.f;
+        if (cudaEventSynchronize(p.b) == cudaSuccess && cudaEventElapsedTime(&t, p.a, p.b) == cudaSuccess) {
+            ms[p.name] += t;
+            g_counts[p.name] += 1;
+        } else {
+            cudaGetLastError();  // not replayed yet
+        }
+    }
     int n = 0;
     for (size_t i = 0; i < g_names.size(); ++i) {
         if (g_counts[i] == 0) continue;
@@ -128,6 +161,16 @@ extern "C" rl_status reallife_trace_read(rl_trace_entry* out, int max, int* n_ou
     }
     if (n_out) *n_out = n;
     return st;
+}
+
+extern "C" rl_status reallife_trace_release_captured(void) {
+    std::lock_guard<std::mutex> lk(g_tmu);
+    for (const TracePending& p : g_captured) {
+        g_free_events.push_back(p.a);
+        g_free_events.push_back(p.b);
+    }
+    g_captured.clear();
+    return RL_OK;
 }
 
 // ------------------------------------------------------------------ geometry

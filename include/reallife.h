@@ -75,14 +75,26 @@ typedef struct {
     rl_camera ref;
 } rl_mpi;
 
-/* One HSGD iteration: keep k planes per pixel (Sec. 3.3 "Gradient Sparsification"),
- * step `lambda` (the analytic update of Sec. 3.1 read as descent), clamp the updated
- * values to [0,1] when clamp01 != 0, work at pyramid level `level`. */
+/* Selection criteria (Sec. 3.3 "Gradient Sparsification" and the ablation of Sec. 5.5). */
+typedef enum {
+    RL_SELECT_TOPK = 0, /* the k largest reference-view alpha weights A_d, ties to the lower d */
+    RL_SELECT_MVS = 1   /* MVS-sampling: the argmax of A_d (ties to the lower d) and its (k-1)/2
+                           neighbours on each side, i.e. k consecutive planes starting at
+                           argmax - floor((k-1)/2), shifted to stay within [0, D) */
+} rl_selection;
+
+/* One HSGD iteration: keep k planes per pixel chosen by `selection`, step `lambda` (the
+ * analytic update of Sec. 3.1 read as descent), clamp the updated values to [0,1] when
+ * clamp01 != 0, work at pyramid level `level`.  lambda_s > 0 adds the sparsity prior of
+ * Sec. 3.4 as the prior phi of Sec. 3.1: lambda_s dL_s/dalpha, L_s = mean over the D x H_l x
+ * W_l voxels of log(1.5 - |0.5 - alpha|), on the alphas of the level MPI. */
 typedef struct {
     int k;
     float lambda;
     int clamp01;
     int level;
+    int selection;  /* rl_selection */
+    float lambda_s;
 } rl_hsgd_params;
 
 /* Upper bounds checked on the host (also D*H*W < 2^29 voxels). */
@@ -158,14 +170,14 @@ rl_status reallife_downsample_f32(const float* x, int P, int H, int W, int C, in
                                   cudaStream_t stream);
 
 /* Selection on an MPI `m` (at whatever resolution it has): A_d = alpha_d prod_{j>d}
- * (1 - alpha_j) in FP32 at the reference view (Eq. eq_gradient), keep the k largest per
- * pixel, ties to the lower d (Sec. 3.3).  S device [k][H][W] uint8 (ascending), mask
- * device [H][W] uint64; either may be NULL. */
-rl_status reallife_select(const rl_mpi* m, int k, uint8_t* S, uint64_t* mask, cudaStream_t stream);
+ * (1 - alpha_j) in FP32 at the reference view (Eq. eq_gradient), then k planes per pixel by
+ * `selection` (rl_selection; Sec. 3.3).  S device [k][H][W] uint8 (ascending), mask device
+ * [H][W] uint64; either may be NULL. */
+rl_status reallife_select(const rl_mpi* m, int k, int selection, uint8_t* S, uint64_t* mask, cudaStream_t stream);
 
 /* Same selection from caller-supplied FP32 keys `keys` device [D][H][W]. */
-rl_status reallife_select_keys(const float* keys, int D, int H, int W, int k, uint8_t* S, uint64_t* mask,
-                               cudaStream_t stream);
+rl_status reallife_select_keys(const float* keys, int D, int H, int W, int k, int selection, uint8_t* S,
+                               uint64_t* mask, cudaStream_t stream);
 
 /* Photometric loss of N views of `m` against `images` (both at m's resolution) and its
  * gradient (warp + composite + loss + exact adjoint, Sec. 3.1/3.3):
@@ -183,7 +195,8 @@ rl_status reallife_loss_grad(const rl_mpi* m, const float* images, const rl_came
  * upsampling to full resolution): for every full-resolution pixel (y, x) and j < k,
  *   d = S[j][y>>level][x>>level];
  *   M[d][y][x] <- clamp01 ? clamp(M - lambda G[j][y>>level][x>>level], 0, 1) : M - lambda G.
- * S device [k][H_l][W_l] uint8, G device [k][H_l][W_l][4] FP32. */
+ * S device [k][H_l][W_l] uint8, G device [k][H_l][W_l][4] FP32.  No sparsity prior here
+ * (reallife_hsgd_step applies it). */
 rl_status reallife_sparse_update(rl_mpi* m, const uint8_t* S, const float* G, int k, int level, float lambda,
                                  int clamp01, cudaStream_t stream);
 

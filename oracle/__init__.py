@@ -69,6 +69,13 @@ def _load():
             lib.orc_down_levels.argtypes = [dp, i, i, i, i, i, dp]
             lib.orc_hsgd_step.argtypes = [dp, i, i, i, d, d, cam, dp, cam, i, i, d, i, i, u8p, u8p, dp]
             lib.orc_hsgd_step.restype = i
+            lib.orc_hsgd_step2.argtypes = [dp, i, i, i, d, d, cam, dp, cam, i, i, d, i, i, i, d, u8p, u8p, dp]
+            lib.orc_hsgd_step2.restype = i
+            lib.orc_select_mvs.argtypes = [dp, i, i, i, i, u8p, u64p]
+            lib.orc_sparsity_grad.argtypes = [d, i, i, i]
+            lib.orc_sparsity_grad.restype = d
+            lib.orc_sparsity_loss.argtypes = [dp, i, i, i]
+            lib.orc_sparsity_loss.restype = d
             lib.orc_gd_step.argtypes = [dp, i, i, i, d, d, cam, dp, cam, i, d, i, i, dp]
             lib.orc_gd_step.restype = i
             _lib = lib
@@ -184,6 +191,28 @@ def select_topk(A, k: int):
     return S, mask
 
 
+def select_mvs(A, k: int):
+    """MVS-sampling window: argmax plane (ties to lower d) and (k-1)/2 neighbours each side."""
+    A = _f64(A)
+    D, H, W = A.shape
+    S = np.empty((k, H, W), dtype=np.uint8)
+    mask = np.empty((H, W), dtype=np.uint64)
+    _load().orc_select_mvs(_ptr(A), D, H, W, k, _ptr(S, ctypes.c_uint8), _ptr(mask, ctypes.c_uint64))
+    return S, mask
+
+
+def sparsity_loss(M) -> float:
+    """L_s = mean log(1.5 - |0.5 - alpha|) over all voxels (Sec. 3.4)."""
+    M = _f64(M)
+    D, H, W, _ = M.shape
+    return _load().orc_sparsity_loss(_ptr(M), D, H, W)
+
+
+def sparsity_grad(alpha: float, D: int, H: int, W: int) -> float:
+    """dL_s/dalpha of one voxel."""
+    return _load().orc_sparsity_grad(float(alpha), D, H, W)
+
+
 def down(x, level: int) -> np.ndarray:
     """Down^l over the two spatial axes of ``x[P][H][W][C]`` (l successive 2x2 box averages)."""
     x = _f64(x)
@@ -194,8 +223,11 @@ def down(x, level: int) -> np.ndarray:
 
 
 def hsgd_step(M, near, far, ref, views, images, k: int, lam: float = 1.0, clamp: bool = True, level: int = 0,
-              S_pin=None):
-    """One HSGD iteration (Sec. 3.3) at ``level`` on a copy of ``M``: returns (M_new, loss, S)."""
+              S_pin=None, selection: int = 0, lambda_s: float = 0.0):
+    """One HSGD iteration (Sec. 3.3) at ``level`` on a copy of ``M``: returns (M_new, loss, S).
+
+    selection 0: top-k by the reference alpha weight; 1: MVS-sampling window.
+    lambda_s: weight of the sparsity prior L_s (Sec. 3.4) added to the descent direction."""
     M = _f64(M).copy()
     D, H, W, _ = M.shape
     images = _f64(images)
@@ -206,10 +238,10 @@ def hsgd_step(M, near, far, ref, views, images, k: int, lam: float = 1.0, clamp:
         pin = np.ascontiguousarray(S_pin, dtype=np.uint8)
         assert pin.shape == (k, h, w)
     L = ctypes.c_double()
-    rc = _load().orc_hsgd_step(_ptr(M), D, H, W, near, far, ctypes.byref(_cam(ref)), _ptr(images), _cams(views),
-                               len(views), k, lam, int(clamp), level,
-                               _ptr(pin, ctypes.c_uint8) if pin is not None else None, _ptr(S, ctypes.c_uint8),
-                               ctypes.byref(L))
+    rc = _load().orc_hsgd_step2(_ptr(M), D, H, W, near, far, ctypes.byref(_cam(ref)), _ptr(images), _cams(views),
+                                len(views), k, lam, int(clamp), level, int(selection), float(lambda_s),
+                                _ptr(pin, ctypes.c_uint8) if pin is not None else None, _ptr(S, ctypes.c_uint8),
+                                ctypes.byref(L))
     if rc:
         raise ValueError("oracle hsgd_step: invalid arguments")
     return M, L.value, S
@@ -229,12 +261,12 @@ def gd_step(M, near, far, ref, views, images, lam: float = 1.0, clamp: bool = Tr
 
 
 def refine(M, near, far, ref, views, images, k: int, schedule=(2, 1, 0), lam: float = 1.0, clamp: bool = True,
-           S_pins=None):
+           S_pins=None, selection: int = 0, lambda_s: float = 0.0):
     """HSGD refinement: one ``hsgd_step`` per entry of ``schedule``; returns (M, losses, selections)."""
     losses, sels = [], []
     for it, level in enumerate(schedule):
         M, L, S = hsgd_step(M, near, far, ref, views, images, k, lam, clamp, level,
-                            None if S_pins is None else S_pins[it])
+                            None if S_pins is None else S_pins[it], selection, lambda_s)
         losses.append(L)
         sels.append(S)
     return M, losses, sels

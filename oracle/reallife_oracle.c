@@ -303,6 +303,48 @@ void orc_select_topk(const double* A, int D, int H, int W, int k, uint8_t* S, ui
     free(order);
 }
 
+/*
+ * MVS-sampling selection (the ablation alternative of Sec. 3.3 and Sec. 5.5): the plane
+ * with the largest key (ties to the lower index) and its (k-1)/2 neighbours on each side,
+ * i.e. the k consecutive planes starting at argmax - floor((k-1)/2), shifted to stay in
+ * [0, D).  S ascending, mask with bit d per kept plane.
+ */
+void orc_select_mvs(const double* A, int D, int H, int W, int k, uint8_t* S, uint64_t* mask) {
+    for (int y = 0; y < H; ++y)
+        for (int x = 0; x < W; ++x) {
+            size_t p = (size_t)y * W + x;
+            int best = 0;
+            for (int d = 1; d < D; ++d)
+                if (A[(size_t)d * H * W + p] > A[(size_t)best * H * W + p]) best = d;
+            int start = best - (k - 1) / 2;
+            if (start > D - k) start = D - k;
+            if (start < 0) start = 0;
+            uint64_t mk = 0;
+            for (int j = 0; j < k; ++j) {
+                mk |= (uint64_t)1 << (start + j);
+                S[(size_t)j * H * W + p] = (uint8_t)(start + j);
+            }
+            mask[p] = mk;
+        }
+}
+
+/*
+ * Gradient of the sparsity loss of Sec. 3.4, L_s = mean_{h,w,d} log(1.5 - |0.5 - alpha|),
+ * with respect to one alpha of an MPI of D x H x W voxels:
+ *   dL_s/dalpha = sign(0.5 - alpha) / ((1.5 - |0.5 - alpha|) H W D)   (0 at alpha = 0.5).
+ */
+double orc_sparsity_grad(double alpha, int D, int H, int W) {
+    double s = (alpha < 0.5) ? 1.0 : (alpha > 0.5 ? -1.0 : 0.0);
+    return s / ((1.5 - fabs(0.5 - alpha)) * (double)H * W * D);
+}
+
+/* L_s itself (mean of log(1.5 - |0.5 - alpha|) over all voxels). */
+double orc_sparsity_loss(const double* M, int D, int H, int W) {
+    double acc = 0.0;
+    for (size_t v = 0; v < (size_t)D * H * W; ++v) acc += log(1.5 - fabs(0.5 - M[v * 4 + 3]));
+    return acc / ((double)D * H * W);
+}
+
 /* ------------------------------------------------------------------ pyramid */
 
 /* 2x2 box average of P stacked [H][W][C] slices -> [H/2][W/2][C]. */
@@ -347,14 +389,16 @@ static double clamp01(double v) { return v < 0.0 ? 0.0 : (v > 1.0 ? 1.0 : v); }
  * One HSGD iteration at pyramid level `level` (Sec. 3.3), updating the full-resolution
  * MPI in place:
  *   M_l = Down^l(M), I_l = Down^l(I), cameras at level l;
- *   S   = top-k of A(M_l) (or S_pin when given);
+ *   S   = top-k of A(M_l) (selection 0), the MVS-sampling window (selection 1), or S_pin;
+ *   g  += lambda_s dL_s/dalpha on the alphas of M_l (the sparsity prior, when lambda_s != 0);
  *   g   = dL/dM_l (dense);
  *   M[d][Y][X] <- clamp(M[d][Y][X] - lambda g[d][Y>>l][X>>l]) for d in S[.][Y>>l][X>>l].
  * S_out (optional) receives the selection [k][H_l][W_l]; loss_out the loss at level l.
  */
-int orc_hsgd_step(double* M, int D, int H, int W, double near_, double far_, const orc_camera* ref,
-                  const double* images, const orc_camera* views, int N, int k, double lambda, int clamp,
-                  int level, const uint8_t* S_pin, uint8_t* S_out, double* loss_out) {
+int orc_hsgd_step2(double* M, int D, int H, int W, double near_, double far_, const orc_camera* ref,
+                   const double* images, const orc_camera* views, int N, int k, double lambda, int clamp,
+                   int level, int selection, double lambda_s, const uint8_t* S_pin, uint8_t* S_out,
+                   double* loss_out) {
     if (k < 1 || k > D || D > 64 || (H % (1 << level)) || (W % (1 << level))) return 1;
     int h = H >> level, w = W >> level;
     double* Ml = down_levels(M, D, H, W, 4, level);
@@ -371,12 +415,19 @@ int orc_hsgd_step(double* M, int D, int H, int W, double near_, double far_, con
         double* A = (double*)malloc(sizeof(double) * (size_t)D * h * w);
         uint64_t* mk = (uint64_t*)malloc(sizeof(uint64_t) * (size_t)h * w);
         orc_alpha_weights(Ml, D, h, w, A);
-        orc_select_topk(A, D, h, w, k, S, mk);
+        if (selection == 1)
+            orc_select_mvs(A, D, h, w, k, S, mk);
+        else
+            orc_select_topk(A, D, h, w, k, S, mk);
         free(mk);
         free(A);
     }
     double* g = (double*)malloc(sizeof(double) * (size_t)D * h * w * 4);
     double L = orc_loss_grad(Ml, D, h, w, near_, far_, &refl, Il, vl, N, g, NULL);
+    /* prior phi = lambda_s L_s on the level-l MPI (Sec. 3.1's dphi/df with L_s of Sec. 3.4) */
+    if (lambda_s != 0.0)
+        for (size_t v = 0; v < (size_t)D * h * w; ++v)
+            g[v * 4 + 3] += lambda_s * orc_sparsity_grad(Ml[v * 4 + 3], D, h, w);
     for (int yy = 0; yy < h; ++yy)
         for (int xx = 0; xx < w; ++xx)
             for (int j = 0; j < k; ++j) {
@@ -398,6 +449,13 @@ int orc_hsgd_step(double* M, int D, int H, int W, double near_, double far_, con
     free(Il);
     free(Ml);
     return 0;
+}
+
+int orc_hsgd_step(double* M, int D, int H, int W, double near_, double far_, const orc_camera* ref,
+                  const double* images, const orc_camera* views, int N, int k, double lambda, int clamp,
+                  int level, const uint8_t* S_pin, uint8_t* S_out, double* loss_out) {
+    return orc_hsgd_step2(M, D, H, W, near_, far_, ref, images, views, N, k, lambda, clamp, level, 0, 0.0, S_pin,
+                          S_out, loss_out);
 }
 
 /*

@@ -29,6 +29,7 @@ __all__ = [
 
 RealLifeError = _lib.RealLifeError
 F32, BF16 = 0, 1
+SELECT_TOPK, SELECT_MVS = 0, 1
 _DT = {torch.float32: F32, torch.bfloat16: BF16}
 
 
@@ -105,9 +106,10 @@ def _check_f32(t: torch.Tensor, shape, name):
         raise ValueError(f"{name} must be float32 {tuple(shape)}, got {t.dtype} {tuple(t.shape)}")
 
 
-def _params(k, lam, clamp, level) -> _lib.RlHsgdParams:
+def _params(k, lam, clamp, level, selection=SELECT_TOPK, lambda_s=0.0) -> _lib.RlHsgdParams:
     p = _lib.RlHsgdParams()
     p.k, p.lambda_, p.clamp01, p.level = int(k), float(lam), int(bool(clamp)), int(level)
+    p.selection, p.lambda_s = int(selection), float(lambda_s)
     return p
 
 
@@ -137,14 +139,15 @@ def reallife_render(m: Mpi, cams, out: torch.Tensor | None = None, stream=None) 
 
 def reallife_hsgd_step(m: Mpi, images: torch.Tensor, src, k: int, lam: float = 1.0, clamp: bool = True,
                        level: int = 0, loss_out: torch.Tensor | None = None, S_out: torch.Tensor | None = None,
-                       ws: torch.Tensor | None = None, stream=None):
+                       ws: torch.Tensor | None = None, stream=None, selection: int = SELECT_TOPK,
+                       lambda_s: float = 0.0):
     """One HSGD iteration on ``m`` in place; returns (loss_out, S_out)."""
     N = len(src)
     _check_f32(images, (N, m.H, m.W, 3), "images")
     if ws is None:
         ws = workspace(N, m.D, m.H, m.W, k, m.data.dtype, m.data.device)
     ms = m.c_struct()
-    p = _params(k, lam, clamp, level)
+    p = _params(k, lam, clamp, level, selection, lambda_s)
     _lib.check("reallife_hsgd_step", _lib.lib().reallife_hsgd_step(
         ctypes.byref(ms), _ptr(images), _lib.cameras(src), N, ctypes.byref(p), _ptr(loss_out), _ptr(S_out),
         _ptr(ws), ws.numel(), _stream(stream)))
@@ -153,14 +156,15 @@ def reallife_hsgd_step(m: Mpi, images: torch.Tensor, src, k: int, lam: float = 1
 
 def reallife_hsgd_step_noalloc(m: Mpi, images: torch.Tensor, src, k: int, lam: float = 1.0, clamp: bool = True,
                                level: int = 0, loss_out: torch.Tensor | None = None,
-                               S_out: torch.Tensor | None = None, stream=None):
+                               S_out: torch.Tensor | None = None, stream=None, selection: int = SELECT_TOPK,
+                               lambda_s: float = 0.0):
     """One HSGD iteration without a caller workspace (for callers that cannot allocate):
     the library's fixed per-device scratch array is used instead.  Same results as
     ``reallife_hsgd_step``; calls that overlap on the GPU race on the shared array."""
     N = len(src)
     _check_f32(images, (N, m.H, m.W, 3), "images")
     ms = m.c_struct()
-    p = _params(k, lam, clamp, level)
+    p = _params(k, lam, clamp, level, selection, lambda_s)
     _lib.check("reallife_hsgd_step_noalloc", _lib.lib().reallife_hsgd_step_noalloc(
         ctypes.byref(ms), _ptr(images), _lib.cameras(src), N, ctypes.byref(p), _ptr(loss_out), _ptr(S_out),
         _stream(stream)))
@@ -169,7 +173,7 @@ def reallife_hsgd_step_noalloc(m: Mpi, images: torch.Tensor, src, k: int, lam: f
 
 def reallife_refine(m: Mpi, images: torch.Tensor, src, k: int, schedule=(2, 1, 0), lam: float = 1.0,
                     clamp: bool = True, loss_per_iter: torch.Tensor | None = None, ws: torch.Tensor | None = None,
-                    stream=None):
+                    stream=None, selection: int = SELECT_TOPK, lambda_s: float = 0.0):
     """HSGD refinement of ``m`` in place over the level schedule; returns ``loss_per_iter``."""
     N = len(src)
     _check_f32(images, (N, m.H, m.W, 3), "images")
@@ -177,7 +181,7 @@ def reallife_refine(m: Mpi, images: torch.Tensor, src, k: int, schedule=(2, 1, 0
         ws = workspace(N, m.D, m.H, m.W, k, m.data.dtype, m.data.device)
     sched = (ctypes.c_int * len(schedule))(*[int(s) for s in schedule])
     ms = m.c_struct()
-    p = _params(k, lam, clamp, 0)
+    p = _params(k, lam, clamp, 0, selection, lambda_s)
     _lib.check("reallife_refine", _lib.lib().reallife_refine(
         ctypes.byref(ms), _ptr(images), _lib.cameras(src), N, ctypes.byref(p), sched, len(schedule),
         _ptr(loss_per_iter), _ptr(ws), ws.numel(), _stream(stream)))
@@ -194,28 +198,30 @@ def reallife_downsample_f32(x: torch.Tensor, level: int, out: torch.Tensor | Non
     return out
 
 
-def reallife_select(m: Mpi, k: int, S: torch.Tensor | None = None, mask: torch.Tensor | None = None, stream=None):
-    """Top-k planes per pixel by the reference-view alpha weight: (S uint8 [k][H][W], mask int64 [H][W])."""
+def reallife_select(m: Mpi, k: int, S: torch.Tensor | None = None, mask: torch.Tensor | None = None, stream=None,
+                    selection: int = SELECT_TOPK):
+    """k planes per pixel by the reference-view alpha weight (top-k or MVS-sampling window):
+    (S uint8 [k][H][W], mask int64 [H][W])."""
     dev = m.data.device
     if S is None:
         S = torch.empty((k, m.H, m.W), dtype=torch.uint8, device=dev)
     if mask is None:
         mask = torch.empty((m.H, m.W), dtype=torch.int64, device=dev)
     ms = m.c_struct()
-    _lib.check("reallife_select", _lib.lib().reallife_select(ctypes.byref(ms), k, _ptr(S), _ptr(mask),
+    _lib.check("reallife_select", _lib.lib().reallife_select(ctypes.byref(ms), k, int(selection), _ptr(S), _ptr(mask),
                                                             _stream(stream)))
     return S, mask
 
 
-def reallife_select_keys(keys: torch.Tensor, k: int, stream=None):
-    """Top-k of caller-supplied float32 keys ``[D][H][W]``: (S, mask)."""
+def reallife_select_keys(keys: torch.Tensor, k: int, stream=None, selection: int = SELECT_TOPK):
+    """Selection from caller-supplied float32 keys ``[D][H][W]``: (S, mask)."""
     D, H, W = keys.shape
     if keys.dtype != torch.float32:
         raise ValueError("keys must be float32")
     S = torch.empty((k, H, W), dtype=torch.uint8, device=keys.device)
     mask = torch.empty((H, W), dtype=torch.int64, device=keys.device)
-    _lib.check("reallife_select_keys", _lib.lib().reallife_select_keys(_ptr(keys), D, H, W, k, _ptr(S), _ptr(mask),
-                                                                      _stream(stream)))
+    _lib.check("reallife_select_keys", _lib.lib().reallife_select_keys(_ptr(keys), D, H, W, k, int(selection), _ptr(S),
+                                                                      _ptr(mask), _stream(stream)))
     return S, mask
 
 

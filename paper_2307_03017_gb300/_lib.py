@@ -36,7 +36,8 @@ class RlMpi(ctypes.Structure):
 
 
 class RlHsgdParams(ctypes.Structure):
-    _fields_ = [("k", ctypes.c_int), ("lambda_", ctypes.c_float), ("clamp01", ctypes.c_int), ("level", ctypes.c_int)]
+    _fields_ = [("k", ctypes.c_int), ("lambda_", ctypes.c_float), ("clamp01", ctypes.c_int), ("level", ctypes.c_int),
+                ("selection", ctypes.c_int), ("lambda_s", ctypes.c_float)]
 
 
 class RlTraceEntry(ctypes.Structure):
@@ -75,8 +76,8 @@ def _declare(lib):
         "reallife_refine": (c_int, [mpi_p, vp, cam_p, c_int, par_p, ctypes.POINTER(c_int), c_int, vp, vp, c_size_t,
                                     vp]),
         "reallife_downsample_f32": (c_int, [vp, c_int, c_int, c_int, c_int, c_int, vp, vp]),
-        "reallife_select": (c_int, [mpi_p, c_int, vp, vp, vp]),
-        "reallife_select_keys": (c_int, [vp, c_int, c_int, c_int, c_int, vp, vp, vp]),
+        "reallife_select": (c_int, [mpi_p, c_int, c_int, vp, vp, vp]),
+        "reallife_select_keys": (c_int, [vp, c_int, c_int, c_int, c_int, c_int, vp, vp, vp]),
         "reallife_loss_grad": (c_int, [mpi_p, vp, cam_p, c_int, vp, c_int, vp, vp, vp, c_size_t, vp]),
         "reallife_sparse_update": (c_int, [mpi_p, vp, vp, c_int, c_int, c_float, c_int, vp]),
         "reallife_render_backward": (c_int, [mpi_p, cam_p, c_int, vp, vp, vp]),

@@ -312,6 +312,9 @@ rl_status check_hsgd(const rl_mpi* m, const float* images, const rl_camera* src,
     if (!p) return rl_fail(RL_EINVAL, "params is NULL");
     if (p->k < 1 || p->k > m->D) return rl_fail(RL_EINVAL, "k=%d outside [1, D=%d]", p->k, m->D);
     if (!std::isfinite(p->lambda)) return rl_fail(RL_EINVAL, "lambda not finite");
+    if (p->selection != RL_SELECT_TOPK && p->selection != RL_SELECT_MVS)
+        return rl_fail(RL_EINVAL, "unknown selection %d", p->selection);
+    if (!std::isfinite(p->lambda_s) || p->lambda_s < 0.f) return rl_fail(RL_EINVAL, "lambda_s must be >= 0");
     if (level < 0 || level > 10 || (m->H % (1 << level)) || (m->W % (1 << level)))
         return rl_fail(RL_EINVAL, "level %d: H=%d and W=%d must be divisible by 2^level", level, m->H, m->W);
     if (!images) return rl_fail(RL_EINVAL, "images is NULL");
@@ -328,7 +331,8 @@ rl_status check_hsgd(const rl_mpi* m, const float* images, const rl_camera* src,
 
 // Enqueue one HSGD iteration (arguments already validated).
 rl_status enqueue_hsgd(rl_mpi* m, const float* images, const rl_camera* src, int N, int k, float lambda, int clamp01,
-                       int level, float* loss_out, uint8_t* S_out, void* ws, cudaStream_t s) {
+                       int level, int selection, float lambda_s, float* loss_out, uint8_t* S_out, void* ws,
+                       cudaStream_t s) {
     const WsLayout L = ws_layout(N, m->D, m->H, m->W, k, m->dtype);
     char* base = (char*)ws;
     const int h = m->H >> level, w = m->W >> level;
@@ -345,7 +349,7 @@ rl_status enqueue_hsgd(rl_mpi* m, const float* images, const rl_camera* src, int
         st = rl_launch_pyramid(m->data, m->dtype, m->D, m->H, m->W, level, Ml, s);
         if (st) return st;
     }
-    st = rl_launch_select(Ml, m->dtype, nullptr, m->D, h, w, k, S, nullptr, slots, G, s, counter);
+    st = rl_launch_select(Ml, m->dtype, nullptr, m->D, h, w, k, S, nullptr, slots, G, s, counter, selection);
     if (st) return st;
     int nb = 0;
     // the gradient kernel's last block reduces the loss partials (fixed order) into loss_out
@@ -353,7 +357,7 @@ rl_status enqueue_hsgd(rl_mpi* m, const float* images, const rl_camera* src, int
     st = rl_launch_grad(Ml, m->dtype, m->D, h, w, views, true, images, level, nullptr, slots, G, 1.0f / (float)N,
                         partials, &nb, s, loss_out, counter, 0.5f / (float)N);
     if (st) return st;
-    return rl_launch_update(m->data, m->dtype, m->D, m->H, m->W, level, S, G, k, lambda, clamp01, s);
+    return rl_launch_update(m->data, m->dtype, m->D, m->H, m->W, level, S, G, k, lambda, clamp01, s, Ml, lambda_s);
 }
 
 __global__ void k_zero(float4* __restrict__ p, size_t n4) {
@@ -401,7 +405,8 @@ extern "C" rl_status reallife_hsgd_step(rl_mpi* m, const float* images, const rl
                                         size_t ws_bytes, cudaStream_t stream) {
     rl_status st = check_hsgd(m, images, src, N, p, p ? p->level : 0, ws, ws_bytes);
     if (st) return st;
-    return enqueue_hsgd(m, images, src, N, p->k, p->lambda, p->clamp01, p->level, loss_out, S_out, ws, stream);
+    return enqueue_hsgd(m, images, src, N, p->k, p->lambda, p->clamp01, p->level, p->selection, p->lambda_s, loss_out,
+                        S_out, ws, stream);
 }
 
 extern "C" rl_status reallife_refine(rl_mpi* m, const float* images, const rl_camera* src, int N,
@@ -413,8 +418,8 @@ extern "C" rl_status reallife_refine(rl_mpi* m, const float* images, const rl_ca
         if (st) return st;
     }
     for (int it = 0; it < iters; ++it) {
-        rl_status st = enqueue_hsgd(m, images, src, N, p->k, p->lambda, p->clamp01, schedule[it],
-                                    loss_per_iter ? loss_per_iter + it : nullptr, nullptr, ws, stream);
+        rl_status st = enqueue_hsgd(m, images, src, N, p->k, p->lambda, p->clamp01, schedule[it], p->selection,
+                                    p->lambda_s, loss_per_iter ? loss_per_iter + it : nullptr, nullptr, ws, stream);
         if (st) return st;
     }
     return RL_OK;
@@ -428,19 +433,24 @@ extern "C" rl_status reallife_downsample_f32(const float* x, int P, int H, int W
     return rl_launch_downsample_f32(x, P, H, W, C, level, y, stream);
 }
 
-extern "C" rl_status reallife_select(const rl_mpi* m, int k, uint8_t* S, uint64_t* mask, cudaStream_t stream) {
+extern "C" rl_status reallife_select(const rl_mpi* m, int k, int selection, uint8_t* S, uint64_t* mask,
+                                     cudaStream_t stream) {
     rl_status st = check_mpi(m);
     if (st) return st;
     if (k < 1 || k > m->D) return rl_fail(RL_EINVAL, "k=%d outside [1, D=%d]", k, m->D);
+    if (selection != RL_SELECT_TOPK && selection != RL_SELECT_MVS)
+        return rl_fail(RL_EINVAL, "unknown selection %d", selection);
     if (!S && !mask) return rl_fail(RL_EINVAL, "select: no output");
-    return rl_launch_select(m->data, m->dtype, nullptr, m->D, m->H, m->W, k, S, mask, nullptr, nullptr, stream);
+    return rl_launch_select(m->data, m->dtype, nullptr, m->D, m->H, m->W, k, S, mask, nullptr, nullptr, stream,
+                            nullptr, selection);
 }
 
-extern "C" rl_status reallife_select_keys(const float* keys, int D, int H, int W, int k, uint8_t* S, uint64_t* mask,
-                                          cudaStream_t stream) {
-    if (!keys || D < 1 || D > RL_MAX_PLANES || H < 1 || W < 1 || k < 1 || k > D || (!S && !mask))
+extern "C" rl_status reallife_select_keys(const float* keys, int D, int H, int W, int k, int selection, uint8_t* S,
+                                          uint64_t* mask, cudaStream_t stream) {
+    if (!keys || D < 1 || D > RL_MAX_PLANES || H < 1 || W < 1 || k < 1 || k > D || (!S && !mask) ||
+        (selection != RL_SELECT_TOPK && selection != RL_SELECT_MVS))
         return rl_fail(RL_EINVAL, "select_keys: bad arguments");
-    return rl_launch_select(nullptr, RL_F32, keys, D, H, W, k, S, mask, nullptr, nullptr, stream);
+    return rl_launch_select(nullptr, RL_F32, keys, D, H, W, k, S, mask, nullptr, nullptr, stream, nullptr, selection);
 }
 
 extern "C" rl_status reallife_loss_grad(const rl_mpi* m, const float* images, const rl_camera* src, int N,
@@ -572,5 +582,6 @@ extern "C" rl_status reallife_hsgd_step_noalloc(rl_mpi* m, const float* images, 
     if (st) return st;
     // every part of the scratch this iteration reads is written earlier in the same
     // iteration (level MPI, selection, slot map; the select kernel zeroes the gradient slots)
-    return enqueue_hsgd(m, images, src, N, p->k, p->lambda, p->clamp01, p->level, loss_out, S_out, ws, stream);
+    return enqueue_hsgd(m, images, src, N, p->k, p->lambda, p->clamp01, p->level, p->selection, p->lambda_s, loss_out,
+                        S_out, ws, stream);
 }

@@ -80,12 +80,14 @@ rl_status rl_launch_loss_reduce(const float* partials, int n, float scale, float
 // [k][h][w][4] is zeroed.
 rl_status rl_launch_select(const void* M, rl_dtype dt, const float* keys, int D, int h, int w, int k, uint8_t* S,
                            uint64_t* mask, uint8_t* slots, float* Gzero, cudaStream_t s,
-                           unsigned* counter_zero = nullptr);
+                           unsigned* counter_zero = nullptr, int mode = 0);
 // Level-l MPI Ml [D][H>>l][W>>l][4] = Down^l(M).
 rl_status rl_launch_pyramid(const void* M, rl_dtype dt, int D, int H, int W, int level, void* Ml, cudaStream_t s);
 // Slot map [D][h][w] from a selection mask [h][w].
 rl_status rl_launch_mask_to_slots(const uint64_t* mask, int D, int hw, uint8_t* slots, cudaStream_t s);
 rl_status rl_launch_downsample_f32(const float* x, int P, int H, int W, int C, int level, float* y,
                                    cudaStream_t s);
+// With Ml (level MPI) and lambda_s != 0 the sparsity prior joins the alpha step.
 rl_status rl_launch_update(void* M, rl_dtype dt, int D, int H, int W, int level, const uint8_t* S, const float* G,
-                           int k, float lambda, int clamp01, cudaStream_t s);
+                           int k, float lambda, int clamp01, cudaStream_t s, const void* Ml = nullptr,
+                           float lambda_s = 0.f);

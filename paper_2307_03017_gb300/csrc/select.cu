@@ -13,6 +13,8 @@
 // slots of the pixel are zeroed for the adjoint that follows.
 //   k <= 8: a register-resident sorted list, one compare-exchange pass per plane.
 //   k  > 8: rank counting over the D keys (O(D^2) per pixel, kept in local memory).
+// MVS-sampling mode keeps instead the k consecutive planes around the argmax of the keys
+// (ties to the lower d), shifted to stay within [0, D).
 #include "rl_internal.h"
 
 namespace {
@@ -23,7 +25,7 @@ template <typename Tm, bool FROM_KEYS, int KMAX>
 __global__ void __launch_bounds__(128)
 k_select(const Tm* __restrict__ M, const float* __restrict__ keys, int D, int h, int w, int k,
          uint8_t* __restrict__ S, uint64_t* __restrict__ mask_out, uint8_t* __restrict__ slots,
-         float* __restrict__ Gzero, unsigned* __restrict__ counter_zero) {
+         float* __restrict__ Gzero, unsigned* __restrict__ counter_zero, int mode) {
     const long long hw = (long long)h * w;
     const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (p == 0 && counter_zero) *counter_zero = 0u;  // block counter of the loss epilogue that follows
@@ -40,6 +42,8 @@ k_select(const Tm* __restrict__ M, const float* __restrict__ keys, int D, int h,
     // keys are formed nearest plane first; the loads of 16 planes are issued together
     constexpr int kBatch = 16;
     float T = 1.f;
+    float best_key = -INFINITY;
+    int best = D - 1;
     for (int d0 = D - 1; d0 >= 0; d0 -= kBatch) {
         float raw[kBatch];
 #pragma unroll
@@ -62,6 +66,11 @@ k_select(const Tm* __restrict__ M, const float* __restrict__ keys, int D, int h,
                 T = T * (1.f - raw[u]);
             }
             if (!(key == key)) key = -INFINITY;  // NaN keys rank last
+            if (key >= best_key) {  // walking towards lower d: ties go to the lower plane
+                best_key = key;
+                best = d;
+            }
+            if (mode == 1) continue;
             if constexpr (SMALL) {
                 float cv = key;
                 int ci = d;
@@ -79,7 +88,11 @@ k_select(const Tm* __restrict__ M, const float* __restrict__ keys, int D, int h,
         }
     }
     uint64_t mk = 0;
-    if constexpr (SMALL) {
+    if (mode == 1) {
+        int start = best - (k - 1) / 2;
+        start = max(0, min(start, D - k));
+        mk = (k >= 64 ? ~0ull : ((1ull << k) - 1ull)) << start;
+    } else if constexpr (SMALL) {
 #pragma unroll
         for (int j = 0; j < KMAX; ++j)
             if (j < k) mk |= 1ull << ki[j];
@@ -110,15 +123,15 @@ k_select(const Tm* __restrict__ M, const float* __restrict__ keys, int D, int h,
 
 template <typename Tm, bool FROM_KEYS>
 void launch_select_t(const void* M, const float* keys, int D, int h, int w, int k, uint8_t* S, uint64_t* mask,
-                     uint8_t* slots, float* Gzero, unsigned* counter_zero, cudaStream_t s) {
+                     uint8_t* slots, float* Gzero, unsigned* counter_zero, int mode, cudaStream_t s) {
     const long long hw = (long long)h * w;
     const int blocks = (int)((hw + 127) / 128);
-    if (k <= 8)
+    if (k <= 8 || mode == 1)
         k_select<Tm, FROM_KEYS, 8><<<blocks, 128, 0, s>>>((const Tm*)M, keys, D, h, w, k, S, mask, slots, Gzero,
-                                                          counter_zero);
+                                                          counter_zero, mode);
     else
         k_select<Tm, FROM_KEYS, 64><<<blocks, 128, 0, s>>>((const Tm*)M, keys, D, h, w, k, S, mask, slots, Gzero,
-                                                           counter_zero);
+                                                           counter_zero, mode);
 }
 
 template <typename Tm>
@@ -178,16 +191,17 @@ __global__ void k_downsample_f32(const float* __restrict__ x, int P, int H, int 
 }  // namespace
 
 rl_status rl_launch_select(const void* M, rl_dtype dt, const float* keys, int D, int h, int w, int k, uint8_t* S,
-                           uint64_t* mask, uint8_t* slots, float* Gzero, cudaStream_t s, unsigned* counter_zero) {
+                           uint64_t* mask, uint8_t* slots, float* Gzero, cudaStream_t s, unsigned* counter_zero,
+                           int mode) {
     if (keys) {
         RLTraceScope ts("select_keys", s);
-        launch_select_t<float, true>(nullptr, keys, D, h, w, k, S, mask, slots, Gzero, counter_zero, s);
+        launch_select_t<float, true>(nullptr, keys, D, h, w, k, S, mask, slots, Gzero, counter_zero, mode, s);
     } else if (dt == RL_F32) {
         RLTraceScope ts("select_f32", s);
-        launch_select_t<float, false>(M, nullptr, D, h, w, k, S, mask, slots, Gzero, counter_zero, s);
+        launch_select_t<float, false>(M, nullptr, D, h, w, k, S, mask, slots, Gzero, counter_zero, mode, s);
     } else {
         RLTraceScope ts("select_bf16", s);
-        launch_select_t<__nv_bfloat16, false>(M, nullptr, D, h, w, k, S, mask, slots, Gzero, counter_zero, s);
+        launch_select_t<__nv_bfloat16, false>(M, nullptr, D, h, w, k, S, mask, slots, Gzero, counter_zero, mode, s);
     }
     return rl_check_launch("select");
 }

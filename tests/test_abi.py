@@ -92,4 +92,10 @@ def test_invalid_arguments_rejected_on_host(cpu_only):
     many = _lib.cameras([sg.Camera(sg.intrinsics(16, 16), np.eye(3), np.zeros(3))] * 17)
     assert lib.reallife_hsgd_step(ctypes.byref(m), img, many, 17, ctypes.byref(P), None, None, ws, 1 << 30,
                                   None) == 1
-    assert lib.reallife_select_keys(ctypes.c_void_p(4096), 4, 8, 8, 5, ctypes.c_void_p(4096), None, None) == 1
+    assert lib.reallife_select_keys(ctypes.c_void_p(4096), 4, 8, 8, 5, 0, ctypes.c_void_p(4096), None, None) == 1
+    assert lib.reallife_select_keys(ctypes.c_void_p(4096), 8, 8, 8, 5, 7, ctypes.c_void_p(4096), None, None) == 1
+    # unknown selection mode, negative prior weight
+    P.k, P.level, P.selection = 2, 0, 3
+    assert lib.reallife_hsgd_step(ctypes.byref(m), img, cams, 1, ctypes.byref(P), None, None, ws, 1 << 30, None) == 1
+    P.selection, P.lambda_s = 0, -1.0
+    assert lib.reallife_hsgd_step(ctypes.byref(m), img, cams, 1, ctypes.byref(P), None, None, ws, 1 << 30, None) == 1

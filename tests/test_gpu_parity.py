@@ -341,3 +341,38 @@ def test_bf16_odd_width_and_large_plane_counts(rl, D):
     M_o, L_o, _ = oracle.hsgd_step(Mq, sc.near, sc.far, sc.ref, sc.src, sc.images, 9, S_pin=S.cpu().numpy())
     assert np.abs(m.data.float().cpu().numpy() - M_o).max() <= TOL16
     assert abs(loss.item() - L_o) <= 1e-5 * L_o
+
+
+# ------------------------------------------- MVS-sampling selection and sparsity prior
+
+def test_mvs_selection_bit_exact_against_oracle(rl, small):
+    sc = small
+    M = sc.coarse_mpi.astype(np.float64).copy()
+    M[..., 3] = np.round(M[..., 3] * 8) / 8  # ties
+    keys32 = oracle.alpha_weights(M).astype(np.float32)
+    for k in (1, 3, 5, sc.D):
+        S_g, mask_g = rl.reallife_select_keys(_dev(keys32), k, selection=rl.SELECT_MVS)
+        S_o, mask_o = oracle.select_mvs(keys32.astype(np.float64), k)
+        assert np.array_equal(S_g.cpu().numpy(), S_o), k
+        assert np.array_equal(mask_g.cpu().numpy().view(np.uint64), mask_o), k
+
+
+@pytest.mark.parametrize("level", [0, 1])
+def test_hsgd_mvs_and_sparsity_prior_match_oracle(rl, small, level):
+    sc = small
+    k, lam_s = 3, 4000.0
+    for selection in (rl.SELECT_TOPK, rl.SELECT_MVS):
+        m = _mpi(rl, sc)
+        S = torch.empty((k, sc.H >> level, sc.W >> level), dtype=torch.uint8, device="cuda")
+        loss = torch.empty(1, dtype=torch.float32, device="cuda")
+        rl.reallife_hsgd_step(m, _dev(sc.images), sc.src, k, level=level, loss_out=loss, S_out=S, selection=selection,
+                              lambda_s=lam_s)
+        S = S.cpu().numpy()
+        M_o, L_o, _ = oracle.hsgd_step(sc.coarse_mpi, sc.near, sc.far, sc.ref, sc.src, sc.images, k, level=level,
+                                       S_pin=S, lambda_s=lam_s)
+        assert np.abs(m.data.cpu().numpy() - M_o).max() <= TOL32
+        if selection == rl.SELECT_MVS:
+            Ml = oracle.down(sc.coarse_mpi, level)
+            best = np.argmax(oracle.alpha_weights(Ml), axis=0)  # first maximum
+            assert np.all(np.diff(S.astype(int), axis=0) == 1)
+            assert np.mean(np.any(S == best[None], axis=0)) > 0.999  # FP32 vs FP64 near-ties aside

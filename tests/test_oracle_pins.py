@@ -399,3 +399,71 @@ def test_refinement_improves_novel_views():
     M, losses, _ = oracle.refine(sc.coarse_mpi, sc.near, sc.far, sc.ref, sc.src, sc.images, k=5,
                                  schedule=(2, 1, 0, 0, 0))
     assert err(M) < e0
+
+
+# ------------------------------------------------- MVS-sampling and sparsity prior
+
+def test_mvs_sampling_window_definition():
+    """Argmax plane (ties to the lower index) plus (k-1)/2 neighbours each side, shifted into [0, D)."""
+    rng = np.random.default_rng(14)
+    D, H, W = 9, 4, 5
+    keys = rng.choice([0.0, 0.1, 0.2, 0.5], size=(D, H, W))
+    keys[:, 0, 0] = 0.0                      # all tied: argmax = 0, window at the back
+    keys[:, 0, 1] = np.arange(D)             # argmax = D-1: window at the front
+    keys[4, 0, 2], keys[6, 0, 2] = 1.0, 1.0  # tie between 4 and 6: argmax 4
+    for k in (1, 3, 5, D):
+        S, mask = oracle.select_mvs(keys, k)
+        for y in range(H):
+            for x in range(W):
+                col = list(keys[:, y, x])
+                best = col.index(max(col))  # first maximum = lowest index
+                start = min(max(best - (k - 1) // 2, 0), D - k)
+                assert list(S[:, y, x]) == list(range(start, start + k))
+                assert best in S[:, y, x]
+                assert int(mask[y, x]) == sum(1 << d for d in range(start, start + k))
+    assert list(oracle.select_mvs(keys, 3)[0][:, 0, 0]) == [0, 1, 2]
+    assert list(oracle.select_mvs(keys, 3)[0][:, 0, 1]) == [D - 3, D - 2, D - 1]
+    assert list(oracle.select_mvs(keys, 3)[0][:, 0, 2]) == [3, 4, 5]
+
+
+def test_sparsity_prior_gradient_matches_finite_differences():
+    """dL_s/dalpha of Sec. 3.4's L_s = mean log(1.5 - |0.5 - alpha|), by central differences."""
+    rng = np.random.default_rng(15)
+    D, H, W = 3, 4, 5
+    M = rng.uniform(0.02, 0.98, size=(D, H, W, 4))
+    M[..., 3][np.abs(M[..., 3] - 0.5) < 0.02] = 0.3  # keep away from the kink
+    h = 1e-6
+    for idx in [(0, 0, 0), (1, 2, 3), (2, 3, 4), (0, 1, 2)]:
+        Mp, Mm = M.copy(), M.copy()
+        Mp[idx + (3,)] += h
+        Mm[idx + (3,)] -= h
+        fd = (oracle.sparsity_loss(Mp) - oracle.sparsity_loss(Mm)) / (2 * h)
+        assert abs(fd - oracle.sparsity_grad(M[idx + (3,)], D, H, W)) < 1e-8
+    # closed form at the ends: log(1) = 0 at alpha in {0, 1}, log(1.5) at 0.5
+    Z = np.zeros((1, 1, 1, 4))
+    assert oracle.sparsity_loss(Z) == 0.0
+    Z[..., 3] = 0.5
+    assert abs(oracle.sparsity_loss(Z) - np.log(1.5)) < 1e-15
+    assert oracle.sparsity_grad(0.5, 1, 1, 1) == 0.0
+
+
+def test_sparsity_prior_pushes_alpha_to_the_ends(tiny_scene):
+    """With only the prior (photometric step lambda = 0 would also freeze it, so use a huge
+    lambda_s and a tiny lambda), selected alphas below 0.5 fall and above 0.5 rise."""
+    sc = tiny_scene
+    M0 = sc.coarse_mpi.astype(np.float64)
+    M1, _, S = oracle.hsgd_step(M0, sc.near, sc.far, sc.ref, sc.src, sc.images, k=sc.D, lam=1e-12, clamp=False,
+                                lambda_s=1e12 * sc.D * sc.H * sc.W)
+    a0, a1 = M0[..., 3], M1[..., 3]
+    assert np.all(a1[a0 < 0.49] < a0[a0 < 0.49]) and np.all(a1[a0 > 0.51] > a0[a0 > 0.51])
+
+
+def test_hsgd_with_mvs_selection_updates_only_the_window(tiny_scene):
+    sc = tiny_scene
+    k = 3
+    M1, _, S = oracle.hsgd_step(sc.coarse_mpi, sc.near, sc.far, sc.ref, sc.src, sc.images, k=k, clamp=False,
+                                selection=1)
+    A = oracle.alpha_weights(sc.coarse_mpi)
+    S_want, _ = oracle.select_mvs(A, k)
+    assert np.array_equal(S, S_want)
+    assert np.all(np.diff(S.astype(int), axis=0) == 1)  # consecutive planes

@@ -345,11 +345,10 @@ rl_status enqueue_hsgd(rl_mpi* m, const float* images, const rl_camera* src, int
     RLViews views;
     rl_status st = make_views(m, src, N, level, views);
     if (st) return st;
-    if (level) {
-        st = rl_launch_pyramid(m->data, m->dtype, m->D, m->H, m->W, level, Ml, s);
-        if (st) return st;
-    }
-    st = rl_launch_select(Ml, m->dtype, nullptr, m->D, h, w, k, S, nullptr, slots, G, s, counter, selection);
+    // coarse levels: the pyramid and the selection share one pass over M
+    st = level ? rl_launch_pyramid_select(m->data, m->dtype, m->D, m->H, m->W, level, Ml, k, S, slots, G, counter,
+                                          selection, s)
+               : rl_launch_select(Ml, m->dtype, nullptr, m->D, h, w, k, S, nullptr, slots, G, s, counter, selection);
     if (st) return st;
     int nb = 0;
     // the gradient kernel's last block reduces the loss partials (fixed order) into loss_out

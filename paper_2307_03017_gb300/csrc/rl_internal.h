@@ -81,8 +81,11 @@ rl_status rl_launch_loss_reduce(const float* partials, int n, float scale, float
 rl_status rl_launch_select(const void* M, rl_dtype dt, const float* keys, int D, int h, int w, int k, uint8_t* S,
                            uint64_t* mask, uint8_t* slots, float* Gzero, cudaStream_t s,
                            unsigned* counter_zero = nullptr, int mode = 0);
-// Level-l MPI Ml [D][H>>l][W>>l][4] = Down^l(M).
-rl_status rl_launch_pyramid(const void* M, rl_dtype dt, int D, int H, int W, int level, void* Ml, cudaStream_t s);
+// Level-l MPI Ml [D][H>>l][W>>l][4] = Down^l(M) (level >= 1) and the selection on it in one pass: outputs as
+// rl_launch_select without the mask, identical values.
+rl_status rl_launch_pyramid_select(const void* M, rl_dtype dt, int D, int H, int W, int level, void* Ml, int k,
+                                   uint8_t* S, uint8_t* slots, float* Gzero, unsigned* counter_zero, int mode,
+                                   cudaStream_t s);
 // Slot map [D][h][w] from a selection mask [h][w].
 rl_status rl_launch_mask_to_slots(const uint64_t* mask, int D, int hw, uint8_t* slots, cudaStream_t s);
 rl_status rl_launch_downsample_f32(const float* x, int P, int H, int W, int C, int level, float* y,

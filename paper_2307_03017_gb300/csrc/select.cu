@@ -1,8 +1,8 @@
 // select.cu -- level pyramid of the MPI, the content-aligned top-k selection (Sec. 3.3
 // "Gradient Sparsification") and image/tensor box downsampling.
 //
-// Pyramid: one thread per level-l voxel, the mean of its 2^l x 2^l full-resolution voxels
-// (Sec. 3.2, hierarchical downsampling), rounded to the storage type.
+// Pyramid: each level-l voxel is the mean of its 2^l x 2^l full-resolution voxels (Sec. 3.2,
+// hierarchical downsampling), rounded to the storage type.
 //
 // Selection: one thread per pixel.  Walking the planes nearest first, it forms the
 // reference-view alpha weight A_d = alpha_d T_d (Eq. eq_gradient / eq_overA) with
@@ -11,33 +11,36 @@
 // index list S[j][p] in ascending depth order, and the slot map used by the adjoint
 // (slot j of plane S[j][p], RL_SLOT_NONE for the planes not kept); the compact gradient
 // slots of the pixel are zeroed for the adjoint that follows.
-//   k <= 8: a register-resident sorted list, one compare-exchange pass per plane.
+//   k <= 8: a register-resident sorted list (compiled for each k), entered only by planes
+//           whose key reaches its last entry.
 //   k  > 8: rank counting over the D keys (O(D^2) per pixel, kept in local memory).
 // MVS-sampling mode keeps instead the k consecutive planes around the argmax of the keys
 // (ties to the lower d), shifted to stay within [0, D).
+// On the coarse levels of an HSGD step the pyramid and the selection run as one kernel: the
+// level voxels of a tile of pixels go to Ml and, through shared memory, to the selection.
 #include "rl_internal.h"
 
 namespace {
 
 __device__ __forceinline__ bool beats(float a, int ia, float b, int ib) { return a > b || (a == b && ia < ib); }
 
-template <typename Tm, bool FROM_KEYS, int KMAX>
-__global__ void __launch_bounds__(128)
-k_select(const Tm* __restrict__ M, const float* __restrict__ keys, int D, int h, int w, int k,
-         uint8_t* __restrict__ S, uint64_t* __restrict__ mask_out, uint8_t* __restrict__ slots,
-         float* __restrict__ Gzero, unsigned* __restrict__ counter_zero, int mode) {
-    const long long hw = (long long)h * w;
-    const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p == 0 && counter_zero) *counter_zero = 0u;  // block counter of the loss epilogue that follows
-    if (p >= hw) return;
-
-    constexpr bool SMALL = KMAX <= 8;
-    float kv[SMALL ? KMAX : 1];
-    int ki[SMALL ? KMAX : 1];
+// Per-pixel selection.  raw_at(d) gives alpha_d (keys mode: the key of plane d).  Returns the
+// 64-bit mask of the kept planes.
+//   K <= 8: a register-resident list sorted by (key descending, d ascending).  The walk
+//   visits the planes in descending d, so a new plane is below every listed one and wins
+//   every tie: it enters iff key >= the last listed key, and the insertion is a chain of
+//   `>=` compare-exchanges.  Planes that cannot enter cost one comparison.
+//   K == 64: rank counting over the D keys (O(D^2), kept in local memory).
+// mode 1 (MVS sampling) keeps the k consecutive planes around the argmax of the keys.
+template <int K, bool FROM_KEYS, typename RawFn>
+__device__ __forceinline__ uint64_t select_mask(const RawFn& raw_at, int D, int k, int mode) {
+    constexpr bool SMALL = K <= 8;
+    float kv[SMALL ? K : 1];
+    int ki[SMALL ? K : 1];
     float allk[SMALL ? 1 : RL_DEV_MAX_PLANES];
     if constexpr (SMALL) {
 #pragma unroll
-        for (int j = 0; j < KMAX; ++j) { kv[j] = -INFINITY; ki[j] = 255; }
+        for (int j = 0; j < K; ++j) { kv[j] = -INFINITY; ki[j] = 255; }
     }
     // keys are formed nearest plane first; the loads of 16 planes are issued together
     constexpr int kBatch = 16;
@@ -49,10 +52,7 @@ k_select(const Tm* __restrict__ M, const float* __restrict__ keys, int D, int h,
 #pragma unroll
         for (int u = 0; u < kBatch; ++u) {
             const int d = d0 - u;
-            if constexpr (FROM_KEYS)
-                raw[u] = d >= 0 ? __ldg(keys + (size_t)d * hw + p) : 0.f;
-            else
-                raw[u] = d >= 0 ? RLStore<Tm>::load1(M + ((size_t)d * hw + p) * 4 + 3) : 0.f;
+            raw[u] = d >= 0 ? raw_at(d) : 0.f;
         }
 #pragma unroll
         for (int u = 0; u < kBatch; ++u) {
@@ -66,20 +66,24 @@ k_select(const Tm* __restrict__ M, const float* __restrict__ keys, int D, int h,
                 T = T * (1.f - raw[u]);
             }
             if (!(key == key)) key = -INFINITY;  // NaN keys rank last
-            if (key >= best_key) {  // walking towards lower d: ties go to the lower plane
-                best_key = key;
-                best = d;
+            if (mode == 1) {
+                if (key >= best_key) {  // walking towards lower d: ties go to the lower plane
+                    best_key = key;
+                    best = d;
+                }
+                continue;
             }
-            if (mode == 1) continue;
             if constexpr (SMALL) {
-                float cv = key;
-                int ci = d;
+                if (key >= kv[K - 1]) {
+                    float cv = key;
+                    int ci = d;
 #pragma unroll
-                for (int j = 0; j < KMAX; ++j) {
-                    if (j < k && beats(cv, ci, kv[j], ki[j])) {
-                        const float tv = kv[j]; const int ti = ki[j];
-                        kv[j] = cv; ki[j] = ci;
-                        cv = tv; ci = ti;
+                    for (int j = 0; j < K; ++j) {
+                        if (cv >= kv[j]) {
+                            const float tv = kv[j]; const int ti = ki[j];
+                            kv[j] = cv; ki[j] = ci;
+                            cv = tv; ci = ti;
+                        }
                     }
                 }
             } else {
@@ -94,8 +98,7 @@ k_select(const Tm* __restrict__ M, const float* __restrict__ keys, int D, int h,
         mk = (k >= 64 ? ~0ull : ((1ull << k) - 1ull)) << start;
     } else if constexpr (SMALL) {
 #pragma unroll
-        for (int j = 0; j < KMAX; ++j)
-            if (j < k) mk |= 1ull << ki[j];
+        for (int j = 0; j < K; ++j) mk |= 1ull << ki[j];
     } else {
         for (int d = 0; d < D; ++d) {
             int rank = 0;
@@ -103,6 +106,14 @@ k_select(const Tm* __restrict__ M, const float* __restrict__ keys, int D, int h,
             if (rank < k) mk |= 1ull << d;
         }
     }
+    return mk;
+}
+
+// Writes the selection of pixel p: mask, slot map, compact list S (ascending depth) and
+// zeroes the pixel's compact gradient slots.
+__device__ __forceinline__ void write_selection(uint64_t mk, int D, int k, long long hw, long long p,
+                                                uint8_t* __restrict__ S, uint64_t* __restrict__ mask_out,
+                                                uint8_t* __restrict__ slots, float* __restrict__ Gzero) {
     if (mask_out) mask_out[p] = mk;
     if (slots) {
         int j = 0;
@@ -121,41 +132,156 @@ k_select(const Tm* __restrict__ M, const float* __restrict__ keys, int D, int h,
     }
 }
 
+template <typename Tm, bool FROM_KEYS, int K>
+__global__ void __launch_bounds__(128)
+k_select(const Tm* __restrict__ M, const float* __restrict__ keys, int D, int h, int w, int k,
+         uint8_t* __restrict__ S, uint64_t* __restrict__ mask_out, uint8_t* __restrict__ slots,
+         float* __restrict__ Gzero, unsigned* __restrict__ counter_zero, int mode) {
+    const long long hw = (long long)h * w;
+    const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p == 0 && counter_zero) *counter_zero = 0u;  // block counter of the loss epilogue that follows
+    if (p >= hw) return;
+    const uint64_t mk = select_mask<K, FROM_KEYS>(
+        [&](int d) {
+            if constexpr (FROM_KEYS) return __ldg(keys + (size_t)d * hw + p);
+            else return RLStore<Tm>::load1(M + ((size_t)d * hw + p) * 4 + 3);
+        },
+        D, k, mode);
+    write_selection(mk, D, k, hw, p, S, mask_out, slots, Gzero);
+}
+
+// Mean of the 2^l x 2^l full-resolution voxels of level voxel (d, y, x), summed row by row.
+template <typename Tm, int LOG>
+__device__ __forceinline__ float4 pyramid_mean(const Tm* __restrict__ M, int H, int W, int level, int d, int y,
+                                               int x) {
+    const int s = LOG >= 0 ? (1 << LOG) : (1 << level);
+    const Tm* base = M + (((size_t)d * H + (size_t)y * s) * W + (size_t)x * s) * 4;
+    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+    if constexpr (LOG >= 0) {
+        constexpr int SS = 1 << LOG;
+        float4 v[SS * SS];
+#pragma unroll
+        for (int yy = 0; yy < SS; ++yy)
+#pragma unroll
+            for (int xx = 0; xx < SS; ++xx) v[yy * SS + xx] = RLStore<Tm>::load4(base + ((size_t)yy * W + xx) * 4);
+#pragma unroll
+        for (int i = 0; i < SS * SS; ++i) {
+            acc.x += v[i].x; acc.y += v[i].y; acc.z += v[i].z; acc.w += v[i].w;
+        }
+    } else {
+        for (int yy = 0; yy < s; ++yy)
+#pragma unroll 4
+            for (int xx = 0; xx < s; ++xx) {
+                const float4 v = RLStore<Tm>::load4(base + ((size_t)yy * W + xx) * 4);
+                acc.x += v.x; acc.y += v.y; acc.z += v.z; acc.w += v.w;
+            }
+    }
+    const float inv = 1.f / (float)(s * s);
+    acc.x *= inv; acc.y *= inv; acc.z *= inv; acc.w *= inv;
+    return acc;
+}
+
+// Pyramid level l and its selection in one pass.  A block takes kTile consecutive level
+// pixels: its threads form the kTile x D level voxels (a warp per plane row of the tile),
+// store them to Ml and keep their alphas, as stored, in shared memory; the first warp then
+// selects for the tile's pixels from shared memory.  Same arithmetic as forming Ml and then
+// running the selection kernel on it.
+constexpr int kTile = 32;
+
+template <typename Tm, int K, int LOG>
+__global__ void __launch_bounds__(256)
+k_pyramid_select(const Tm* __restrict__ M, int D, int H, int W, int level, Tm* __restrict__ Ml, int k,
+                 uint8_t* __restrict__ S, uint8_t* __restrict__ slots, float* __restrict__ Gzero,
+                 unsigned* __restrict__ counter_zero, int mode) {
+    __shared__ float alpha[RL_DEV_MAX_PLANES][kTile];
+    const int h = H >> level, w = W >> level;
+    const long long hw = (long long)h * w;
+    const long long p0 = (long long)blockIdx.x * kTile;
+    if (p0 == 0 && threadIdx.x == 0 && counter_zero) *counter_zero = 0u;
+    // level 1: the loads of NB voxels (4 full-resolution voxels each) are issued together
+    constexpr int NB = LOG == 1 ? 4 : 1;
+    for (int i0 = threadIdx.x; i0 < D * kTile; i0 += NB * blockDim.x) {
+        float4 v[NB];
+#pragma unroll
+        for (int b = 0; b < NB; ++b) {
+            const int i = i0 + b * blockDim.x;
+            const long long p = p0 + i % kTile;
+            if (i < D * kTile && p < hw)
+                v[b] = pyramid_mean<Tm, LOG>(M, H, W, level, i / kTile, (int)(p / w), (int)(p % w));
+        }
+#pragma unroll
+        for (int b = 0; b < NB; ++b) {
+            const int i = i0 + b * blockDim.x;
+            const int d = i / kTile, j = i % kTile;
+            const long long p = p0 + j;
+            if (i >= D * kTile || p >= hw) continue;
+            RLStore<Tm>::store4(Ml + ((size_t)d * hw + p) * 4, v[b]);
+            alpha[d][j] = RLStore<Tm>::round1(v[b].w);
+        }
+    }
+    __syncthreads();
+    const int j = threadIdx.x;
+    const long long p = p0 + j;
+    if (j >= kTile || p >= hw) return;
+    const uint64_t mk = select_mask<K, false>([&](int d) { return alpha[d][j]; }, D, k, mode);
+    write_selection(mk, D, k, hw, p, S, nullptr, slots, Gzero);
+}
+
 template <typename Tm, bool FROM_KEYS>
 void launch_select_t(const void* M, const float* keys, int D, int h, int w, int k, uint8_t* S, uint64_t* mask,
                      uint8_t* slots, float* Gzero, unsigned* counter_zero, int mode, cudaStream_t s) {
     const long long hw = (long long)h * w;
     const int blocks = (int)((hw + 127) / 128);
-    if (k <= 8 || mode == 1)
-        k_select<Tm, FROM_KEYS, 8><<<blocks, 128, 0, s>>>((const Tm*)M, keys, D, h, w, k, S, mask, slots, Gzero,
-                                                          counter_zero, mode);
-    else
-        k_select<Tm, FROM_KEYS, 64><<<blocks, 128, 0, s>>>((const Tm*)M, keys, D, h, w, k, S, mask, slots, Gzero,
-                                                           counter_zero, mode);
+#define RL_SEL(KK)                                                                                          \
+    k_select<Tm, FROM_KEYS, KK><<<blocks, 128, 0, s>>>((const Tm*)M, keys, D, h, w, k, S, mask, slots, Gzero, \
+                                                       counter_zero, mode)
+    switch (mode == 1 ? 1 : k) {
+        case 1: RL_SEL(1); break;
+        case 2: RL_SEL(2); break;
+        case 3: RL_SEL(3); break;
+        case 4: RL_SEL(4); break;
+        case 5: RL_SEL(5); break;
+        case 6: RL_SEL(6); break;
+        case 7: RL_SEL(7); break;
+        case 8: RL_SEL(8); break;
+        default: RL_SEL(64); break;
+    }
+#undef RL_SEL
+}
+
+template <typename Tm, int LOG>
+void launch_pyramid_select_l(const Tm* M, int D, int H, int W, int level, Tm* Ml, int k, uint8_t* S,
+                             uint8_t* slots, float* Gzero, unsigned* counter_zero, int mode, cudaStream_t s) {
+    const long long hw = (long long)(H >> level) * (W >> level);
+    const unsigned blocks = (unsigned)((hw + kTile - 1) / kTile);
+#define RL_PS(KK) \
+    k_pyramid_select<Tm, KK, LOG><<<blocks, 256, 0, s>>>(M, D, H, W, level, Ml, k, S, slots, Gzero, counter_zero, mode)
+    switch (mode == 1 ? 1 : k) {
+        case 1: RL_PS(1); break;
+        case 2: RL_PS(2); break;
+        case 3: RL_PS(3); break;
+        case 4: RL_PS(4); break;
+        case 5: RL_PS(5); break;
+        case 6: RL_PS(6); break;
+        case 7: RL_PS(7); break;
+        case 8: RL_PS(8); break;
+        default: RL_PS(64); break;
+    }
+#undef RL_PS
 }
 
 template <typename Tm>
-__global__ void __launch_bounds__(256)
-k_pyramid(const Tm* __restrict__ M, int D, int H, int W, int level, Tm* __restrict__ Ml) {
-    const int h = H >> level, w = W >> level, s = 1 << level;
-    const long long n = (long long)D * h * w;
-    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const int x = (int)(i % w);
-    const long long r = i / w;
-    const int y = (int)(r % h);
-    const int d = (int)(r / h);
-    const Tm* base = M + (((size_t)d * H + (size_t)y * s) * W + (size_t)x * s) * 4;
-    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-    for (int yy = 0; yy < s; ++yy)
-#pragma unroll 4
-        for (int xx = 0; xx < s; ++xx) {
-            const float4 v = RLStore<Tm>::load4(base + ((size_t)yy * W + xx) * 4);
-            acc.x += v.x; acc.y += v.y; acc.z += v.z; acc.w += v.w;
-        }
-    const float inv = 1.f / (float)(s * s);
-    acc.x *= inv; acc.y *= inv; acc.z *= inv; acc.w *= inv;
-    RLStore<Tm>::store4(Ml + (size_t)i * 4, acc);
+void launch_pyramid_select_t(const void* M, int D, int H, int W, int level, void* Ml, int k, uint8_t* S,
+                             uint8_t* slots, float* Gzero, unsigned* counter_zero, int mode, cudaStream_t s) {
+    if (level == 1)
+        launch_pyramid_select_l<Tm, 1>((const Tm*)M, D, H, W, level, (Tm*)Ml, k, S, slots, Gzero, counter_zero,
+                                       mode, s);
+    else if (level == 2)
+        launch_pyramid_select_l<Tm, 2>((const Tm*)M, D, H, W, level, (Tm*)Ml, k, S, slots, Gzero, counter_zero,
+                                       mode, s);
+    else
+        launch_pyramid_select_l<Tm, -1>((const Tm*)M, D, H, W, level, (Tm*)Ml, k, S, slots, Gzero, counter_zero,
+                                        mode, s);
 }
 
 __global__ void k_mask_to_slots(const uint64_t* __restrict__ mask, int D, int hw, uint8_t* __restrict__ slots) {
@@ -206,18 +332,17 @@ rl_status rl_launch_select(const void* M, rl_dtype dt, const float* keys, int D,
     return rl_check_launch("select");
 }
 
-rl_status rl_launch_pyramid(const void* M, rl_dtype dt, int D, int H, int W, int level, void* Ml, cudaStream_t s) {
-    const long long n = (long long)D * (H >> level) * (W >> level);
-    const unsigned blocks = (unsigned)((n + 255) / 256);
+rl_status rl_launch_pyramid_select(const void* M, rl_dtype dt, int D, int H, int W, int level, void* Ml, int k,
+                                   uint8_t* S, uint8_t* slots, float* Gzero, unsigned* counter_zero, int mode,
+                                   cudaStream_t s) {
     if (dt == RL_F32) {
-        RLTraceScope ts("pyramid_f32", s);
-        k_pyramid<float><<<blocks, 256, 0, s>>>((const float*)M, D, H, W, level, (float*)Ml);
+        RLTraceScope ts("pyramid_select_f32", s);
+        launch_pyramid_select_t<float>(M, D, H, W, level, Ml, k, S, slots, Gzero, counter_zero, mode, s);
     } else {
-        RLTraceScope ts("pyramid_bf16", s);
-        k_pyramid<__nv_bfloat16><<<blocks, 256, 0, s>>>((const __nv_bfloat16*)M, D, H, W, level,
-                                                        (__nv_bfloat16*)Ml);
+        RLTraceScope ts("pyramid_select_bf16", s);
+        launch_pyramid_select_t<__nv_bfloat16>(M, D, H, W, level, Ml, k, S, slots, Gzero, counter_zero, mode, s);
     }
-    return rl_check_launch("pyramid");
+    return rl_check_launch("pyramid_select");
 }
 
 rl_status rl_launch_mask_to_slots(const uint64_t* mask, int D, int hw, uint8_t* slots, cudaStream_t s) {

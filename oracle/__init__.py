@@ -78,6 +78,13 @@ def _load():
             lib.orc_sparsity_loss.restype = d
             lib.orc_gd_step.argtypes = [dp, i, i, i, d, d, cam, dp, cam, i, d, i, i, dp]
             lib.orc_gd_step.restype = i
+            lib.orc_ref_to_view.argtypes = [cam, cam, d, d, d, dp, dp]
+            lib.orc_ref_to_view.restype = i
+            lib.orc_view_alpha_weights.argtypes = [dp, i, i, i, d, d, cam, cam, dp]
+            lib.orc_psv_view.argtypes = [dp, i, i, i, d, d, cam, cam, dp]
+            lib.orc_inverse_warp_stack.argtypes = [dp, i, i, i, d, d, cam, cam, dp]
+            lib.orc_gradient_volume.argtypes = [dp, i, i, i, d, d, cam, dp, cam, i, i, i, i, u8p, u8p, dp]
+            lib.orc_gradient_volume.restype = i
             _lib = lib
     return _lib
 
@@ -270,3 +277,64 @@ def refine(M, near, far, ref, views, images, k: int, schedule=(2, 1, 0), lam: fl
         losses.append(L)
         sels.append(S)
     return M, losses, sels
+
+
+def ref_to_view(ref, view, z: float, u: float, v: float):
+    """Inverse warp of Eq. (eq_homo): view pixel of reference pixel (u, v) on the plane at depth z; None if
+    the point is behind the view."""
+    x, y = ctypes.c_double(), ctypes.c_double()
+    ok = _load().orc_ref_to_view(ctypes.byref(_cam(ref)), ctypes.byref(_cam(view)), z, u, v,
+                                 ctypes.byref(x), ctypes.byref(y))
+    return (x.value, y.value) if ok else None
+
+
+def view_alpha_weights(M, near: float, far: float, ref, view) -> np.ndarray:
+    """Alpha weights of the MPI warped into ``view`` (Eq. eq_gradient on M_i) -> ``[D][H][W]``."""
+    M = _f64(M)
+    D, H, W, _ = M.shape
+    A = np.empty((D, H, W))
+    _load().orc_view_alpha_weights(_ptr(M), D, H, W, near, far, ctypes.byref(_cam(ref)), ctypes.byref(_cam(view)),
+                                   _ptr(A))
+    return A
+
+
+def psv_view(image, D: int, near: float, far: float, ref, view) -> np.ndarray:
+    """Plane sweep volume of one source view (Sec. 3.2): ``image[H][W][3]`` -> ``[D][H][W][3]``."""
+    image = _f64(image)
+    H, W, _ = image.shape
+    P = np.empty((D, H, W, 3))
+    _load().orc_psv_view(_ptr(image), D, H, W, near, far, ctypes.byref(_cam(ref)), ctypes.byref(_cam(view)), _ptr(P))
+    return P
+
+
+def inverse_warp_stack(X, near: float, far: float, ref, view) -> np.ndarray:
+    """Inverse warp of view-frame maps ``X[D][H][W]`` into the reference frame (Sec. 3.3)."""
+    X = _f64(X)
+    D, H, W = X.shape
+    out = np.empty((D, H, W))
+    _load().orc_inverse_warp_stack(_ptr(X), D, H, W, near, far, ctypes.byref(_cam(ref)), ctypes.byref(_cam(view)),
+                                   _ptr(out))
+    return out
+
+
+def gradient_volume(M, near, far, ref, views, images, k: int, level: int = 0, selection: int = 0, S_pin=None):
+    """Sparsified gradient volume V_s (Sec. 3.3, Eq. eq_simplifiedGradients / eq_V) at ``level``:
+    returns (Vs[4N+4][k][h][w], S[k][h][w]).  Channels: P_l (3N, view-major), A^{w^-1} (N), M_l (4)."""
+    M = _f64(M)
+    D, H, W, _ = M.shape
+    images = _f64(images)
+    N = len(views)
+    h, w = H >> level, W >> level
+    S = np.empty((k, h, w), dtype=np.uint8)
+    Vs = np.empty((4 * N + 4, k, h, w))
+    pin = None
+    if S_pin is not None:
+        pin = np.ascontiguousarray(S_pin, dtype=np.uint8)
+        assert pin.shape == (k, h, w)
+    rc = _load().orc_gradient_volume(_ptr(M), D, H, W, near, far, ctypes.byref(_cam(ref)), _ptr(images),
+                                     _cams(views), N, k, level, int(selection),
+                                     _ptr(pin, ctypes.c_uint8) if pin is not None else None,
+                                     _ptr(S, ctypes.c_uint8), _ptr(Vs))
+    if rc:
+        raise ValueError("oracle gradient_volume: invalid arguments")
+    return Vs, S

@@ -31,6 +31,12 @@
  *     and adds the nearest-neighbour upsampled masked step to the full MPI (the
  *     restore operator R(., S) of Sec. 3.3 followed by the coarse-to-fine upsampling).
  *   - Update: M[d] <- clamp(M[d] - lambda g[d], 0, 1) for selected d (clamp optional).
+ *   - Gradient volume (Sec. 3.3): the PSV samples each source image at the reference pixel
+ *     carried into the view by Eq. (eq_homo)'s inverse homography (computed geometrically);
+ *     the level-l PSV is Down^l of the full-resolution PSV, as Sec. 3.2 downsamples the
+ *     volume itself.  The inverse-warped alpha weights of view i come from the level MPI
+ *     M_l warped into view i at level l (Eq. eq_gradient at every view pixel), sampled back at
+ *     the reference pixels the same way.  Channels: P (3N, view-major), A (N), M_l (4).
  */
 #include <math.h>
 #include <stdint.h>
@@ -379,6 +385,187 @@ void orc_down_levels(const double* x, int P, int H, int W, int C, int level, dou
     double* r = down_levels(x, P, H, W, C, level);
     memcpy(y, r, sizeof(double) * (size_t)P * (H >> level) * (W >> level) * C);
     free(r);
+}
+
+/* ---------------------------------------------------- gradient volume (Sec. 3.3) */
+
+/*
+ * Inverse homographic warp of Eq. (eq_homo): reference pixel (u,v) on the plane z_ref = z
+ * -> pixel (x,y) of camera `view`.  Back-projects the reference pixel to depth z in the
+ * reference frame, takes the point to the world frame and into the view camera, projects.
+ * Returns 0 when the point is not in front of the view.
+ */
+int orc_ref_to_view(const orc_camera* ref, const orc_camera* view, double z, double u, double v, double* x,
+                    double* y) {
+    double Kinv[9];
+    inv3(ref->K, Kinv);
+    double Xr[3];
+    for (int a = 0; a < 3; ++a) Xr[a] = z * (Kinv[a * 3 + 0] * u + Kinv[a * 3 + 1] * v + Kinv[a * 3 + 2]);
+    /* world point X_w = R_r^T (X_r - t_r) */
+    double Xw[3];
+    for (int a = 0; a < 3; ++a)
+        Xw[a] = ref->R[0 * 3 + a] * (Xr[0] - ref->t[0]) + ref->R[1 * 3 + a] * (Xr[1] - ref->t[1]) +
+                ref->R[2 * 3 + a] * (Xr[2] - ref->t[2]);
+    double Xv[3];
+    for (int a = 0; a < 3; ++a)
+        Xv[a] = view->R[a * 3 + 0] * Xw[0] + view->R[a * 3 + 1] * Xw[1] + view->R[a * 3 + 2] * Xw[2] + view->t[a];
+    if (!(Xv[2] > 0.0)) return 0;
+    const double* K = view->K;
+    double hx = K[0] * Xv[0] + K[1] * Xv[1] + K[2] * Xv[2];
+    double hy = K[3] * Xv[0] + K[4] * Xv[1] + K[5] * Xv[2];
+    double hz = K[6] * Xv[0] + K[7] * Xv[1] + K[8] * Xv[2];
+    *x = hx / hz;
+    *y = hy / hz;
+    return 1;
+}
+
+/* Bilinear sample (zero padding per tap) of a [H][W][C] image at (x, y): out[C]. */
+static void sample_image(const double* img, int H, int W, int C, int valid, double x, double y, double* out) {
+    for (int c = 0; c < C; ++c) out[c] = 0.0;
+    if (!valid) return;
+    int tx[4], ty[4];
+    double w[4];
+    bilinear_taps(x, y, W, H, tx, ty, w);
+    for (int k = 0; k < 4; ++k) {
+        if (w[k] == 0.0) continue;
+        const double* v = img + ((size_t)ty[k] * W + tx[k]) * C;
+        for (int c = 0; c < C; ++c) out[c] += w[k] * v[c];
+    }
+}
+
+/*
+ * Alpha weights of the MPI warped into a view (Eq. eq_gradient applied to M_i):
+ * A[d][y][x] = alpha_d(q) prod_{j>d} (1 - alpha_j(q)), alpha_j(q) the alpha of plane j
+ * sampled along the ray of view pixel q = (x, y) (the same warp as the render).  The view
+ * has the MPI's size H x W.
+ */
+void orc_view_alpha_weights(const double* M, int D, int H, int W, double near_, double far_, const orc_camera* ref,
+                            const orc_camera* view, double* A) {
+    double* rho = (double*)malloc(sizeof(double) * D);
+    double* alpha = (double*)malloc(sizeof(double) * D);
+    orc_plane_inverse_depths(D, near_, far_, rho);
+    for (int y = 0; y < H; ++y)
+        for (int x = 0; x < W; ++x) {
+            for (int d = 0; d < D; ++d) {
+                double px, py;
+                int ok = orc_view_to_ref(ref, view, 1.0 / rho[d], x, y, &px, &py);
+                sample_t s;
+                sample_plane(M, d, H, W, ok, px, py, &s);
+                alpha[d] = s.m[3];
+            }
+            for (int d = 0; d < D; ++d) {
+                double T = 1.0;
+                for (int j = d + 1; j < D; ++j) T *= (1.0 - alpha[j]);
+                A[((size_t)d * H + y) * W + x] = alpha[d] * T;
+            }
+        }
+    free(alpha);
+    free(rho);
+}
+
+/*
+ * Plane sweep volume of one source view (Sec. 3.2): P[d][y][x][3] = grid_sample of the
+ * view's image [H][W][3] at the inverse-warped reference pixel (x, y) of plane d
+ * (orc_ref_to_view), bilinear with zero padding.
+ */
+void orc_psv_view(const double* image, int D, int H, int W, double near_, double far_, const orc_camera* ref,
+                  const orc_camera* view, double* P) {
+    double* rho = (double*)malloc(sizeof(double) * D);
+    orc_plane_inverse_depths(D, near_, far_, rho);
+    for (int d = 0; d < D; ++d)
+        for (int y = 0; y < H; ++y)
+            for (int x = 0; x < W; ++x) {
+                double vx, vy;
+                int ok = orc_ref_to_view(ref, view, 1.0 / rho[d], x, y, &vx, &vy);
+                sample_image(image, H, W, 3, ok, vx, vy, P + (((size_t)d * H + y) * W + x) * 3);
+            }
+    free(rho);
+}
+
+/*
+ * Inverse warp of a per-plane stack of view-frame maps X[D][H][W] (one channel) into the
+ * reference frame: out[d][y][x] = bilinear(X[d], orc_ref_to_view(ref, view, z_d, x, y)).
+ */
+void orc_inverse_warp_stack(const double* X, int D, int H, int W, double near_, double far_, const orc_camera* ref,
+                            const orc_camera* view, double* out) {
+    double* rho = (double*)malloc(sizeof(double) * D);
+    orc_plane_inverse_depths(D, near_, far_, rho);
+    for (int d = 0; d < D; ++d)
+        for (int y = 0; y < H; ++y)
+            for (int x = 0; x < W; ++x) {
+                double vx, vy;
+                int ok = orc_ref_to_view(ref, view, 1.0 / rho[d], x, y, &vx, &vy);
+                sample_image(X + (size_t)d * H * W, H, W, 1, ok, vx, vy, out + ((size_t)d * H + y) * W + x);
+            }
+    free(rho);
+}
+
+/*
+ * Sparsified gradient volume of one HSGD iteration at level l (Sec. 3.3, Eq.
+ * eq_simplifiedGradients and eq_V): V = [P_l, A^{w^-1}_1 .. A^{w^-1}_N, M_l] with
+ *   P_l        = Down^l of the full-resolution plane sweep volume of the N source views
+ *                (Sec. 3.2, "we downsample it hierarchically"), 3N channels, view-major;
+ *   A^{w^-1}_i = the alpha weights of M_l warped into view i at level l, inverse-warped
+ *                back to the reference frame, N channels;
+ *   M_l        = Down^l(M), 4 channels (R, G, B, alpha);
+ * compacted along depth to the k planes of S (Sec. 3.3, "Gradient Sparsification"):
+ *   Vs[c][j][y][x] = V[c][S[j][y][x]][y][x],  C = 4N + 4 channels.
+ * S is the selection of orc_hsgd_step2 on M_l (top-k or MVS window) or S_pin; S_out gets it.
+ */
+int orc_gradient_volume(const double* M, int D, int H, int W, double near_, double far_, const orc_camera* ref,
+                        const double* images, const orc_camera* views, int N, int k, int level, int selection,
+                        const uint8_t* S_pin, uint8_t* S_out, double* Vs) {
+    if (k < 1 || k > D || D > 64 || (H % (1 << level)) || (W % (1 << level))) return 1;
+    const int h = H >> level, w = W >> level, C = 4 * N + 4;
+    const size_t hw = (size_t)h * w;
+    double* Ml = down_levels(M, D, H, W, 4, level);
+    orc_camera refl;
+    orc_camera_at_level(ref, level, &refl);
+    uint8_t* S = (uint8_t*)malloc((size_t)k * hw);
+    if (S_pin) {
+        memcpy(S, S_pin, (size_t)k * hw);
+    } else {
+        double* A = (double*)malloc(sizeof(double) * (size_t)D * hw);
+        uint64_t* mk = (uint64_t*)malloc(sizeof(uint64_t) * hw);
+        orc_alpha_weights(Ml, D, h, w, A);
+        if (selection == 1)
+            orc_select_mvs(A, D, h, w, k, S, mk);
+        else
+            orc_select_topk(A, D, h, w, k, S, mk);
+        free(mk);
+        free(A);
+    }
+    double* Pfull = (double*)malloc(sizeof(double) * (size_t)D * H * W * 3);
+    double* Aview = (double*)malloc(sizeof(double) * (size_t)D * hw);
+    double* Ainv = (double*)malloc(sizeof(double) * (size_t)D * hw);
+    for (int i = 0; i < N; ++i) {
+        orc_psv_view(images + (size_t)i * H * W * 3, D, H, W, near_, far_, ref, &views[i], Pfull);
+        double* Pl = down_levels(Pfull, D, H, W, 3, level);
+        orc_camera vl;
+        orc_camera_at_level(&views[i], level, &vl);
+        orc_view_alpha_weights(Ml, D, h, w, near_, far_, &refl, &vl, Aview);
+        orc_inverse_warp_stack(Aview, D, h, w, near_, far_, &refl, &vl, Ainv);
+        for (int j = 0; j < k; ++j)
+            for (size_t p = 0; p < hw; ++p) {
+                const int d = S[(size_t)j * hw + p];
+                for (int c = 0; c < 3; ++c)
+                    Vs[((size_t)(3 * i + c) * k + j) * hw + p] = Pl[((size_t)d * hw + p) * 3 + c];
+                Vs[((size_t)(3 * N + i) * k + j) * hw + p] = Ainv[(size_t)d * hw + p];
+            }
+        free(Pl);
+    }
+    for (int j = 0; j < k; ++j)
+        for (size_t p = 0; p < hw; ++p) {
+            const int d = S[(size_t)j * hw + p];
+            for (int c = 0; c < 4; ++c) Vs[((size_t)(4 * N + c) * k + j) * hw + p] = Ml[((size_t)d * hw + p) * 4 + c];
+        }
+    if (S_out) memcpy(S_out, S, (size_t)k * hw);
+    free(Ainv);
+    free(Aview);
+    free(Pfull);
+    free(S);
+    free(Ml);
+    return 0;
 }
 
 /* ------------------------------------------------------------------- update */

@@ -161,6 +161,34 @@ rl_status reallife_refine(rl_mpi* m, const float* images, const rl_camera* src, 
 rl_status reallife_hsgd_step_noalloc(rl_mpi* m, const float* images, const rl_camera* src, int N,
                                      const rl_hsgd_params* p, float* loss_out, uint8_t* S_out, cudaStream_t stream);
 
+/* --------------------------------------------------------- gradient volume */
+
+/* Bytes of workspace that reallife_gradient_volume needs for an MPI of D x H x W with N
+ * views and k kept planes, at any level (a multiple of 256). */
+size_t reallife_gradient_volume_workspace_bytes(int N, int D, int H, int W, int k, rl_dtype dtype);
+
+/* The sparsified gradient volume V_s of one HSGD iteration at level `level` (Sec. 3.3,
+ * Eq. eq_simplifiedGradients and eq_V): the input of the paper's learned update.  With
+ * M_l = Down^l(M), S the selection on M_l (top-k of the reference alpha weights or the
+ * MVS window, `selection`), h = H/2^l and w = W/2^l, for slot j < k of level pixel p and
+ * d = S[j][p]:
+ *   V[3i + c][j][p]  c < 3   PSV of source view i (Sec. 3.2): the full-resolution image i
+ *                            bilinearly sampled (zero padding) where the inverse homography
+ *                            of Eq. eq_homo carries each of p's 2^l x 2^l full-resolution
+ *                            child pixels on plane d, averaged over the children;
+ *   V[3N + i][j][p]          A^{w^-1}_i: the alpha weights alpha_d prod_{j>d}(1 - alpha_j) of
+ *                            M_l warped into view i at level l (Eq. eq_gradient), sampled
+ *                            bilinearly where the inverse homography carries p on plane d;
+ *   V[4N + c][j][p]  c < 4   M_l[d][p] (R, G, B, alpha).
+ * images: device [N][H][W][3] FP32 (full resolution).  V: device [4N+4][k][h][w] FP32,
+ * overwritten.  S_out: device [k][h][w] uint8 (ascending d) or NULL.  The MPI is not
+ * modified.  ws: device workspace, 256-byte aligned, at least
+ * reallife_gradient_volume_workspace_bytes(...) bytes (RL_ENOMEM when smaller).
+ * Asynchronous on `stream`; RL_EINVAL for the argument errors of reallife_hsgd_step. */
+rl_status reallife_gradient_volume(const rl_mpi* m, const float* images, const rl_camera* src, int N, int k,
+                                   int level, int selection, uint8_t* S_out, float* V, void* ws, size_t ws_bytes,
+                                   cudaStream_t stream);
+
 /* -------------------------------------------------------- steps of the iteration */
 
 /* Down^l of P stacked [H][W][C] FP32 slices (2x2 box average applied l times, computed

@@ -188,6 +188,37 @@ def reallife_refine(m: Mpi, images: torch.Tensor, src, k: int, schedule=(2, 1, 0
     return loss_per_iter
 
 
+def reallife_gradient_volume_workspace_bytes(N: int, D: int, H: int, W: int, k: int, dtype=torch.float32) -> int:
+    return int(_lib.lib().reallife_gradient_volume_workspace_bytes(N, D, H, W, k, _DT[dtype]))
+
+
+def reallife_gradient_volume(m: Mpi, images: torch.Tensor, src, k: int, level: int = 0,
+                             selection: int = SELECT_TOPK, V: torch.Tensor | None = None,
+                             S_out: torch.Tensor | None = None, ws: torch.Tensor | None = None, stream=None):
+    """Sparsified gradient volume of Sec. 3.3 at ``level``: returns (V [4N+4][k][h][w] float32,
+    S [k][h][w] uint8).  Channels: PSV (3N, view-major), inverse-warped alpha weights (N),
+    the level MPI (4).  ``m`` is not modified."""
+    N = len(src)
+    _check_f32(images, (N, m.H, m.W, 3), "images")
+    h, w = m.H >> level, m.W >> level
+    dev = m.data.device
+    if V is None:
+        V = torch.empty((4 * N + 4, k, h, w), dtype=torch.float32, device=dev)
+    _check_f32(V, (4 * N + 4, k, h, w), "V")
+    if S_out is None:
+        S_out = torch.empty((k, h, w), dtype=torch.uint8, device=dev)
+    if S_out.dtype != torch.uint8 or tuple(S_out.shape) != (k, h, w):
+        raise ValueError(f"S_out must be uint8 {(k, h, w)}")
+    if ws is None:
+        ws = torch.empty(reallife_gradient_volume_workspace_bytes(N, m.D, m.H, m.W, k, m.data.dtype),
+                         dtype=torch.uint8, device=dev)
+    ms = m.c_struct()
+    _lib.check("reallife_gradient_volume", _lib.lib().reallife_gradient_volume(
+        ctypes.byref(ms), _ptr(images), _lib.cameras(src), N, int(k), int(level), int(selection), _ptr(S_out),
+        _ptr(V), _ptr(ws), ws.numel(), _stream(stream)))
+    return V, S_out
+
+
 def reallife_downsample_f32(x: torch.Tensor, level: int, out: torch.Tensor | None = None, stream=None):
     """Down^l of ``x[P][H][W][C]`` float32 (2^l x 2^l box average)."""
     P, H, W, C = x.shape

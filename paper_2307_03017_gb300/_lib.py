@@ -19,6 +19,7 @@ EXPORTS = [
     "reallife_sparse_update", "reallife_render_backward", "reallife_warp_offsets", "reallife_trace_enable",
     "reallife_trace_read", "reallife_strerror", "reallife_last_error", "reallife_set_kernel_path",
     "reallife_device_status", "reallife_hsgd_step_noalloc", "reallife_trace_release_captured",
+    "reallife_gradient_volume_workspace_bytes", "reallife_gradient_volume",
 ]
 
 
@@ -89,6 +90,9 @@ def _declare(lib):
         "reallife_set_kernel_path": (c_int, [c_int]),
         "reallife_device_status": (c_int, [c_int, ctypes.POINTER(ctypes.c_uint)]),
         "reallife_last_error": (ctypes.c_char_p, []),
+        "reallife_gradient_volume_workspace_bytes": (c_size_t, [c_int, c_int, c_int, c_int, c_int, c_int]),
+        "reallife_gradient_volume": (c_int, [mpi_p, vp, cam_p, c_int, c_int, c_int, c_int, vp, vp, vp, c_size_t,
+                                             vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)

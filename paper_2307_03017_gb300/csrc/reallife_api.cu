@@ -239,6 +239,36 @@ RLViewParam view_param(const rl_camera& ref, const rl_camera& view) {
     return P;
 }
 
+// Inverse warp parameters (reference -> view) of rl_common.cuh for one view.
+RLInvParam inv_view_param(const rl_camera& ref, const rl_camera& view) {
+    double Rrel[9];  // R_v R_r^T
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) {
+            double s = 0.0;
+            for (int j = 0; j < 3; ++j) s += view.R[a * 3 + j] * ref.R[b * 3 + j];
+            Rrel[a * 3 + b] = s;
+        }
+    RLInvParam P;
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) P.F[a * 3 + b] = (float)(Rrel[a * 3 + b] - (a == b ? 1.0 : 0.0));
+    for (int a = 0; a < 3; ++a) {  // t_rel = t_v - R_rel t_r
+        double s = 0.0;
+        for (int j = 0; j < 3; ++j) s += Rrel[a * 3 + j] * ref.t[j];
+        P.t[a] = (float)(view.t[a] - s);
+    }
+    P.inv_fxr = (float)(1.0 / ref.K[0]);
+    P.inv_fyr = (float)(1.0 / ref.K[4]);
+    P.cxr = (float)ref.K[2];
+    P.cyr = (float)ref.K[5];
+    P.fxv = (float)view.K[0];
+    P.fyv = (float)view.K[4];
+    P.dcx = (float)(view.K[2] - ref.K[2]);
+    P.dcy = (float)(view.K[5] - ref.K[5]);
+    P.dfx = (float)(view.K[0] - ref.K[0]);
+    P.dfy = (float)(view.K[4] - ref.K[4]);
+    return P;
+}
+
 void fill_rho(RLViews& v, int D, double near_, double far_) {
     for (int d = 0; d < RL_DEV_MAX_PLANES; ++d) v.rho[d] = 0.f;
     for (int d = 0; d < D; ++d) {
@@ -359,6 +389,25 @@ rl_status enqueue_hsgd(rl_mpi* m, const float* images, const rl_camera* src, int
     return rl_launch_update(m->data, m->dtype, m->D, m->H, m->W, level, S, G, k, lambda, clamp01, s, Ml, lambda_s);
 }
 
+// Workspace of reallife_gradient_volume: the level MPI (levels >= 1), the selection and
+// the view alpha weights [N][D][h][w] (largest at level 0).
+struct VolLayout {
+    size_t Ml, S, A, total;
+};
+
+VolLayout vol_layout(int N, int D, int H, int W, int k, rl_dtype dt) {
+    VolLayout L;
+    size_t off = 0;
+    L.Ml = off;
+    if (H % 2 == 0 && W % 2 == 0) off += align_up((size_t)D * (H / 2) * (W / 2) * 4 * elt_size(dt));
+    L.S = off;
+    off += align_up((size_t)k * H * W);
+    L.A = off;
+    off += align_up((size_t)N * D * H * W * sizeof(float));
+    L.total = off;
+    return L;
+}
+
 __global__ void k_zero(float4* __restrict__ p, size_t n4) {
     for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += (size_t)gridDim.x * blockDim.x)
         p[i] = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -422,6 +471,53 @@ extern "C" rl_status reallife_refine(rl_mpi* m, const float* images, const rl_ca
         if (st) return st;
     }
     return RL_OK;
+}
+
+extern "C" size_t reallife_gradient_volume_workspace_bytes(int N, int D, int H, int W, int k, rl_dtype dtype) {
+    if (N < 1 || D < 1 || H < 1 || W < 1 || k < 1) return 0;
+    return vol_layout(N, D, H, W, k, dtype).total;
+}
+
+extern "C" rl_status reallife_gradient_volume(const rl_mpi* m, const float* images, const rl_camera* src, int N,
+                                              int k, int level, int selection, uint8_t* S_out, float* V, void* ws,
+                                              size_t ws_bytes, cudaStream_t stream) {
+    rl_hsgd_params p;
+    std::memset(&p, 0, sizeof(p));
+    p.k = k;
+    p.lambda = 1.0f;
+    p.selection = selection;
+    const size_t need = (m && N >= 1) ? vol_layout(N, m->D, m->H, m->W, k, m->dtype).total : 0;
+    // the step's checks (MPI, k, selection, level, images, cameras); its workspace is not used
+    rl_status st = check_hsgd(m, images, src, N, &p, level, ws, ~(size_t)0);
+    if (st) return st;
+    if (!V || ((uintptr_t)V & 3) != 0) return rl_fail(RL_EINVAL, "V must be a non-NULL, 4-byte aligned device buffer");
+    if (ws_bytes < need) return rl_fail(RL_ENOMEM, "workspace %zu bytes < %zu needed", ws_bytes, need);
+    const VolLayout L = vol_layout(N, m->D, m->H, m->W, k, m->dtype);
+    char* base = (char*)ws;
+    const int h = m->H >> level, w = m->W >> level;
+    void* Ml = level == 0 ? m->data : (void*)(base + L.Ml);
+    uint8_t* S = S_out ? S_out : (uint8_t*)(base + L.S);
+    float* A = (float*)(base + L.A);
+    RLViews views;
+    st = make_views(m, src, N, level, views);
+    if (st) return st;
+    RLInvViews iv;
+    std::memset(&iv, 0, sizeof(iv));
+    iv.n = N;
+    for (int d = 0; d < RL_DEV_MAX_PLANES; ++d) iv.rho[d] = views.rho[d];
+    const rl_camera refl = camera_at_level(m->ref, level);
+    for (int i = 0; i < N; ++i) {
+        iv.lv[i] = inv_view_param(refl, camera_at_level(src[i], level));
+        iv.full[i] = inv_view_param(m->ref, src[i]);
+    }
+    st = level ? rl_launch_pyramid_select(m->data, m->dtype, m->D, m->H, m->W, level, Ml, k, S, nullptr, nullptr,
+                                          nullptr, selection, stream)
+               : rl_launch_select(Ml, m->dtype, nullptr, m->D, h, w, k, S, nullptr, nullptr, nullptr, stream,
+                                  nullptr, selection);
+    if (st) return st;
+    st = rl_launch_view_alpha(Ml, m->dtype, m->D, h, w, views, A, stream);
+    if (st) return st;
+    return rl_launch_volume(Ml, m->dtype, m->D, h, w, level, S, k, A, images, iv, V, stream);
 }
 
 extern "C" rl_status reallife_downsample_f32(const float* x, int P, int H, int W, int C, int level, float* y,

@@ -83,6 +83,69 @@ __device__ __forceinline__ RLTaps rl_taps(const RLWarp& w, float rho, int qx, in
     return t;
 }
 
+// Inverse warp (reference -> view, the direction of Eq. eq_homo's H^{-1}).  The reference
+// pixel (u, v) on the plane of inverse depth rho has reference-frame direction
+// m = K_r^{-1}(u, v, 1); in the view camera it lies along R_rel m + rho t_rel, with
+// R_rel = R_v R_r^T and t_rel = t_v - R_rel t_r.  Writing R_rel = I + F and e = F m:
+//     x = u + (cx_v - cx_r) + (fx_v - fx_r) m_x + fx_v (e_x - m_x e_z + rho (t_x - m_x t_z)) / Z,
+//     Z = 1 + e_z + rho t_z,                                            (same for y)
+// and the point is in front of the view iff Z > 0.  As for the forward warp, the offset
+// from u is formed from small terms only.
+struct RLInvParam {
+    float F[9];          // R_rel - I (row-major)
+    float t[3];          // t_rel
+    float inv_fxr, inv_fyr, cxr, cyr;
+    float fxv, fyv;
+    float dcx, dcy;      // cx_v - cx_r, cy_v - cy_r
+    float dfx, dfy;      // fx_v - fx_r, fy_v - fy_r
+};
+
+// Inverse-warp parameters of one launch (level-l and full-resolution cameras of each view).
+struct RLInvViews {
+    int n;
+    float rho[RL_DEV_MAX_PLANES];
+    RLInvParam lv[RL_DEV_MAX_VIEWS];
+    RLInvParam full[RL_DEV_MAX_VIEWS];
+};
+
+// Per-pixel inverse-warp coefficients: offset = a + f_v (g + rho h) / (z0 + rho tz).
+struct RLInvWarp {
+    float gx, gy, hx, hy, z0, tz, ax, ay;
+};
+
+__device__ __forceinline__ RLInvWarp rl_inv_coeffs(const RLInvParam& P, float u, float v) {
+    RLInvWarp c;
+    const float mx = (u - P.cxr) * P.inv_fxr;
+    const float my = (v - P.cyr) * P.inv_fyr;
+    const float ex = fmaf(P.F[0], mx, fmaf(P.F[1], my, P.F[2]));
+    const float ey = fmaf(P.F[3], mx, fmaf(P.F[4], my, P.F[5]));
+    const float ez = fmaf(P.F[6], mx, fmaf(P.F[7], my, P.F[8]));
+    c.gx = fmaf(-mx, ez, ex);
+    c.gy = fmaf(-my, ez, ey);
+    c.hx = fmaf(-mx, P.t[2], P.t[0]);
+    c.hy = fmaf(-my, P.t[2], P.t[1]);
+    c.z0 = 1.0f + ez;
+    c.tz = P.t[2];
+    c.ax = fmaf(P.dfx, mx, P.dcx);
+    c.ay = fmaf(P.dfy, my, P.dcy);
+    return c;
+}
+
+__device__ __forceinline__ RLTaps rl_inv_taps(const RLInvWarp& c, const RLInvParam& P, float rho, int u, int v) {
+    RLTaps t;
+    const float Z = fmaf(rho, c.tz, c.z0);
+    const float inv = 1.0f / Z;
+    const float dx = fmaf(P.fxv, fmaf(rho, c.hx, c.gx) * inv, c.ax);
+    const float dy = fmaf(P.fyv, fmaf(rho, c.hy, c.gy) * inv, c.ay);
+    const float flx = floorf(dx), fly = floorf(dy);
+    t.fx = dx - flx;
+    t.fy = dy - fly;
+    t.x0 = u + (int)flx;
+    t.y0 = v + (int)fly;
+    t.ok = Z > 0.0f && fabsf(dx) < 1.0e7f && fabsf(dy) < 1.0e7f;
+    return t;
+}
+
 // ---------------------------------------------------------------- storage types
 
 template <typename T> struct RLStore;

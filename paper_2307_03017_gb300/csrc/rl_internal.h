@@ -94,3 +94,11 @@ rl_status rl_launch_downsample_f32(const float* x, int P, int H, int W, int C, i
 rl_status rl_launch_update(void* M, rl_dtype dt, int D, int H, int W, int level, const uint8_t* S, const float* G,
                            int k, float lambda, int clamp01, cudaStream_t s, const void* Ml = nullptr,
                            float lambda_s = 0.f);
+
+// Alpha weights of the MPI warped into each view (Eq. eq_gradient): A device [N][D][H][W].
+rl_status rl_launch_view_alpha(const void* M, rl_dtype dt, int D, int H, int W, const RLViews& views, float* A,
+                               cudaStream_t s);
+// Sparsified gradient volume V [4N+4][k][h][w] from the level MPI Ml [D][h][w][4], the
+// selection S [k][h][w], the view alpha weights A [N][D][h][w] and full-resolution images.
+rl_status rl_launch_volume(const void* Ml, rl_dtype dt, int D, int h, int w, int level, const uint8_t* S, int k,
+                           const float* A, const float* images, const RLInvViews& iv, float* V, cudaStream_t s);

@@ -1,0 +1,153 @@
+// volume.cu -- the sparsified gradient volume V_s of Sec. 3.3 (Eq. eq_simplifiedGradients and
+// eq_V): for every kept voxel (slot j of level pixel p, plane d = S[j][p]) the C = 4N + 4
+// channels [P (3N, view-major), A^{w^-1}_1..N (N), M_l (4)], stored [C][k][h][w] FP32.
+//
+// k_view_alpha (one thread per view pixel q, all views in one launch, view-fastest blocks):
+//   the alpha weights of the level MPI warped into view i (Eq. eq_gradient on M_i),
+//   A_{i,d}(q) = alpha_d(q) prod_{j>d}(1 - alpha_j(q)), nearest plane first, stored
+//   [N][D][h][w] FP32.  The warp and the bilinear alpha sample are the render's.
+// k_volume (one thread per kept voxel): the level pixel carried into view i by the inverse
+//   warp (reference -> view) at plane d; a bilinear sample (zero padding) of A_{i,d} there;
+//   the PSV channels as the mean of the full-resolution PSV samples of the 2^l x 2^l child
+//   pixels (Sec. 3.2 downsamples the full-resolution volume); and M_l[d][p].
+#include "rl_internal.h"
+
+namespace {
+
+constexpr int kAlphaBX = 32, kAlphaBY = 4;
+
+// Bilinear sample (zero padding per tap) of the alpha channel of one plane [H][W][4].
+template <typename Tm>
+__device__ __forceinline__ float sample_alpha(const Tm* __restrict__ plane, int H, int W, const RLTaps& t) {
+    if (!t.ok) return 0.f;
+    const float w00 = (1.f - t.fx) * (1.f - t.fy), w10 = t.fx * (1.f - t.fy);
+    const float w01 = (1.f - t.fx) * t.fy, w11 = t.fx * t.fy;
+    const bool x0in = (unsigned)t.x0 < (unsigned)W, x1in = (unsigned)(t.x0 + 1) < (unsigned)W;
+    const bool y0in = (unsigned)t.y0 < (unsigned)H, y1in = (unsigned)(t.y0 + 1) < (unsigned)H;
+    const size_t r0 = (size_t)t.y0 * W, r1 = r0 + W;
+    float a = 0.f;
+    if (y0in && x0in) a = fmaf(w00, RLStore<Tm>::load1(plane + (r0 + t.x0) * 4 + 3), a);
+    if (y0in && x1in) a = fmaf(w10, RLStore<Tm>::load1(plane + (r0 + t.x0 + 1) * 4 + 3), a);
+    if (y1in && x0in) a = fmaf(w01, RLStore<Tm>::load1(plane + (r1 + t.x0) * 4 + 3), a);
+    if (y1in && x1in) a = fmaf(w11, RLStore<Tm>::load1(plane + (r1 + t.x0 + 1) * 4 + 3), a);
+    return a;
+}
+
+// Bilinear sample (zero padding per tap) of a [H][W][C] FP32 map; C = 1 or 3.
+template <int C>
+__device__ __forceinline__ void sample_map(const float* __restrict__ img, int H, int W, const RLTaps& t, float* out) {
+#pragma unroll
+    for (int c = 0; c < C; ++c) out[c] = 0.f;
+    if (!t.ok) return;
+    const float wt[4] = {(1.f - t.fx) * (1.f - t.fy), t.fx * (1.f - t.fy), (1.f - t.fx) * t.fy, t.fx * t.fy};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int x = t.x0 + (k & 1), y = t.y0 + (k >> 1);
+        if ((unsigned)x >= (unsigned)W || (unsigned)y >= (unsigned)H) continue;
+        const float* v = img + ((size_t)y * W + x) * C;
+#pragma unroll
+        for (int c = 0; c < C; ++c) out[c] = fmaf(wt[k], __ldg(v + c), out[c]);
+    }
+}
+
+template <typename Tm>
+__global__ void __launch_bounds__(kAlphaBX * kAlphaBY)
+k_view_alpha(const Tm* __restrict__ M, int D, int H, int W, const __grid_constant__ RLViews views,
+             float* __restrict__ A) {
+    const int view = blockIdx.x;  // grid (views, tiles_x, tiles_y)
+    const int qx = blockIdx.y * kAlphaBX + threadIdx.x;
+    const int qy = blockIdx.z * kAlphaBY + threadIdx.y;
+    if (qx >= W || qy >= H) return;
+    const RLWarp w = rl_warp_coeffs(views.v[view], (float)qx, (float)qy);
+    const size_t plane = (size_t)H * W * 4, hw = (size_t)H * W;
+    float* out = A + (size_t)view * D * hw + (size_t)qy * W + qx;
+    float T = 1.f;
+    for (int d = D - 1; d >= 0; --d) {
+        const RLTaps t = rl_taps(w, views.rho[d], qx, qy);
+        const float a = sample_alpha(M + d * plane, H, W, t);
+        out[(size_t)d * hw] = a * T;
+        T = T * (1.f - a);
+    }
+}
+
+template <typename Tm>
+__global__ void __launch_bounds__(128)
+k_volume(const Tm* __restrict__ Ml, int D, int h, int w, int level, const uint8_t* __restrict__ S, int k,
+         const float* __restrict__ A, const float* __restrict__ images, const __grid_constant__ RLInvViews iv,
+         float* __restrict__ V) {
+    const long long hw = (long long)h * w;
+    const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y;
+    if (p >= hw) return;
+    const int y = (int)(p / w), x = (int)(p % w);
+    const int d = __ldg(S + (size_t)j * hw + p);
+    const int N = iv.n;
+    const size_t cstride = (size_t)k * hw;  // channel stride of V
+    float* out = V + (size_t)j * hw + p;
+    if (d >= D) {  // not a plane: the voxel's channels are zero
+        for (int c = 0; c < 4 * N + 4; ++c) out[(size_t)c * cstride] = 0.f;
+        return;
+    }
+    const float rho = iv.rho[d];
+    const int s = 1 << level, H = h << level, W = w << level;
+    const float inv_area = 1.f / (float)(s * s);
+    for (int i = 0; i < N; ++i) {
+        // inverse-warped alpha weight of view i, at level l
+        const RLInvWarp c = rl_inv_coeffs(iv.lv[i], (float)x, (float)y);
+        float a;
+        sample_map<1>(A + ((size_t)i * D + d) * hw, h, w, rl_inv_taps(c, iv.lv[i], rho, x, y), &a);
+        out[(size_t)(3 * N + i) * cstride] = a;
+        // PSV of view i: mean over the full-resolution children of p
+        float acc[3] = {0.f, 0.f, 0.f};
+        const float* img = images + (size_t)i * H * W * 3;
+        for (int yy = 0; yy < s; ++yy)
+            for (int xx = 0; xx < s; ++xx) {
+                const int X = x * s + xx, Y = y * s + yy;
+                const RLInvWarp cf = rl_inv_coeffs(iv.full[i], (float)X, (float)Y);
+                float v[3];
+                sample_map<3>(img, H, W, rl_inv_taps(cf, iv.full[i], rho, X, Y), v);
+                acc[0] += v[0];
+                acc[1] += v[1];
+                acc[2] += v[2];
+            }
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch) out[(size_t)(3 * i + ch) * cstride] = acc[ch] * inv_area;
+    }
+    const float4 m = RLStore<Tm>::load4(Ml + ((size_t)d * hw + p) * 4);
+    out[(size_t)(4 * N + 0) * cstride] = m.x;
+    out[(size_t)(4 * N + 1) * cstride] = m.y;
+    out[(size_t)(4 * N + 2) * cstride] = m.z;
+    out[(size_t)(4 * N + 3) * cstride] = m.w;
+}
+
+}  // namespace
+
+rl_status rl_launch_view_alpha(const void* M, rl_dtype dt, int D, int H, int W, const RLViews& views, float* A,
+                               cudaStream_t s) {
+    const dim3 grid((unsigned)views.n, (unsigned)((W + kAlphaBX - 1) / kAlphaBX),
+                    (unsigned)((H + kAlphaBY - 1) / kAlphaBY));
+    const dim3 block(kAlphaBX, kAlphaBY);
+    if (dt == RL_F32) {
+        RLTraceScope ts("view_alpha_f32", s);
+        k_view_alpha<float><<<grid, block, 0, s>>>((const float*)M, D, H, W, views, A);
+    } else {
+        RLTraceScope ts("view_alpha_bf16", s);
+        k_view_alpha<__nv_bfloat16><<<grid, block, 0, s>>>((const __nv_bfloat16*)M, D, H, W, views, A);
+    }
+    return rl_check_launch("view_alpha");
+}
+
+rl_status rl_launch_volume(const void* Ml, rl_dtype dt, int D, int h, int w, int level, const uint8_t* S, int k,
+                           const float* A, const float* images, const RLInvViews& iv, float* V, cudaStream_t s) {
+    const long long hw = (long long)h * w;
+    const dim3 grid((unsigned)((hw + 127) / 128), (unsigned)k);
+    if (dt == RL_F32) {
+        RLTraceScope ts("volume_f32", s);
+        k_volume<float><<<grid, 128, 0, s>>>((const float*)Ml, D, h, w, level, S, k, A, images, iv, V);
+    } else {
+        RLTraceScope ts("volume_bf16", s);
+        k_volume<__nv_bfloat16><<<grid, 128, 0, s>>>((const __nv_bfloat16*)Ml, D, h, w, level, S, k, A, images, iv,
+                                                     V);
+    }
+    return rl_check_launch("volume");
+}

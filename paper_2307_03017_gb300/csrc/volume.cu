@@ -6,10 +6,10 @@
 //   the alpha weights of the level MPI warped into view i (Eq. eq_gradient on M_i),
 //   A_{i,d}(q) = alpha_d(q) prod_{j>d}(1 - alpha_j(q)), nearest plane first, stored
 //   [N][D][h][w] FP32.  The warp and the bilinear alpha sample are the render's.
-// k_volume (one thread per kept voxel): the level pixel carried into view i by the inverse
-//   warp (reference -> view) at plane d; a bilinear sample (zero padding) of A_{i,d} there;
-//   the PSV channels as the mean of the full-resolution PSV samples of the 2^l x 2^l child
-//   pixels (Sec. 3.2 downsamples the full-resolution volume); and M_l[d][p].
+// k_volume (one thread per kept voxel and view): the level pixel carried into view i by the
+//   inverse warp (reference -> view) at plane d; a bilinear sample (zero padding) of A_{i,d}
+//   there; the PSV channels as the mean of the full-resolution PSV samples of the 2^l x 2^l
+//   child pixels (Sec. 3.2 downsamples the full-resolution volume); and M_l[d][p].
 #include "rl_internal.h"
 
 namespace {
@@ -75,9 +75,10 @@ __global__ void __launch_bounds__(128)
 k_volume(const Tm* __restrict__ Ml, int D, int h, int w, int level, const uint8_t* __restrict__ S, int k,
          const float* __restrict__ A, const float* __restrict__ images, const __grid_constant__ RLInvViews iv,
          float* __restrict__ V) {
+    // grid (pixel blocks, k, N): one thread per (kept voxel, view); view 0 also writes M_l
     const long long hw = (long long)h * w;
     const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const int j = blockIdx.y;
+    const int j = blockIdx.y, i = blockIdx.z;
     if (p >= hw) return;
     const int y = (int)(p / w), x = (int)(p % w);
     const int d = __ldg(S + (size_t)j * hw + p);
@@ -85,39 +86,44 @@ k_volume(const Tm* __restrict__ Ml, int D, int h, int w, int level, const uint8_
     const size_t cstride = (size_t)k * hw;  // channel stride of V
     float* out = V + (size_t)j * hw + p;
     if (d >= D) {  // not a plane: the voxel's channels are zero
-        for (int c = 0; c < 4 * N + 4; ++c) out[(size_t)c * cstride] = 0.f;
+        out[(size_t)(3 * i) * cstride] = 0.f;
+        out[(size_t)(3 * i + 1) * cstride] = 0.f;
+        out[(size_t)(3 * i + 2) * cstride] = 0.f;
+        out[(size_t)(3 * N + i) * cstride] = 0.f;
+        if (i == 0)
+            for (int c = 0; c < 4; ++c) out[(size_t)(4 * N + c) * cstride] = 0.f;
         return;
     }
     const float rho = iv.rho[d];
     const int s = 1 << level, H = h << level, W = w << level;
     const float inv_area = 1.f / (float)(s * s);
-    for (int i = 0; i < N; ++i) {
-        // inverse-warped alpha weight of view i, at level l
-        const RLInvWarp c = rl_inv_coeffs(iv.lv[i], (float)x, (float)y);
-        float a;
-        sample_map<1>(A + ((size_t)i * D + d) * hw, h, w, rl_inv_taps(c, iv.lv[i], rho, x, y), &a);
-        out[(size_t)(3 * N + i) * cstride] = a;
-        // PSV of view i: mean over the full-resolution children of p
-        float acc[3] = {0.f, 0.f, 0.f};
-        const float* img = images + (size_t)i * H * W * 3;
-        for (int yy = 0; yy < s; ++yy)
-            for (int xx = 0; xx < s; ++xx) {
-                const int X = x * s + xx, Y = y * s + yy;
-                const RLInvWarp cf = rl_inv_coeffs(iv.full[i], (float)X, (float)Y);
-                float v[3];
-                sample_map<3>(img, H, W, rl_inv_taps(cf, iv.full[i], rho, X, Y), v);
-                acc[0] += v[0];
-                acc[1] += v[1];
-                acc[2] += v[2];
-            }
+    // inverse-warped alpha weight of view i, at level l
+    const RLInvWarp c = rl_inv_coeffs(iv.lv[i], (float)x, (float)y);
+    float a;
+    sample_map<1>(A + ((size_t)i * D + d) * hw, h, w, rl_inv_taps(c, iv.lv[i], rho, x, y), &a);
+    out[(size_t)(3 * N + i) * cstride] = a;
+    // PSV of view i: mean over the full-resolution children of p
+    float acc[3] = {0.f, 0.f, 0.f};
+    const float* img = images + (size_t)i * H * W * 3;
+    for (int yy = 0; yy < s; ++yy)
+        for (int xx = 0; xx < s; ++xx) {
+            const int X = x * s + xx, Y = y * s + yy;
+            const RLInvWarp cf = rl_inv_coeffs(iv.full[i], (float)X, (float)Y);
+            float v[3];
+            sample_map<3>(img, H, W, rl_inv_taps(cf, iv.full[i], rho, X, Y), v);
+            acc[0] += v[0];
+            acc[1] += v[1];
+            acc[2] += v[2];
+        }
 #pragma unroll
-        for (int ch = 0; ch < 3; ++ch) out[(size_t)(3 * i + ch) * cstride] = acc[ch] * inv_area;
+    for (int ch = 0; ch < 3; ++ch) out[(size_t)(3 * i + ch) * cstride] = acc[ch] * inv_area;
+    if (i == 0) {
+        const float4 m = RLStore<Tm>::load4(Ml + ((size_t)d * hw + p) * 4);
+        out[(size_t)(4 * N + 0) * cstride] = m.x;
+        out[(size_t)(4 * N + 1) * cstride] = m.y;
+        out[(size_t)(4 * N + 2) * cstride] = m.z;
+        out[(size_t)(4 * N + 3) * cstride] = m.w;
     }
-    const float4 m = RLStore<Tm>::load4(Ml + ((size_t)d * hw + p) * 4);
-    out[(size_t)(4 * N + 0) * cstride] = m.x;
-    out[(size_t)(4 * N + 1) * cstride] = m.y;
-    out[(size_t)(4 * N + 2) * cstride] = m.z;
-    out[(size_t)(4 * N + 3) * cstride] = m.w;
 }
 
 }  // namespace
@@ -140,7 +146,7 @@ rl_status rl_launch_view_alpha(const void* M, rl_dtype dt, int D, int H, int W, 
 rl_status rl_launch_volume(const void* Ml, rl_dtype dt, int D, int h, int w, int level, const uint8_t* S, int k,
                            const float* A, const float* images, const RLInvViews& iv, float* V, cudaStream_t s) {
     const long long hw = (long long)h * w;
-    const dim3 grid((unsigned)((hw + 127) / 128), (unsigned)k);
+    const dim3 grid((unsigned)((hw + 127) / 128), (unsigned)k, (unsigned)iv.n);
     if (dt == RL_F32) {
         RLTraceScope ts("volume_f32", s);
         k_volume<float><<<grid, 128, 0, s>>>((const float*)Ml, D, h, w, level, S, k, A, images, iv, V);

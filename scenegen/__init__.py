@@ -34,7 +34,7 @@ import numpy as np
 __all__ = [
     "Camera", "Layer", "Scene", "intrinsics", "random_rotation", "look_at",
     "plane_inverse_depths", "make_scene", "raycast", "workload", "serve_requests",
-    "WORKLOADS",
+    "WORKLOADS", "LgdWeights", "lgd_weights",
 ]
 
 
@@ -357,3 +357,39 @@ def serve_requests(n: int = 2000, rate: float = 200.0, seed: int = 12345) -> lis
         out.append(dict(id=r, arrival=t, H=H, W=W, D=int(rng.choice([16, 32, 48, 64])),
                         N=int(rng.integers(2, 7)), iters=int(rng.integers(2, 4)), seed=int(rng.integers(0, 2**31))))
     return out
+
+
+@dataclass
+class LgdWeights:
+    """Random parameters of the learned-update network (no trained weights exist here):
+    ``conv_w[l]`` [F][C_l][3][3][3] and ``conv_b[l]`` [F] for the five 3x3x3 blocks, their
+    batch-norm statistics and affine terms ``bn_gamma/bn_beta/bn_mean/bn_var[l]`` [F], and the
+    final 1x1x1 layer ``out_w`` [4][F], ``out_b`` [4].  All float32."""
+    conv_w: list
+    conv_b: list
+    bn_gamma: list
+    bn_beta: list
+    bn_mean: list
+    bn_var: list
+    out_w: np.ndarray
+    out_b: np.ndarray
+    eps: float = 1e-5
+
+
+def lgd_weights(seed: int, c_in: int, width: int = 32, blocks: int = 5) -> LgdWeights:
+    """He-normal convolution weights and plausible batch-norm statistics, fixed by ``seed``."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    cw, cb, g, b, m, v = [], [], [], [], [], []
+    c = c_in
+    for _ in range(blocks):
+        fan_in = c * 27
+        cw.append((rng.standard_normal((width, c, 3, 3, 3)) * math.sqrt(2.0 / fan_in)).astype(np.float32))
+        cb.append((rng.standard_normal(width) * 0.05).astype(np.float32))
+        g.append(rng.uniform(0.5, 1.5, width).astype(np.float32))
+        b.append((rng.standard_normal(width) * 0.1).astype(np.float32))
+        m.append((rng.standard_normal(width) * 0.1).astype(np.float32))
+        v.append(rng.uniform(0.5, 2.0, width).astype(np.float32))
+        c = width
+    out_w = (rng.standard_normal((4, width)) * math.sqrt(1.0 / width) * 0.1).astype(np.float32)
+    out_b = np.zeros(4, dtype=np.float32)
+    return LgdWeights(cw, cb, g, b, m, v, out_w, out_b)

@@ -189,6 +189,60 @@ rl_status reallife_gradient_volume(const rl_mpi* m, const float* images, const r
                                    int level, int selection, uint8_t* S_out, float* V, void* ws, size_t ws_bytes,
                                    cudaStream_t stream);
 
+/* ---------------------------------------------------------- learned update */
+
+/* Parameters of the learned-update network N_w of Sec. 3.3 ("Sparse Gradient Update"), as
+ * trained: five blocks of 3x3x3 convolution (zero padding 1), batch norm and ReLU, then a
+ * 1x1x1 convolution to the 4-channel (R, G, B, alpha) residual (Sec. 4 names the block
+ * structure; kernel size, 32 channels per block and inference-mode batch norm are this
+ * library's reading).  All pointers are device FP32:
+ *   conv_w[l] [32][c_l][3][3][3] (c_0 = c_in, else 32), conv_b[l], bn_*[l] [32];
+ *   out_w [4][32], out_b [4].  c_in = 4N + 4 <= 32 for the volume of N views. */
+typedef struct {
+    int c_in;
+    float eps;
+    const float* conv_w[5];
+    const float* conv_b[5];
+    const float* bn_gamma[5];
+    const float* bn_beta[5];
+    const float* bn_mean[5];
+    const float* bn_var[5];
+    const float* out_w;
+    const float* out_b;
+} rl_lgd_params;
+
+/* Bytes of a packed network (BF16 weights with batch norm folded, FP32 biases). */
+size_t reallife_lgd_net_bytes(void);
+
+/* Folds batch norm into each block (w' = w gamma / sqrt(var + eps), b' = (b - mean) gamma /
+ * sqrt(var + eps) + beta), rounds the weights to BF16 (nearest even) and packs them for the
+ * tensor-core kernels.  net: device, 256-byte aligned, reallife_lgd_net_bytes() bytes;
+ * written asynchronously on `stream`.  RL_EINVAL for NULL parameters or c_in outside [1, 32]. */
+rl_status reallife_lgd_prepare(const rl_lgd_params* p, void* net, cudaStream_t stream);
+
+/* Workspace of reallife_lgd_forward: two BF16 activation volumes of k x h x w x 32. */
+size_t reallife_lgd_workspace_bytes(int k, int h, int w);
+
+/* N_w(V): V device [C][k][h][w] FP32 (C <= 32; e.g. the volume of reallife_gradient_volume),
+ * residual device [k][h][w][4] FP32 (16-byte aligned, overwritten).  The input is rounded to
+ * BF16, every block accumulates in FP32 on the tensor cores and stores BF16 activations; the
+ * last block's output feeds the 1x1x1 layer in FP32.  ws: device, 256-byte aligned, at least
+ * reallife_lgd_workspace_bytes(k, h, w) bytes (RL_ENOMEM when smaller). */
+rl_status reallife_lgd_forward(const void* net, const float* V, int C, int k, int h, int w, float* residual,
+                               void* ws, size_t ws_bytes, cudaStream_t stream);
+
+/* Workspace of reallife_lgd_step (any level). */
+size_t reallife_lgd_step_workspace_bytes(int N, int D, int H, int W, int k, rl_dtype dtype);
+
+/* One learned HSGD iteration at `level` (Sec. 3.3, M_{n+1} = M_n + R(N_w(V_s), S)):
+ * reallife_gradient_volume, reallife_lgd_forward, then for every full-resolution pixel (y, x)
+ * and slot j, d = S[j][y>>l][x>>l]: M[d][y][x] += residual[j][y>>l][x>>l], clamped to [0, 1]
+ * when clamp01, rounded to the storage type.  N <= 7 (4N + 4 <= 32 channels).  S_out: device
+ * [k][h][w] or NULL.  Same argument checks as reallife_gradient_volume. */
+rl_status reallife_lgd_step(rl_mpi* m, const float* images, const rl_camera* src, int N, int k, int level,
+                            int selection, int clamp01, const void* net, uint8_t* S_out, void* ws, size_t ws_bytes,
+                            cudaStream_t stream);
+
 /* -------------------------------------------------------- steps of the iteration */
 
 /* Down^l of P stacked [H][W][C] FP32 slices (2x2 box average applied l times, computed

@@ -219,6 +219,68 @@ def reallife_gradient_volume(m: Mpi, images: torch.Tensor, src, k: int, level: i
     return V, S_out
 
 
+class LgdNet:
+    """The learned-update network on the device: the trained parameters (FP32 tensors, kept
+    alive here) packed by ``reallife_lgd_prepare`` into ``packed`` (BF16 weights with batch norm
+    folded).  ``params`` is any object with the fields of ``scenegen.LgdWeights``."""
+
+    def __init__(self, params, device="cuda", stream=None):
+        def t(a):
+            return torch.as_tensor(np.ascontiguousarray(a, dtype=np.float32)).to(device)
+        self.c_in = int(params.conv_w[0].shape[1])
+        self._keep = []
+        p = _lib.RlLgdParams()
+        p.c_in, p.eps = self.c_in, float(params.eps)
+        for name in ("conv_w", "conv_b", "bn_gamma", "bn_beta", "bn_mean", "bn_var"):
+            arr = getattr(p, name)
+            for l, a in enumerate(getattr(params, name)):
+                ta = t(a)
+                self._keep.append(ta)
+                arr[l] = ta.data_ptr()
+        ow, ob = t(params.out_w), t(params.out_b)
+        self._keep += [ow, ob]
+        p.out_w, p.out_b = ow.data_ptr(), ob.data_ptr()
+        self.packed = torch.empty(int(_lib.lib().reallife_lgd_net_bytes()), dtype=torch.uint8, device=device)
+        _lib.check("reallife_lgd_prepare", _lib.lib().reallife_lgd_prepare(ctypes.byref(p), _ptr(self.packed),
+                                                                          _stream(stream)))
+
+
+def reallife_lgd_forward(net: LgdNet, V: torch.Tensor, residual: torch.Tensor | None = None,
+                         ws: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """N_w(V): V [C][k][h][w] float32 (C <= 32) -> residual [k][h][w][4] float32."""
+    C, k, h, w = V.shape
+    if V.dtype != torch.float32:
+        raise ValueError("V must be float32")
+    if residual is None:
+        residual = torch.empty((k, h, w, 4), dtype=torch.float32, device=V.device)
+    _check_f32(residual, (k, h, w, 4), "residual")
+    if ws is None:
+        ws = torch.empty(int(_lib.lib().reallife_lgd_workspace_bytes(k, h, w)), dtype=torch.uint8, device=V.device)
+    _lib.check("reallife_lgd_forward", _lib.lib().reallife_lgd_forward(
+        _ptr(net.packed), _ptr(V), C, k, h, w, _ptr(residual), _ptr(ws), ws.numel(), _stream(stream)))
+    return residual
+
+
+def reallife_lgd_step_workspace_bytes(N: int, D: int, H: int, W: int, k: int, dtype=torch.float32) -> int:
+    return int(_lib.lib().reallife_lgd_step_workspace_bytes(N, D, H, W, k, _DT[dtype]))
+
+
+def reallife_lgd_step(m: Mpi, images: torch.Tensor, src, k: int, net: LgdNet, level: int = 0,
+                      selection: int = SELECT_TOPK, clamp: bool = True, S_out: torch.Tensor | None = None,
+                      ws: torch.Tensor | None = None, stream=None):
+    """One learned HSGD iteration on ``m`` in place: M <- M + R(N_w(V_s), S); returns S_out."""
+    N = len(src)
+    _check_f32(images, (N, m.H, m.W, 3), "images")
+    if ws is None:
+        ws = torch.empty(reallife_lgd_step_workspace_bytes(N, m.D, m.H, m.W, k, m.data.dtype), dtype=torch.uint8,
+                         device=m.data.device)
+    ms = m.c_struct()
+    _lib.check("reallife_lgd_step", _lib.lib().reallife_lgd_step(
+        ctypes.byref(ms), _ptr(images), _lib.cameras(src), N, int(k), int(level), int(selection), int(bool(clamp)),
+        _ptr(net.packed), _ptr(S_out), _ptr(ws), ws.numel(), _stream(stream)))
+    return S_out
+
+
 def reallife_downsample_f32(x: torch.Tensor, level: int, out: torch.Tensor | None = None, stream=None):
     """Down^l of ``x[P][H][W][C]`` float32 (2^l x 2^l box average)."""
     P, H, W, C = x.shape

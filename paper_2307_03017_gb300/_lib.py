@@ -19,7 +19,9 @@ EXPORTS = [
     "reallife_sparse_update", "reallife_render_backward", "reallife_warp_offsets", "reallife_trace_enable",
     "reallife_trace_read", "reallife_strerror", "reallife_last_error", "reallife_set_kernel_path",
     "reallife_device_status", "reallife_hsgd_step_noalloc", "reallife_trace_release_captured",
-    "reallife_gradient_volume_workspace_bytes", "reallife_gradient_volume",
+    "reallife_gradient_volume_workspace_bytes", "reallife_gradient_volume", "reallife_lgd_net_bytes",
+    "reallife_lgd_prepare", "reallife_lgd_workspace_bytes", "reallife_lgd_forward",
+    "reallife_lgd_step_workspace_bytes", "reallife_lgd_step",
 ]
 
 
@@ -39,6 +41,14 @@ class RlMpi(ctypes.Structure):
 class RlHsgdParams(ctypes.Structure):
     _fields_ = [("k", ctypes.c_int), ("lambda_", ctypes.c_float), ("clamp01", ctypes.c_int), ("level", ctypes.c_int),
                 ("selection", ctypes.c_int), ("lambda_s", ctypes.c_float)]
+
+
+class RlLgdParams(ctypes.Structure):
+    _fields_ = [("c_in", ctypes.c_int), ("eps", ctypes.c_float),
+                ("conv_w", ctypes.c_void_p * 5), ("conv_b", ctypes.c_void_p * 5),
+                ("bn_gamma", ctypes.c_void_p * 5), ("bn_beta", ctypes.c_void_p * 5),
+                ("bn_mean", ctypes.c_void_p * 5), ("bn_var", ctypes.c_void_p * 5),
+                ("out_w", ctypes.c_void_p), ("out_b", ctypes.c_void_p)]
 
 
 class RlTraceEntry(ctypes.Structure):
@@ -93,6 +103,12 @@ def _declare(lib):
         "reallife_gradient_volume_workspace_bytes": (c_size_t, [c_int, c_int, c_int, c_int, c_int, c_int]),
         "reallife_gradient_volume": (c_int, [mpi_p, vp, cam_p, c_int, c_int, c_int, c_int, vp, vp, vp, c_size_t,
                                              vp]),
+        "reallife_lgd_net_bytes": (c_size_t, []),
+        "reallife_lgd_prepare": (c_int, [ctypes.POINTER(RlLgdParams), vp, vp]),
+        "reallife_lgd_workspace_bytes": (c_size_t, [c_int, c_int, c_int]),
+        "reallife_lgd_forward": (c_int, [vp, vp, c_int, c_int, c_int, c_int, vp, vp, c_size_t, vp]),
+        "reallife_lgd_step_workspace_bytes": (c_size_t, [c_int, c_int, c_int, c_int, c_int, c_int]),
+        "reallife_lgd_step": (c_int, [mpi_p, vp, cam_p, c_int, c_int, c_int, c_int, c_int, vp, vp, vp, c_size_t, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)

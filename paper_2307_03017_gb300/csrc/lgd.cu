@@ -1,0 +1,534 @@
+// lgd.cu -- the learned update of Sec. 3.3 ("Sparse Gradient Update"): the network N_w over
+// the sparsified volume V_s [C][k][h][w] -- five blocks of 3x3x3 convolution (inference batch
+// norm folded into weights and bias) with ReLU, then a 1x1x1 convolution to the 4-channel
+// (R, G, B, alpha) residual -- as implicit GEMMs on the tcgen05 tensor cores, and the learned
+// HSGD iteration M <- clamp(M + R(N_w(V_s), S)).
+//
+// Activations: BF16, 32 channels, chunked channels-last layout act[z][y][4][xp][8] (four
+// chunks of 8 channels; xp = x padded to a multiple of 8 with zero voxels; one chunk row of a
+// (z, y) line is contiguous).  Eight voxels x 8 channels of a chunk row are one 128-byte
+// core matrix of tcgen05.mma's K-major, no-swizzle operand layout, so one TMA tile copy of box
+// {64, 18, 4} (18 core matrices of 4 chunks) at (0, x0/8 - 1, 0, y + dy - 1, z + dz - 1)
+// lands in shared memory as [chunk][144 rows][8]: 8-row groups 128 bytes apart along M, the
+// two core matrices of a 16-wide K step 144 x 16 bytes apart.  The copy engine zero-fills
+// rows and planes outside the volume: the convolution's zero padding.  The taps dx = -1, 0,
+// +1 are the same halo read from rows 7, 8 and 9 on (the operand start moved by 16 bytes a
+// row).
+//
+// Output tile: 128 consecutive voxels of one (z, y) line x 32 channels, accumulated in FP32 in
+// tensor memory over 9 halos x 3 shifts x 2 K steps = 54 MMAs of 128x32x16 (BF16 inputs).
+// Persistent CTAs (one per SM), warp-specialised: warp 0 issues the TMA copies, warp 1 the
+// MMAs (one lane), warps 2-5 drain the two tensor-memory accumulators: bias, ReLU, BF16
+// rounding and the store of the next layer's activations; after the last block they also
+// apply the 1x1x1 layer and store the FP32 residual [z][y][x][4].
+//
+// Every mbarrier wait is bounded; a wait that gives up sets RL_DEVFLAG_TIMEOUT, the roles
+// stop, the producer waits (bounded) for its copies in flight and the MMA lane for its MMAs,
+// and tensor memory is freed before the CTA exits.
+#include "rl_internal.h"
+#include "rl_tma.cuh"
+
+namespace {
+
+using namespace rltma;
+
+constexpr int kF = 32;                           // channels of every block
+constexpr int kTileM = 128;                      // voxels per output tile
+constexpr int kHaloCM = kTileM / 8 + 2;          // core matrices (8 voxels) of one staged halo
+constexpr int kHalo = kHaloCM * 8;               // 144 rows: x0 - 8 .. x0 + 135
+constexpr int kChunkBytes = kHalo * 16;          // one 8-channel chunk of a halo
+constexpr int kStageBytes = 4 * kChunkBytes;     // 9216
+constexpr int kStages = 12;
+constexpr int kTapBytes = 4 * kF * 16;           // weights of one tap: [chunk][32][8] BF16
+constexpr int kWBytes = 27 * kTapBytes;          // 55296
+constexpr int kThreads = 192;
+constexpr uint32_t kTmemCols = 256;              // accumulators at columns 0 and 128
+constexpr uint32_t kAccStride = 128;
+// instruction descriptor: D FP32, A and B BF16, both K-major, N = 32, M = 128
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kF >> 3) << 17) |
+                            ((uint32_t)(kTileM >> 4) << 24);
+static_assert(kIdesc == 0x08080490u, "instruction descriptor");
+
+// Packed network: per block [27 taps][4 chunks][32 out][8 in] BF16, then biases, then the
+// 1x1x1 layer.
+constexpr size_t kNetW = 0;
+constexpr size_t kNetBias = 5 * (size_t)kWBytes;              // 5 x 32 FP32
+constexpr size_t kNetOutW = kNetBias + 5 * kF * 4;            // 4 x 32 FP32
+constexpr size_t kNetOutB = kNetOutW + 4 * kF * 4;            // 4 FP32
+constexpr size_t kNetBytes = (kNetOutB + 16 + 255) & ~(size_t)255;
+
+struct SmemLayout {
+    static constexpr int W = 0;
+    static constexpr int A = W + kWBytes;
+    static constexpr int BAR = A + kStages * kStageBytes;
+    static constexpr int NBAR = 2 * kStages + 6;
+    static constexpr int TSLOT = BAR + NBAR * 8;
+    static constexpr int BIAS = TSLOT + 16;
+    static constexpr int OUTW = BIAS + kF * 4;
+    static constexpr int OUTB = OUTW + 4 * kF * 4;
+    static constexpr int TOTAL = OUTB + 16;
+};
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ void tma_load_5d(void* dst, const CUtensorMap* map, uint64_t* bar, int c0, int c1, int c2,
+                                            int c3, int c4) {
+    asm volatile(
+        "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5, %6, "
+        "%7}], [%2];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4)
+        : "memory");
+}
+
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(reinterpret_cast<uint64_t>(src)), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// Shared-memory matrix descriptor: no swizzle, byte offsets between core matrices along K
+// (lbo) and between 8-row groups along M/N (sbo).
+__device__ __forceinline__ uint64_t umma_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+    uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFFu);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+    d |= 1ull << 46;
+    return d;
+}
+
+__device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t accumulate) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(kIdesc), "r"(accumulate)
+        : "memory");
+}
+
+__device__ __forceinline__ void umma_commit(uint64_t* bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
+// 32 lanes x 32 consecutive FP32 columns: thread t of the warp gets lane (base + t).
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ void flag_timeout(unsigned int* status) { atomicOr(status, RL_DEVFLAG_TIMEOUT); }
+
+template <bool FINAL>
+__global__ void __launch_bounds__(kThreads, 1)
+k_conv_tc(const __grid_constant__ CUtensorMap in_map, const unsigned char* __restrict__ net, int layer, int K, int H,
+          int W, int Wp, __nv_bfloat16* __restrict__ out_act, float* __restrict__ out_res,
+          unsigned int* __restrict__ status) {
+    extern __shared__ __align__(1024) unsigned char smem[];
+    unsigned char* sW = smem + SmemLayout::W;
+    unsigned char* sA = smem + SmemLayout::A;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + SmemLayout::BAR);
+    uint64_t* full = bars;
+    uint64_t* empty = bars + kStages;
+    uint64_t* tfull = bars + 2 * kStages;
+    uint64_t* tempty = tfull + 2;
+    uint64_t* wbar = tempty + 2;
+    uint64_t* mma_done = wbar + 1;  // drain of the MMAs on an abort
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + SmemLayout::TSLOT);
+    float* sBias = reinterpret_cast<float*>(smem + SmemLayout::BIAS);
+    float* sOutW = reinterpret_cast<float*>(smem + SmemLayout::OUTW);
+    float* sOutB = reinterpret_cast<float*>(smem + SmemLayout::OUTB);
+    __shared__ int s_abort;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int tiles_x = (W + kTileM - 1) / kTileM;
+    const int ntiles = K * H * tiles_x;
+    const float* bias_g = reinterpret_cast<const float*>(net + kNetBias) + layer * kF;
+
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < kStages; ++i) {
+            mbar_init(&full[i], 1);
+            mbar_init(&empty[i], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&tfull[b], 1);
+            mbar_init(&tempty[b], 4);
+        }
+        mbar_init(wbar, 1);
+        mbar_init(mma_done, 1);
+        fence_mbar_init();
+        s_abort = 0;
+    }
+    if (threadIdx.x < kF) sBias[threadIdx.x] = bias_g[threadIdx.x];
+    if (FINAL && threadIdx.x < 4 * kF) sOutW[threadIdx.x] = reinterpret_cast<const float*>(net + kNetOutW)[threadIdx.x];
+    if (FINAL && threadIdx.x < 4) sOutB[threadIdx.x] = reinterpret_cast<const float*>(net + kNetOutB)[threadIdx.x];
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
+                     "r"(kTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tslot;
+
+    if (warp == 0 && lane == 0) {
+        // ------------------------------------------------------------- producer
+        mbar_expect_tx(wbar, kWBytes);
+        bulk_load(sW, net + kNetW + (size_t)layer * kWBytes, kWBytes, wbar);
+        int it = 0;
+        bool ok = true;
+        for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+            const int tx = tile % tiles_x;
+            const int zy = tile / tiles_x;
+            const int y = zy % H, z = zy / H;
+            for (int hh = 0; hh < 9 && ok; ++hh, ++it) {
+                const int s = it % kStages, r = it / kStages;
+                if (r > 0 && !mbar_wait(&empty[s], (uint32_t)((r - 1) & 1))) {
+                    ok = false;
+                    break;
+                }
+                if (*(volatile int*)&s_abort) {
+                    ok = false;
+                    break;
+                }
+                mbar_expect_tx(&full[s], kStageBytes);
+                tma_load_5d(sA + s * kStageBytes, &in_map, &full[s], 0, tx * (kTileM / 8) - 1, 0, y + hh % 3 - 1,
+                            z + hh / 3 - 1);
+            }
+        }
+        if (!ok) {
+            flag_timeout(status);
+            s_abort = 1;
+        }
+        // copies in flight: the last load of every stage must have landed before exit; on the
+        // normal path also its release by the MMAs (the tensor core's arrival on empty[s])
+        for (int s = 0; s < kStages && s < it; ++s) {
+            const int last = it - 1 - ((it - 1 - s) % kStages);
+            if (!mbar_wait(&full[s], (uint32_t)((last / kStages) & 1))) flag_timeout(status);
+            if (ok && !mbar_wait(&empty[s], (uint32_t)((last / kStages) & 1))) flag_timeout(status);
+        }
+        if (!mbar_wait(wbar, 0)) flag_timeout(status);
+    } else if (warp == 1 && lane == 0) {
+        // ------------------------------------------------------------- MMA issuer
+        bool ok = mbar_wait(wbar, 0);
+        const uint32_t wbase = smem_u32(sW), abase = smem_u32(sA);
+        int it = 0, t = 0;
+        for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, ++t) {
+            const int b = t & 1, u = t >> 1;
+            if (u > 0 && !mbar_wait(&tempty[b], (uint32_t)((u - 1) & 1))) {
+                ok = false;
+                break;
+            }
+            tc_fence_after();
+            const uint32_t d = tmem + (uint32_t)b * kAccStride;
+            for (int hh = 0; hh < 9; ++hh, ++it) {
+                const int s = it % kStages, r = it / kStages;
+                if (!mbar_wait(&full[s], (uint32_t)(r & 1)) || *(volatile int*)&s_abort) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t st = abase + (uint32_t)(s * kStageBytes);
+#pragma unroll
+                for (int dx = 0; dx < 3; ++dx)
+#pragma unroll
+                    for (int kk = 0; kk < 2; ++kk) {
+                        const int tap = hh * 3 + dx;
+                        const uint64_t ad =
+                            umma_desc(st + (uint32_t)(kk * 2 * kChunkBytes + (7 + dx) * 16), kChunkBytes, 128);
+                        const uint64_t bd = umma_desc(wbase + (uint32_t)(tap * kTapBytes + kk * 2 * kF * 16), kF * 16,
+                                                      128);
+                        umma_bf16(d, ad, bd, (hh | dx | kk) != 0 ? 1u : 0u);
+                    }
+                umma_commit(&empty[s]);  // the stage is free once these MMAs have read it
+            }
+            if (!ok) break;
+            umma_commit(&tfull[b]);
+        }
+        if (!ok) {
+            flag_timeout(status);
+            s_abort = 1;
+            // wait for the MMAs already issued before tensor memory is released
+            umma_commit(mma_done);
+            if (!mbar_wait(mma_done, 0)) flag_timeout(status);
+        }
+    } else if (warp >= 2) {
+        // ------------------------------------------------------------- epilogue
+        const int q = warp & 3;  // tensor-memory lane quarter this warp may access
+        int t = 0;
+        for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++t) {
+            const int b = t & 1, u = t >> 1;
+            bool ok = true;
+            if (lane == 0) ok = mbar_wait(&tfull[b], (uint32_t)(u & 1)) && !*(volatile int*)&s_abort;
+            ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+            if (!ok) {
+                if (lane == 0) {
+                    flag_timeout(status);
+                    s_abort = 1;
+                }
+                break;
+            }
+            tc_fence_after();
+            float acc[32];
+            tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)b * kAccStride, acc);
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&tempty[b]);
+            const int tx = tile % tiles_x;
+            const int zy = tile / tiles_x;
+            const int y = zy % H, z = zy / H;
+            const int x = tx * kTileM + 32 * q + lane;
+            if (x >= (FINAL ? W : Wp)) continue;
+            const bool pad = x >= W;  // padding voxels of a line stay zero
+#pragma unroll
+            for (int c = 0; c < kF; ++c) acc[c] = pad ? 0.f : fmaxf(acc[c] + sBias[c], 0.f);
+            if constexpr (FINAL) {
+                float4 r;
+                r.x = sOutB[0]; r.y = sOutB[1]; r.z = sOutB[2]; r.w = sOutB[3];
+#pragma unroll
+                for (int c = 0; c < kF; ++c) {
+                    r.x = fmaf(sOutW[0 * kF + c], acc[c], r.x);
+                    r.y = fmaf(sOutW[1 * kF + c], acc[c], r.y);
+                    r.z = fmaf(sOutW[2 * kF + c], acc[c], r.z);
+                    r.w = fmaf(sOutW[3 * kF + c], acc[c], r.w);
+                }
+                *reinterpret_cast<float4*>(out_res + (((size_t)z * H + y) * W + x) * 4) = r;
+            } else {
+#pragma unroll
+                for (int ch = 0; ch < 4; ++ch) {
+                    uint4 pk;
+                    __nv_bfloat162 p0 = __floats2bfloat162_rn(acc[ch * 8 + 0], acc[ch * 8 + 1]);
+                    __nv_bfloat162 p1 = __floats2bfloat162_rn(acc[ch * 8 + 2], acc[ch * 8 + 3]);
+                    __nv_bfloat162 p2 = __floats2bfloat162_rn(acc[ch * 8 + 4], acc[ch * 8 + 5]);
+                    __nv_bfloat162 p3 = __floats2bfloat162_rn(acc[ch * 8 + 6], acc[ch * 8 + 7]);
+                    pk.x = *reinterpret_cast<uint32_t*>(&p0);
+                    pk.y = *reinterpret_cast<uint32_t*>(&p1);
+                    pk.z = *reinterpret_cast<uint32_t*>(&p2);
+                    pk.w = *reinterpret_cast<uint32_t*>(&p3);
+                    *reinterpret_cast<uint4*>(out_act + ((((size_t)z * H + y) * 4 + ch) * Wp + x) * 8) = pk;
+                }
+            }
+        }
+    }
+    __syncwarp();  // the single-lane roles rejoin their warps
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
+    }
+}
+
+// V_s [C][K][H][W] FP32 -> act [K][H][4][Wp][8] BF16 (round to nearest even); channels >= C
+// and voxels x >= W are zero.
+__global__ void k_pack_input(const float* __restrict__ V, int C, int K, int H, int W, int Wp,
+                             __nv_bfloat16* __restrict__ act) {
+    const long long n = (long long)K * H * Wp;
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int x = (int)(i % Wp);
+    const long long zy = i / Wp;
+    const size_t plane = (size_t)K * H * W;
+#pragma unroll
+    for (int ch = 0; ch < 4; ++ch) {
+        float v[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            const int c = ch * 8 + e;
+            v[e] = (c < C && x < W) ? __ldg(V + (size_t)c * plane + (size_t)zy * W + x) : 0.f;
+        }
+        uint4 pk;
+        __nv_bfloat162 p0 = __floats2bfloat162_rn(v[0], v[1]), p1 = __floats2bfloat162_rn(v[2], v[3]);
+        __nv_bfloat162 p2 = __floats2bfloat162_rn(v[4], v[5]), p3 = __floats2bfloat162_rn(v[6], v[7]);
+        pk.x = *reinterpret_cast<uint32_t*>(&p0);
+        pk.y = *reinterpret_cast<uint32_t*>(&p1);
+        pk.z = *reinterpret_cast<uint32_t*>(&p2);
+        pk.w = *reinterpret_cast<uint32_t*>(&p3);
+        *reinterpret_cast<uint4*>(act + ((zy * 4 + ch) * Wp + x) * 8) = pk;
+    }
+}
+
+// Batch-norm folding and packing of one block: w [32][cin][3][3][3] FP32 ->
+// [27 taps][4 chunks][32 out][8 in] BF16 (inputs >= cin zero) and the folded bias.
+__global__ void k_prepare_block(const float* __restrict__ w, const float* __restrict__ b, const float* __restrict__ gamma,
+                                const float* __restrict__ beta, const float* __restrict__ mean,
+                                const float* __restrict__ var, float eps, int cin, __nv_bfloat16* __restrict__ wp,
+                                float* __restrict__ bias) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;  // over 27 * 32 * 32
+    if (i < kF) {
+        const float s = gamma[i] / sqrtf(var[i] + eps);
+        bias[i] = (b[i] - mean[i]) * s + beta[i];
+    }
+    if (i >= 27 * kF * kF) return;
+    const int ci = i % kF, co = (i / kF) % kF, tap = i / (kF * kF);
+    const float s = gamma[co] / sqrtf(var[co] + eps);
+    const float v = ci < cin ? w[((size_t)co * cin + ci) * 27 + tap] * s : 0.f;
+    wp[(((size_t)tap * 4 + ci / 8) * kF + co) * 8 + ci % 8] = __float2bfloat16_rn(v);
+}
+
+}  // namespace
+
+size_t rl_lgd_net_bytes() { return kNetBytes; }
+
+rl_status rl_lgd_prepare(const rl_lgd_params* p, void* net, cudaStream_t s) {
+    unsigned char* base = (unsigned char*)net;
+    for (int l = 0; l < 5; ++l) {
+        const int cin = l == 0 ? p->c_in : kF;
+        k_prepare_block<<<(27 * kF * kF + 255) / 256, 256, 0, s>>>(
+            p->conv_w[l], p->conv_b[l], p->bn_gamma[l], p->bn_beta[l], p->bn_mean[l], p->bn_var[l], p->eps, cin,
+            (__nv_bfloat16*)(base + kNetW + (size_t)l * kWBytes), (float*)(base + kNetBias) + l * kF);
+    }
+    cudaMemcpyAsync(base + kNetOutW, p->out_w, 4 * kF * sizeof(float), cudaMemcpyDeviceToDevice, s);
+    cudaMemcpyAsync(base + kNetOutB, p->out_b, 4 * sizeof(float), cudaMemcpyDeviceToDevice, s);
+    return rl_check_launch("lgd_prepare");
+}
+
+int lgd_pitch(int W) { return (W + 7) & ~7; }
+
+size_t rl_lgd_act_bytes(int K, int H, int W) { return ((size_t)K * H * lgd_pitch(W) * kF * 2 + 255) & ~(size_t)255; }
+
+rl_status rl_lgd_forward(const void* net, const float* V, int C, int K, int H, int W, float* residual, void* act0,
+                         void* act1, cudaStream_t s) {
+    const int Wp = lgd_pitch(W);
+    const long long n = (long long)K * H * Wp;
+    {
+        RLTraceScope ts("lgd_pack", s);
+        k_pack_input<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(V, C, K, H, W, Wp, (__nv_bfloat16*)act0);
+    }
+    rl_status st = rl_check_launch("lgd_pack");
+    if (st) return st;
+    CUtensorMap maps[2];
+    if (!rl_encode_act_tmap(&maps[0], act0, K, H, Wp, kHaloCM) || !rl_encode_act_tmap(&maps[1], act1, K, H, Wp, kHaloCM))
+        return rl_fail(RL_ECUDA, "lgd: activation tensor maps could not be encoded");
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const long long ntiles = (long long)K * H * ((W + kTileM - 1) / kTileM);
+    const unsigned grid = (unsigned)std::min<long long>(ntiles, sms > 0 ? sms : 1);
+    const size_t smem = SmemLayout::TOTAL;
+    cudaFuncSetAttribute(k_conv_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(k_conv_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    unsigned int* status = rl_device_status_ptr();
+    if (!status) return rl_fail(RL_ECUDA, "device status word unavailable");
+    void* acts[2] = {act0, act1};
+    for (int l = 0; l < 5; ++l) {
+        const int src = l & 1;
+        if (l < 4) {
+            RLTraceScope ts("lgd_conv_tc", s);
+            k_conv_tc<false><<<grid, kThreads, smem, s>>>(maps[src], (const unsigned char*)net, l, K, H, W, Wp,
+                                                          (__nv_bfloat16*)acts[src ^ 1], nullptr, status);
+        } else {
+            RLTraceScope ts("lgd_conv_tc_final", s);
+            k_conv_tc<true><<<grid, kThreads, smem, s>>>(maps[src], (const unsigned char*)net, l, K, H, W, Wp,
+                                                         nullptr, residual, status);
+        }
+        st = rl_check_launch("lgd_conv");
+        if (st) return st;
+    }
+    return RL_OK;
+}
+
+// ------------------------------------------------------------------ C ABI
+
+namespace {
+struct LgdStepLayout {
+    size_t vol, V, res, S, act0, act1, total;
+};
+
+size_t a256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+LgdStepLayout lgd_step_layout(int N, int D, int H, int W, int k, rl_dtype dt) {
+    LgdStepLayout L;
+    size_t off = 0;
+    L.vol = off;
+    off += a256(reallife_gradient_volume_workspace_bytes(N, D, H, W, k, dt));
+    L.V = off;
+    off += a256((size_t)(4 * N + 4) * k * H * W * sizeof(float));
+    L.res = off;
+    off += a256((size_t)k * H * W * 4 * sizeof(float));
+    L.S = off;
+    off += a256((size_t)k * H * W);
+    L.act0 = off;
+    off += rl_lgd_act_bytes(k, H, W);
+    L.act1 = off;
+    off += rl_lgd_act_bytes(k, H, W);
+    L.total = off;
+    return L;
+}
+}  // namespace
+
+extern "C" size_t reallife_lgd_net_bytes(void) { return rl_lgd_net_bytes(); }
+
+extern "C" rl_status reallife_lgd_prepare(const rl_lgd_params* p, void* net, cudaStream_t stream) {
+    if (!p || !net || ((uintptr_t)net & 255) != 0) return rl_fail(RL_EINVAL, "lgd_prepare: NULL or misaligned");
+    if (p->c_in < 1 || p->c_in > 32) return rl_fail(RL_EINVAL, "lgd_prepare: c_in=%d outside [1,32]", p->c_in);
+    if (!(p->eps >= 0.f)) return rl_fail(RL_EINVAL, "lgd_prepare: eps must be >= 0");
+    for (int l = 0; l < 5; ++l)
+        if (!p->conv_w[l] || !p->conv_b[l] || !p->bn_gamma[l] || !p->bn_beta[l] || !p->bn_mean[l] || !p->bn_var[l])
+            return rl_fail(RL_EINVAL, "lgd_prepare: block %d has a NULL parameter", l);
+    if (!p->out_w || !p->out_b) return rl_fail(RL_EINVAL, "lgd_prepare: NULL output layer");
+    return rl_lgd_prepare(p, net, stream);
+}
+
+extern "C" size_t reallife_lgd_workspace_bytes(int k, int h, int w) {
+    if (k < 1 || h < 1 || w < 1) return 0;
+    return 2 * rl_lgd_act_bytes(k, h, w);
+}
+
+extern "C" rl_status reallife_lgd_forward(const void* net, const float* V, int C, int k, int h, int w,
+                                          float* residual, void* ws, size_t ws_bytes, cudaStream_t stream) {
+    if (!net || ((uintptr_t)net & 255) != 0 || !V || !residual || ((uintptr_t)residual & 15) != 0 || !ws ||
+        ((uintptr_t)ws & 255) != 0)
+        return rl_fail(RL_EINVAL, "lgd_forward: NULL or misaligned pointer");
+    if (C < 1 || C > 32 || k < 1 || h < 1 || w < 1 || (long long)k * h * w >= (1ll << 31))
+        return rl_fail(RL_EINVAL, "lgd_forward: C=%d (<= 32), k=%d, h=%d, w=%d", C, k, h, w);
+    const size_t need = reallife_lgd_workspace_bytes(k, h, w);
+    if (ws_bytes < need) return rl_fail(RL_ENOMEM, "workspace %zu bytes < %zu needed", ws_bytes, need);
+    char* b = (char*)ws;
+    return rl_lgd_forward(net, V, C, k, h, w, residual, b, b + rl_lgd_act_bytes(k, h, w), stream);
+}
+
+extern "C" size_t reallife_lgd_step_workspace_bytes(int N, int D, int H, int W, int k, rl_dtype dtype) {
+    if (N < 1 || D < 1 || H < 1 || W < 1 || k < 1) return 0;
+    return lgd_step_layout(N, D, H, W, k, dtype).total;
+}
+
+extern "C" rl_status reallife_lgd_step(rl_mpi* m, const float* images, const rl_camera* src, int N, int k, int level,
+                                       int selection, int clamp01, const void* net, uint8_t* S_out, void* ws,
+                                       size_t ws_bytes, cudaStream_t stream) {
+    if (N < 1 || 4 * N + 4 > 32) return rl_fail(RL_EINVAL, "lgd_step: N=%d views give more than 32 channels", N);
+    if (!net || ((uintptr_t)net & 255) != 0) return rl_fail(RL_EINVAL, "lgd_step: net NULL or misaligned");
+    if (!m || !ws || ((uintptr_t)ws & 255) != 0) return rl_fail(RL_EINVAL, "lgd_step: NULL or misaligned");
+    if (m->D < 1 || m->H < 1 || m->W < 1) return rl_fail(RL_EINVAL, "lgd_step: bad MPI shape");
+    const LgdStepLayout L = lgd_step_layout(N, m->D, m->H, m->W, k, m->dtype);
+    if (ws_bytes < L.total) return rl_fail(RL_ENOMEM, "workspace %zu bytes < %zu needed", ws_bytes, L.total);
+    char* b = (char*)ws;
+    uint8_t* S = S_out ? S_out : (uint8_t*)(b + L.S);
+    float* V = (float*)(b + L.V);
+    float* res = (float*)(b + L.res);
+    // V_s and S (validates the MPI, views, k, level and selection)
+    rl_status st = reallife_gradient_volume(m, images, src, N, k, level, selection, S, V, b + L.vol,
+                                            L.V - L.vol, stream);
+    if (st) return st;
+    const int h = m->H >> level, w = m->W >> level;
+    st = rl_lgd_forward(net, V, 4 * N + 4, k, h, w, res, b + L.act0, b + L.act1, stream);
+    if (st) return st;
+    // M <- M + R(residual, S): the masked update with step -1 (and the level's upsampling)
+    return rl_launch_update(m->data, m->dtype, m->D, m->H, m->W, level, S, res, k, -1.0f, clamp01, stream);
+}

@@ -39,6 +39,11 @@ int rl_kernel_path_setting();
 // layout cannot be described (row pitch not a multiple of 16 bytes, misaligned base).
 bool rl_encode_mpi_tmap(CUtensorMap* map, const void* M, rl_dtype dt, int D, int H, int W);
 
+// TMA descriptor of a chunked BF16 activation volume [K][H][4][Wp][8] (32 channels as four
+// chunks of 8, Wp a multiple of 8) with a box of {one 8x8 core matrix, halo_cm core matrices
+// along x, 4 chunks}; false when it cannot be encoded (misaligned base, bad pitch).
+bool rl_encode_act_tmap(CUtensorMap* map, const void* act, int K, int H, int Wp, int halo_cm);
+
 // ----------------------------------------------------------------- launchers
 // All take device pointers and enqueue on `s`; arguments are validated by the caller.
 
@@ -102,3 +107,12 @@ rl_status rl_launch_view_alpha(const void* M, rl_dtype dt, int D, int H, int W, 
 // selection S [k][h][w], the view alpha weights A [N][D][h][w] and full-resolution images.
 rl_status rl_launch_volume(const void* Ml, rl_dtype dt, int D, int h, int w, int level, const uint8_t* S, int k,
                            const float* A, const float* images, const RLInvViews& iv, float* V, cudaStream_t s);
+
+// Learned update network (lgd.cu): packed parameter bytes, parameter packing, activation
+// buffer bytes and the forward pass (V [C][K][H][W] FP32 -> residual [K][H][W][4] FP32,
+// two activation buffers of rl_lgd_act_bytes each).
+size_t rl_lgd_net_bytes();
+rl_status rl_lgd_prepare(const rl_lgd_params* p, void* net, cudaStream_t s);
+size_t rl_lgd_act_bytes(int K, int H, int W);
+rl_status rl_lgd_forward(const void* net, const float* V, int C, int K, int H, int W, float* residual, void* act0,
+                         void* act1, cudaStream_t s);

@@ -10,6 +10,11 @@ writing a 512 MB buffer (both outside the step's CUDA events).
 Prints one JSON line.  ``--impl reference`` times the FP64 CPU oracle instead (a bounded
 sample per step, on the host cores).  Under torchrun every rank refines its own scene
 (independent problems, no collective on the data path) and rank 0 reports the aggregate.
+
+``--stage volume`` times instead the sparsified gradient volume of Sec. 3.3 at the three
+levels of the schedule (one step = three volumes), and ``--stage lgd`` the learned HSGD
+refinement (one step = one learned iteration at each of the three levels: volume, tensor-core
+network, restore update), each with the roofline of its dominant kernel.
 """
 from __future__ import annotations
 
@@ -54,6 +59,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-clocks", action="store_true")
     ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--stage", choices=["hsgd", "volume", "lgd"], default="hsgd",
+                    help="hsgd: refinement + renders (default); volume: gradient volumes; lgd: learned refinement")
     ap.add_argument("--kernel-path", type=int, default=0,
                     help="warp-kernel family: 0 automatic, 1 TMA windows, 2 per-pixel gather, 3/4 plane-parallel")
     return ap.parse_args()
@@ -333,6 +340,164 @@ def run_ours(args, world, rank, local):
     return result
 
 
+def volume_kernel_bytes(sc, k: int, level: int, elt: int) -> dict:
+    """Algorithmic bytes per launch of the gradient-volume kernels at one level."""
+    N, D = len(sc.src), sc.D
+    h, w = sc.H >> level, sc.W >> level
+    hw = h * w
+    return {
+        # read the level MPI once, write the view alpha weights
+        "view_alpha": D * hw * 4 * elt + N * D * hw * 4,
+        # write V, read S, the kept voxels of M_l, one alpha-weight sample and the images once
+        "volume": (4 * N + 4) * k * hw * 4 + k * hw + k * hw * 4 * elt + N * k * hw * 4 + N * sc.H * sc.W * 12,
+    }
+
+
+def lgd_conv_flops(k: int, h: int, w: int) -> int:
+    """FLOPs of one 3x3x3, 32 -> 32 channel block over k x h x w voxels."""
+    return 2 * k * h * w * 27 * 32 * 32
+
+
+def run_stage(args, world, rank, local):
+    """Timed steps of the gradient volume (--stage volume) or the learned refinement (--stage lgd)."""
+    import torch
+    import paper_2307_03017_gb300 as rl
+    import scenegen as sg
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    sc, cfg = load_scene(args.workload, args.seed + rank)
+    dtype = torch.bfloat16 if cfg["dtype"] == "bf16" else torch.float32
+    elt = 2 if dtype == torch.bfloat16 else 4
+    k, sched = cfg["k"], tuple(cfg["schedule"])
+    N = len(sc.src)
+    M0 = torch.from_numpy(sc.coarse_mpi).to(dev).to(dtype).contiguous()
+    M = M0.clone()
+    images = torch.from_numpy(sc.images).to(dev)
+    mpi = rl.make_mpi(M, sc.near, sc.far, sc.ref)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+    if args.stage == "volume":
+        ws = torch.empty(rl.reallife_gradient_volume_workspace_bytes(N, sc.D, sc.H, sc.W, k, dtype), dtype=torch.uint8,
+                         device=dev)
+        Vs = {l: torch.empty((4 * N + 4, k, sc.H >> l, sc.W >> l), device=dev) for l in sched}
+        Ss = {l: torch.empty((k, sc.H >> l, sc.W >> l), dtype=torch.uint8, device=dev) for l in sched}
+
+        def step():
+            for l in sched:
+                rl.reallife_gradient_volume(mpi, images, sc.src, k, l, V=Vs[l], S_out=Ss[l], ws=ws)
+        metric = "gradient volumes/s (Sec. 3.3 V_s at levels 2, 1, 0) at 512x384 D=32"
+        unit = "volume sets/s"
+    else:
+        net = rl.LgdNet(sg.lgd_weights(args.seed, 4 * N + 4), device=dev)
+        ws = torch.empty(rl.reallife_lgd_step_workspace_bytes(N, sc.D, sc.H, sc.W, k, dtype), dtype=torch.uint8,
+                         device=dev)
+
+        def step():
+            for l in sched:
+                rl.reallife_lgd_step(mpi, images, sc.src, k, net, level=l, ws=ws)
+        metric = "learned MPI refinements/s (Sec. 3.3 learned update at levels 2, 1, 0) at 512x384 D=32"
+        unit = "learned refinements/s"
+
+    for _ in range(args.warmup):
+        M.copy_(M0)
+        step()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local) if not args.no_clocks else None
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    stops = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    if clocks:
+        clocks.start()
+    rl.reallife_trace_read()
+    for i in range(args.steps):
+        M.copy_(M0)
+        flush.fill_(i & 0xFF)
+        rl.reallife_trace_enable(True)
+        starts[i].record(stream)
+        step()
+        stops[i].record(stream)
+        rl.reallife_trace_enable(False)
+    torch.cuda.synchronize()
+    trace = rl.reallife_trace_read()
+    clk = clocks.stop() if clocks else None
+    total_ms = reduce_max(sum(a.elapsed_time(b) for a, b in zip(starts, stops)), dist, dev)
+    if dist:
+        dist.barrier()
+    value = world * args.steps / (total_ms / 1e3)
+    assert rl.reallife_device_status(clear=True) == 0
+    launches = sum(v[0] for v in trace.values())
+    dom_name, (dom_n, dom_ms) = max(trace.items(), key=lambda kv: kv[1][1])
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    if args.stage == "lgd" and dom_name.startswith("lgd_conv"):
+        flops = args.steps * sum(4 * lgd_conv_flops(k, sc.H >> l, sc.W >> l) for l in sched)
+        achieved = flops / (dom_ms / 1e3) / 1e12
+        peak, src = (peaks["bf16_tflops"], "measured (burst)") if "bf16_tflops" in peaks else (1900.0, "fallback")
+        roofline = {"bound": "tensor", "kernel": dom_name, "achieved": round(achieved, 1), "peak": peak,
+                    "unit": "TFLOP/s", "frac": round(achieved / peak, 4), "traffic": None,
+                    "alg_flops_per_launch": int(flops / dom_n), "avg_launch_us": round(dom_ms / dom_n * 1e3, 2),
+                    "peak_source": src}
+    else:
+        key = "volume" if dom_name.startswith("volume") else ("view_alpha" if dom_name.startswith("view_alpha")
+                                                              else None)
+        alg = args.steps * sum(volume_kernel_bytes(sc, k, l, elt)[key] for l in sched) if key else None
+        achieved = alg / (dom_ms / 1e3) / 1e9 if alg else None
+        peak, src = (peaks["hbm_gbs"], "measured") if "hbm_gbs" in peaks else (6800.0, "fallback")
+        roofline = {"bound": "hbm", "kernel": dom_name, "achieved": round(achieved, 1) if achieved else None,
+                    "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4) if achieved else None,
+                    "traffic": None, "alg_bytes_per_launch": int(alg / dom_n) if alg else None,
+                    "avg_launch_us": round(dom_ms / dom_n * 1e3, 2), "peak_source": src}
+    kernels = {n: {"launches": c, "ms_per_step": round(t / args.steps, 4)} for n, (c, t) in sorted(trace.items())}
+    result = None
+    if rank == 0:
+        result = {
+            "metric": metric, "value": round(value, 3), "unit": unit, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(total_ms / args.steps, 4), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32" if elt == 4 else "bf16",
+            "data": "synthetic (seeded ray-cast layered scenes; random network weights; no dataset)",
+            "config": {"workload": f"{args.workload}: {sc.W}x{sc.H} D={sc.D} N={N} k={k} levels={list(sched)}",
+                       "stage": args.stage, "storage": cfg["dtype"],
+                       "network": "5 x (3x3x3 conv 32 ch + BN + ReLU) + 1x1x1, BF16 on tcgen05"
+                       if args.stage == "lgd" else None,
+                       "l2": "flushed (512 MB write) before every timed step", "parallelism": f"replicas{world}"},
+            "roofline": roofline, "kernels": kernels, "gpu_launches": int(launches), "clocks": clk, "e2e": None,
+        }
+    if dist:
+        dist.destroy_process_group()
+    return result
+
+
+def cpu_baseline_stage(sc, cfg, stage: str, seed: int) -> dict:
+    """The FP64 oracle on the coarsest level of the stage's step, scaled by that level's share of
+    the step's pixels (levels 2, 1, 0 hold 1/21, 4/21 and 16/21 of them)."""
+    import oracle
+    from oracle import lgd as olgd
+    import scenegen as sg
+    oracle.build()
+    k, sched = cfg["k"], tuple(cfg["schedule"])
+    lvl = max(sched)
+    share = (1 << (2 * (max(sched) - lvl))) / sum(1 << (2 * (max(sched) - l)) for l in sched)
+    t0 = time.perf_counter()
+    if stage == "volume":
+        oracle.gradient_volume(sc.coarse_mpi, sc.near, sc.far, sc.ref, sc.src, sc.images, k, lvl)
+    else:
+        olgd.lgd_step(sc.coarse_mpi, sc.near, sc.far, sc.ref, sc.src, sc.images,
+                      sg.lgd_weights(seed, 4 * len(sc.src) + 4), k, lvl)
+    dt = time.perf_counter() - t0
+    return {"value": round(share / dt, 5), "unit": "volume sets/s" if stage == "volume" else "learned refinements/s",
+            "cores": 1, "kind": "oracle",
+            "sample": f"the level-{lvl} {'gradient volume' if stage == 'volume' else 'learned iteration'} of one step "
+                      f"({share:.4f} of the step's pixels), FP64, single thread, {dt:.2f} s; value scaled by the "
+                      f"pixel share", "cpu": platform_cpu()}
+
+
 def run_e2e(args, rl, sc, cfg, dtype, dev, world, dist):
     """Same metric through the public API from pinned host memory: H2D of the coarse MPI and
     the source images, refine + render, D2H of the rendered views, every step."""
@@ -553,6 +718,13 @@ def main():
         res = run_reference(args, world, rank)
     elif args.workload == "serve":
         res = run_serve(args, world, rank, local) if rank == 0 else None
+    elif args.stage != "hsgd":
+        res = run_stage(args, world, rank, local)
+        if res is not None and not args.no_cpu_baseline and world == 1:
+            sc, cfg = load_scene(args.workload, args.seed)
+            res["cpu_baseline"] = cpu_baseline_stage(sc, cfg, args.stage, args.seed)
+        elif res is not None:
+            res["cpu_baseline"] = None
     else:
         res = run_ours(args, world, rank, local)
         if res is not None and not args.no_cpu_baseline and world == 1:

@@ -16,11 +16,17 @@
 // row).
 //
 // Output tile: 128 consecutive voxels of one (z, y) line x 32 channels, accumulated in FP32 in
-// tensor memory over 9 halos x 3 shifts x 2 K steps = 54 MMAs of 128x32x16 (BF16 inputs).
-// Persistent CTAs (one per SM), warp-specialised: warp 0 issues the TMA copies, warp 1 the
-// MMAs (one lane), warps 2-5 drain the two tensor-memory accumulators: bias, ReLU, BF16
-// rounding and the store of the next layer's activations; after the last block they also
-// apply the 1x1x1 layer and store the FP32 residual [z][y][x][4].
+// tensor memory over 9 halos x 3 shifts x 2 K steps = 54 MMAs of 128x32x16 (BF16 inputs),
+// spread round-robin over four accumulators so that consecutive MMAs are independent (the
+// epilogue adds the four partial sums).
+// Persistent CTAs (one per SM) each take a contiguous run of output lines in (z, x-tile, y)
+// order and walk it along y, so that consecutive lines share six of their nine halos: every
+// input row (the halos of planes z-1, z, z+1 at one y) is copied once into a ring of staged
+// rows and released after the last output line that reads it.  Warp-specialised: warp 0
+// issues the TMA copies, warp 1 the MMAs (one lane), warps 2-5 drain the two tensor-memory
+// accumulators: bias, ReLU, BF16 rounding and the store of the next layer's activations;
+// after the last block they also apply the 1x1x1 layer and store the FP32 residual
+// [z][y][x][4].
 //
 // Every mbarrier wait is bounded; a wait that gives up sets RL_DEVFLAG_TIMEOUT, the roles
 // stop, the producer waits (bounded) for its copies in flight and the MMA lane for its MMAs,
@@ -37,13 +43,15 @@ constexpr int kTileM = 128;                      // voxels per output tile
 constexpr int kHaloCM = kTileM / 8 + 2;          // core matrices (8 voxels) of one staged halo
 constexpr int kHalo = kHaloCM * 8;               // 144 rows: x0 - 8 .. x0 + 135
 constexpr int kChunkBytes = kHalo * 16;          // one 8-channel chunk of a halo
-constexpr int kStageBytes = 4 * kChunkBytes;     // 9216
-constexpr int kStages = 12;
+constexpr int kStageBytes = 4 * kChunkBytes;     // 9216: one halo (one input line of one plane)
+constexpr int kSlotBytes = 3 * kStageBytes;      // one input row y of the three planes z-1, z, z+1
+constexpr int kRowSlots = 5;                     // ring of staged input rows
 constexpr int kTapBytes = 4 * kF * 16;           // weights of one tap: [chunk][32][8] BF16
 constexpr int kWBytes = 27 * kTapBytes;          // 55296
 constexpr int kThreads = 192;
-constexpr uint32_t kTmemCols = 256;              // accumulators at columns 0 and 128
-constexpr uint32_t kAccStride = 128;
+constexpr int kNAcc = 4;                         // independent accumulators per output line
+constexpr uint32_t kTmemCols = 256;              // two lines in flight x 4 accumulators x 32 columns
+constexpr uint32_t kAccStride = kNAcc * kF;      // columns of one line's accumulators
 // instruction descriptor: D FP32, A and B BF16, both K-major, N = 32, M = 128
 constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kF >> 3) << 17) |
                             ((uint32_t)(kTileM >> 4) << 24);
@@ -60,8 +68,8 @@ constexpr size_t kNetBytes = (kNetOutB + 16 + 255) & ~(size_t)255;
 struct SmemLayout {
     static constexpr int W = 0;
     static constexpr int A = W + kWBytes;
-    static constexpr int BAR = A + kStages * kStageBytes;
-    static constexpr int NBAR = 2 * kStages + 6;
+    static constexpr int BAR = A + kRowSlots * kSlotBytes;
+    static constexpr int NBAR = 2 * kRowSlots + 6;
     static constexpr int TSLOT = BAR + NBAR * 8;
     static constexpr int BIAS = TSLOT + 16;
     static constexpr int OUTW = BIAS + kF * 4;
@@ -143,8 +151,8 @@ k_conv_tc(const __grid_constant__ CUtensorMap in_map, const unsigned char* __res
     unsigned char* sA = smem + SmemLayout::A;
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem + SmemLayout::BAR);
     uint64_t* full = bars;
-    uint64_t* empty = bars + kStages;
-    uint64_t* tfull = bars + 2 * kStages;
+    uint64_t* empty = bars + kRowSlots;
+    uint64_t* tfull = bars + 2 * kRowSlots;
     uint64_t* tempty = tfull + 2;
     uint64_t* wbar = tempty + 2;
     uint64_t* mma_done = wbar + 1;  // drain of the MMAs on an abort
@@ -156,11 +164,13 @@ k_conv_tc(const __grid_constant__ CUtensorMap in_map, const unsigned char* __res
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int tiles_x = (W + kTileM - 1) / kTileM;
-    const int ntiles = K * H * tiles_x;
+    // this CTA's output lines: [r_begin, r_end) of the (z, x-tile, y) order
+    const long long R = (long long)K * tiles_x * H;
+    const long long r_begin = R * blockIdx.x / gridDim.x, r_end = R * (blockIdx.x + 1) / gridDim.x;
     const float* bias_g = reinterpret_cast<const float*>(net + kNetBias) + layer * kF;
 
     if (threadIdx.x == 0) {
-        for (int i = 0; i < kStages; ++i) {
+        for (int i = 0; i < kRowSlots; ++i) {
             mbar_init(&full[i], 1);
             mbar_init(&empty[i], 1);
         }
@@ -191,15 +201,17 @@ k_conv_tc(const __grid_constant__ CUtensorMap in_map, const unsigned char* __res
         // ------------------------------------------------------------- producer
         mbar_expect_tx(wbar, kWBytes);
         bulk_load(sW, net + kNetW + (size_t)layer * kWBytes, kWBytes, wbar);
-        int it = 0;
+        int irow = 0;  // input rows staged by this CTA
         bool ok = true;
-        for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
-            const int tx = tile % tiles_x;
-            const int zy = tile / tiles_x;
-            const int y = zy % H, z = zy / H;
-            for (int hh = 0; hh < 9 && ok; ++hh, ++it) {
-                const int s = it % kStages, r = it / kStages;
-                if (r > 0 && !mbar_wait(&empty[s], (uint32_t)((r - 1) & 1))) {
+        for (long long seg = r_begin; seg < r_end && ok;) {
+            const long long col = seg / H;
+            const int y0 = (int)(seg % H);
+            const long long seg_end = min(r_end, (col + 1) * H);
+            const int n = (int)(seg_end - seg);
+            const int tx = (int)(col % tiles_x), z = (int)(col / tiles_x);
+            for (int r = y0 - 1; r <= y0 + n && ok; ++r, ++irow) {  // input rows of outputs y0 .. y0+n-1
+                const int slot = irow % kRowSlots, round = irow / kRowSlots;
+                if (round > 0 && !mbar_wait(&empty[slot], (uint32_t)((round - 1) & 1))) {
                     ok = false;
                     break;
                 }
@@ -207,59 +219,84 @@ k_conv_tc(const __grid_constant__ CUtensorMap in_map, const unsigned char* __res
                     ok = false;
                     break;
                 }
-                mbar_expect_tx(&full[s], kStageBytes);
-                tma_load_5d(sA + s * kStageBytes, &in_map, &full[s], 0, tx * (kTileM / 8) - 1, 0, y + hh % 3 - 1,
-                            z + hh / 3 - 1);
+                mbar_expect_tx(&full[slot], kSlotBytes);
+                unsigned char* dst = sA + slot * kSlotBytes;
+                for (int dz = 0; dz < 3; ++dz)
+                    tma_load_5d(dst + dz * kStageBytes, &in_map, &full[slot], 0, tx * (kTileM / 8) - 1, 0, r,
+                                z + dz - 1);
             }
+            seg = seg_end;
         }
         if (!ok) {
             flag_timeout(status);
             s_abort = 1;
         }
-        // copies in flight: the last load of every stage must have landed before exit; on the
-        // normal path also its release by the MMAs (the tensor core's arrival on empty[s])
-        for (int s = 0; s < kStages && s < it; ++s) {
-            const int last = it - 1 - ((it - 1 - s) % kStages);
-            if (!mbar_wait(&full[s], (uint32_t)((last / kStages) & 1))) flag_timeout(status);
-            if (ok && !mbar_wait(&empty[s], (uint32_t)((last / kStages) & 1))) flag_timeout(status);
+        // copies in flight: the last row of every slot must have landed before exit; on the
+        // normal path also its release by the MMAs (the tensor core's arrival on empty[slot])
+        for (int slot = 0; slot < kRowSlots && slot < irow; ++slot) {
+            const int last = irow - 1 - ((irow - 1 - slot) % kRowSlots);
+            if (!mbar_wait(&full[slot], (uint32_t)((last / kRowSlots) & 1))) flag_timeout(status);
+            if (ok && !mbar_wait(&empty[slot], (uint32_t)((last / kRowSlots) & 1))) flag_timeout(status);
         }
         if (!mbar_wait(wbar, 0)) flag_timeout(status);
     } else if (warp == 1 && lane == 0) {
         // ------------------------------------------------------------- MMA issuer
         bool ok = mbar_wait(wbar, 0);
-        const uint32_t wbase = smem_u32(sW), abase = smem_u32(sA);
-        int it = 0, t = 0;
-        for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, ++t) {
-            const int b = t & 1, u = t >> 1;
-            if (u > 0 && !mbar_wait(&tempty[b], (uint32_t)((u - 1) & 1))) {
-                ok = false;
-                break;
-            }
-            tc_fence_after();
-            const uint32_t d = tmem + (uint32_t)b * kAccStride;
-            for (int hh = 0; hh < 9; ++hh, ++it) {
-                const int s = it % kStages, r = it / kStages;
-                if (!mbar_wait(&full[s], (uint32_t)(r & 1)) || *(volatile int*)&s_abort) {
+        const uint32_t abase = smem_u32(sA);
+        const uint64_t wdesc = umma_desc(smem_u32(sW), kF * 16, 128);
+        int irow = 0, t = 0;
+        for (long long seg = r_begin; seg < r_end && ok;) {
+            const long long col = seg / H;
+            const long long seg_end = min(r_end, (col + 1) * H);
+            const int n = (int)(seg_end - seg);
+            for (int o = 0; o < n && ok; ++o, ++t) {
+                const int b = t & 1, u = t >> 1;
+                if (u > 0 && !mbar_wait(&tempty[b], (uint32_t)((u - 1) & 1))) {
                     ok = false;
                     break;
                 }
+                // input rows y-1, y, y+1 of output line o: staged rows irow + o .. irow + o + 2
+                for (int dy = 0; dy < 3 && ok; ++dy) {
+                    const int j = irow + o + dy;
+                    if (!mbar_wait(&full[j % kRowSlots], (uint32_t)((j / kRowSlots) & 1)) ||
+                        *(volatile int*)&s_abort)
+                        ok = false;
+                }
+                if (!ok) break;
                 tc_fence_after();
-                const uint32_t st = abase + (uint32_t)(s * kStageBytes);
+                const uint32_t d = tmem + (uint32_t)b * kAccStride;
+                // descriptors of the three staged rows; every operand below is one of them (or the
+                // weights' descriptor) advanced by a compile-time offset in 16-byte units
+                uint64_t arow[3];
 #pragma unroll
-                for (int dx = 0; dx < 3; ++dx)
+                for (int dy = 0; dy < 3; ++dy)
+                    arow[dy] = umma_desc(abase + (uint32_t)(((irow + o + dy) % kRowSlots) * kSlotBytes),
+                                         kChunkBytes, 128);
 #pragma unroll
-                    for (int kk = 0; kk < 2; ++kk) {
-                        const int tap = hh * 3 + dx;
-                        const uint64_t ad =
-                            umma_desc(st + (uint32_t)(kk * 2 * kChunkBytes + (7 + dx) * 16), kChunkBytes, 128);
-                        const uint64_t bd = umma_desc(wbase + (uint32_t)(tap * kTapBytes + kk * 2 * kF * 16), kF * 16,
-                                                      128);
-                        umma_bf16(d, ad, bd, (hh | dx | kk) != 0 ? 1u : 0u);
-                    }
-                umma_commit(&empty[s]);  // the stage is free once these MMAs have read it
+                for (int hh = 0; hh < 9; ++hh)
+#pragma unroll
+                    for (int dx = 0; dx < 3; ++dx)
+#pragma unroll
+                        for (int kk = 0; kk < 2; ++kk) {
+                            const uint32_t aoff =
+                                (uint32_t)((hh / 3) * kStageBytes + kk * 2 * kChunkBytes + (7 + dx) * 16);
+                            const uint32_t boff = (uint32_t)((hh * 3 + dx) * kTapBytes + kk * 2 * kF * 16);
+                            // consecutive MMAs go to different accumulators so that they do not
+                            // wait on one another; the epilogue adds the four partial sums
+                            const int idx = (hh * 3 + dx) * 2 + kk;
+                            umma_bf16(d + (uint32_t)((idx % kNAcc) * kF), arow[hh % 3] + (aoff >> 4),
+                                      wdesc + (boff >> 4), idx >= kNAcc ? 1u : 0u);
+                        }
+                umma_commit(&tfull[b]);
+                // row y-1 is read by no later line of this run
+                umma_commit(&empty[(irow + o) % kRowSlots]);
+                if (o == n - 1) {  // the run's last two rows
+                    umma_commit(&empty[(irow + n) % kRowSlots]);
+                    umma_commit(&empty[(irow + n + 1) % kRowSlots]);
+                }
             }
-            if (!ok) break;
-            umma_commit(&tfull[b]);
+            irow += n + 2;
+            seg = seg_end;
         }
         if (!ok) {
             flag_timeout(status);
@@ -272,7 +309,8 @@ k_conv_tc(const __grid_constant__ CUtensorMap in_map, const unsigned char* __res
         // ------------------------------------------------------------- epilogue
         const int q = warp & 3;  // tensor-memory lane quarter this warp may access
         int t = 0;
-        for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++t) {
+        bool run = true;
+        for (long long line = r_begin; line < r_end && run; ++line, ++t) {
             const int b = t & 1, u = t >> 1;
             bool ok = true;
             if (lane == 0) ok = mbar_wait(&tfull[b], (uint32_t)(u & 1)) && !*(volatile int*)&s_abort;
@@ -282,17 +320,25 @@ k_conv_tc(const __grid_constant__ CUtensorMap in_map, const unsigned char* __res
                     flag_timeout(status);
                     s_abort = 1;
                 }
+                run = false;
                 break;
             }
             tc_fence_after();
             float acc[32];
             tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)b * kAccStride, acc);
+#pragma unroll
+            for (int a = 1; a < kNAcc; ++a) {
+                float part[32];
+                tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)b * kAccStride + (uint32_t)(a * kF), part);
+#pragma unroll
+                for (int c = 0; c < kF; ++c) acc[c] += part[c];
+            }
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(&tempty[b]);
-            const int tx = tile % tiles_x;
-            const int zy = tile / tiles_x;
-            const int y = zy % H, z = zy / H;
+            const long long col = line / H;
+            const int y = (int)(line % H);
+            const int tx = (int)(col % tiles_x), z = (int)(col / tiles_x);
             const int x = tx * kTileM + 32 * q + lane;
             if (x >= (FINAL ? W : Wp)) continue;
             const bool pad = x >= W;  // padding voxels of a line stay zero
@@ -419,8 +465,8 @@ rl_status rl_lgd_forward(const void* net, const float* V, int C, int K, int H, i
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const long long ntiles = (long long)K * H * ((W + kTileM - 1) / kTileM);
-    const unsigned grid = (unsigned)std::min<long long>(ntiles, sms > 0 ? sms : 1);
+    const long long lines = (long long)K * H * ((W + kTileM - 1) / kTileM);
+    const unsigned grid = (unsigned)std::min<long long>(lines, sms > 0 ? sms : 1);
     const size_t smem = SmemLayout::TOTAL;
     cudaFuncSetAttribute(k_conv_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     cudaFuncSetAttribute(k_conv_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -4,29 +4,26 @@
 // (R, G, B, alpha) residual -- as implicit GEMMs on the tcgen05 tensor cores, and the learned
 // HSGD iteration M <- clamp(M + R(N_w(V_s), S)).
 //
-// Activations: BF16, 32 channels, chunked channels-last layout act[z][y][4][xp][8] (four
-// chunks of 8 channels; xp = x padded to a multiple of 8 with zero voxels; one chunk row of a
-// (z, y) line is contiguous).  Eight voxels x 8 channels of a chunk row are one 128-byte
-// core matrix of tcgen05.mma's K-major, no-swizzle operand layout, so one TMA tile copy of box
-// {64, 18, 4} (18 core matrices of 4 chunks) at (0, x0/8 - 1, 0, y + dy - 1, z + dz - 1)
-// lands in shared memory as [chunk][144 rows][8]: 8-row groups 128 bytes apart along M, the
-// two core matrices of a 16-wide K step 144 x 16 bytes apart.  The copy engine zero-fills
-// rows and planes outside the volume: the convolution's zero padding.  The taps dx = -1, 0,
-// +1 are the same halo read from rows 7, 8 and 9 on (the operand start moved by 16 bytes a
-// row).
-//
-// Output tile: 128 consecutive voxels of one (z, y) line x 32 channels, accumulated in FP32 in
-// tensor memory over 9 halos x 3 shifts x 2 K steps = 54 MMAs of 128x32x16 (BF16 inputs),
-// spread round-robin over four accumulators so that consecutive MMAs are independent (the
-// epilogue adds the four partial sums).
-// Persistent CTAs (one per SM) each take a contiguous run of output lines in (z, x-tile, y)
-// order and walk it along y, so that consecutive lines share six of their nine halos: every
-// input row (the halos of planes z-1, z, z+1 at one y) is copied once into a ring of staged
-// rows and released after the last output line that reads it.  Warp-specialised: warp 0
-// issues the TMA copies, warp 1 the MMAs (one lane), warps 2-5 drain the two tensor-memory
-// accumulators: bias, ReLU, BF16 rounding and the store of the next layer's activations;
-// after the last block they also apply the 1x1x1 layer and store the FP32 residual
-// [z][y][x][4].
+// Activations: BF16, channels-last act[z][y][x][32] (64 bytes a voxel).  One TMA tile copy of
+// box {32 channels, 144 voxels} at (0, x0 - 8, y, z) with 64-byte swizzling lands in shared
+// memory as the K-major SWIZZLE_64B operand layout of tcgen05.mma (a row of 64 bytes per voxel,
+// 16-byte chunks permuted within 512-byte atoms; 8-row groups 512 bytes apart).  The copy
+// engine zero-fills voxels, lines and planes outside the volume: the convolution's zero
+// padding.  The taps dx = -1, 0, +1 read the same halo from rows 7, 8 and 9 on, and the two
+// 16-channel K steps from byte 0 and 32 of each row (the descriptor's start address moved).
+// Output: lines of 128 consecutive voxels of one (z, y) x 32 channels, accumulated in FP32 in
+// tensor memory.  Persistent CTAs (one per SM) each take a contiguous run of output lines in
+// (z, x-tile, y) order and walk it along y.  Every input row (the halos of planes z-1, z, z+1
+// at one y) is copied once into a ring of staged rows and multiplied once: the weights of one
+// (dz, dx) tap pair are stacked over dy as a 96-row B operand, so that one 128x96x16 MMA adds
+// the row's contribution to the three output lines y+1, y, y-1 that read it (their
+// accumulators sit in consecutive 32-column slots of a 16-line tensor-memory ring, in
+// descending y).  A line is complete after its third input row; 9 (dz, dx) x 2 K steps = 18
+// MMAs per input row (split where the ring wraps, where a line starts, and at the ends of a
+// run).  Warp-specialised: warp 0 issues the TMA copies, warp 1 the MMAs (one lane), warps 2-5
+// drain completed lines: bias, ReLU, BF16 rounding and the store of the next layer's
+// activations; after the last block they also apply the 1x1x1 layer and store the FP32
+// residual [z][y][x][4].
 //
 // Every mbarrier wait is bounded; a wait that gives up sets RL_DEVFLAG_TIMEOUT, the roles
 // stop, the producer waits (bounded) for its copies in flight and the MMA lane for its MMAs,
@@ -40,25 +37,23 @@ using namespace rltma;
 
 constexpr int kF = 32;                           // channels of every block
 constexpr int kTileM = 128;                      // voxels per output tile
-constexpr int kHaloCM = kTileM / 8 + 2;          // core matrices (8 voxels) of one staged halo
-constexpr int kHalo = kHaloCM * 8;               // 144 rows: x0 - 8 .. x0 + 135
-constexpr int kChunkBytes = kHalo * 16;          // one 8-channel chunk of a halo
-constexpr int kStageBytes = 4 * kChunkBytes;     // 9216: one halo (one input line of one plane)
+constexpr int kHalo = kTileM + 16;               // 144 rows: x0 - 8 .. x0 + 135
+constexpr int kRowBytes = kF * 2;                // 64: one voxel's channels
+constexpr int kStageBytes = kHalo * kRowBytes;   // 9216: one halo (one input line of one plane)
 constexpr int kSlotBytes = 3 * kStageBytes;      // one input row y of the three planes z-1, z, z+1
 constexpr int kRowSlots = 5;                     // ring of staged input rows
-constexpr int kTapBytes = 4 * kF * 16;           // weights of one tap: [chunk][32][8] BF16
-constexpr int kWBytes = 27 * kTapBytes;          // 55296
+constexpr int kGroupRows = 3 * kF;               // the dy-stacked weights of one (dz, dx)
+constexpr int kGroupBytes = kGroupRows * kRowBytes;  // [96][32] BF16, 64-byte swizzled
+constexpr int kWBytes = 9 * kGroupBytes;         // 55296
 constexpr int kThreads = 192;
-constexpr int kNAcc = 4;                         // independent accumulators per output line
-constexpr uint32_t kTmemCols = 256;              // two lines in flight x 4 accumulators x 32 columns
-constexpr uint32_t kAccStride = kNAcc * kF;      // columns of one line's accumulators
-// instruction descriptor: D FP32, A and B BF16, both K-major, N = 32, M = 128
-constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kF >> 3) << 17) |
-                            ((uint32_t)(kTileM >> 4) << 24);
-static_assert(kIdesc == 0x08080490u, "instruction descriptor");
+constexpr int kRing = 16;                        // line accumulators in tensor memory
+constexpr uint32_t kTmemCols = kRing * kF;       // 512: all of it (one CTA per SM)
+// instruction descriptor: D FP32, A and B BF16, both K-major, M = 128; N in bits 17-22
+constexpr uint32_t kIdescBase = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kTileM >> 4) << 24);
+static_assert((kIdescBase | (4u << 17)) == 0x08080490u, "instruction descriptor (N = 32)");
 
-// Packed network: per block [27 taps][4 chunks][32 out][8 in] BF16, then biases, then the
-// 1x1x1 layer.
+// Packed network: per block [9 (dz, dx)][3 dy x 32 out][32 in] BF16 in the 64-byte swizzled
+// K-major layout, then biases, then the 1x1x1 layer.
 constexpr size_t kNetW = 0;
 constexpr size_t kNetBias = 5 * (size_t)kWBytes;              // 5 x 32 FP32
 constexpr size_t kNetOutW = kNetBias + 5 * kF * 4;            // 4 x 32 FP32
@@ -69,7 +64,7 @@ struct SmemLayout {
     static constexpr int W = 0;
     static constexpr int A = W + kWBytes;
     static constexpr int BAR = A + kRowSlots * kSlotBytes;
-    static constexpr int NBAR = 2 * kRowSlots + 6;
+    static constexpr int NBAR = 2 * kRowSlots + 2 * kRing + 2;
     static constexpr int TSLOT = BAR + NBAR * 8;
     static constexpr int BIAS = TSLOT + 16;
     static constexpr int OUTW = BIAS + kF * 4;
@@ -81,12 +76,12 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
-__device__ __forceinline__ void tma_load_5d(void* dst, const CUtensorMap* map, uint64_t* bar, int c0, int c1, int c2,
-                                            int c3, int c4) {
+__device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, uint64_t* bar, int c0, int c1, int c2,
+                                            int c3) {
     asm volatile(
-        "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5, %6, "
-        "%7}], [%2];" ::"r"(smem_u32(dst)),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4)
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5, %6}], "
+        "[%2];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(c0), "r"(c1), "r"(c2), "r"(c3)
         : "memory");
 }
 
@@ -100,21 +95,51 @@ __device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t b
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
-// Shared-memory matrix descriptor: no swizzle, byte offsets between core matrices along K
-// (lbo) and between 8-row groups along M/N (sbo).
-__device__ __forceinline__ uint64_t umma_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+// Shared-memory matrix descriptor, K-major with 64-byte swizzling: start address, 8-row group
+// stride 512 bytes, leading offset unused (1), fixed field 0b001, base offset 0 (the swizzle
+// follows the absolute address bits, as the TMA writes it), layout type 4 (SWIZZLE_64B).  The
+// start address is the low field, so a descriptor of addr + off is this one plus off / 16
+// (shared addresses stay below 256 KB: no carry out of the field).
+__device__ __forceinline__ uint64_t umma_desc_sw64(uint32_t saddr) {
     uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFFu);
-    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
-    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+    d |= (uint64_t)1 << 16;
+    d |= (uint64_t)(512 >> 4) << 32;
     d |= 1ull << 46;
+    d |= 4ull << 61;
     return d;
 }
 
-__device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t accumulate) {
+// MMA targets of an input row for taps dy in [a, b]: lines t0j - dy sit in ring slots
+// (dy - t0j) mod kRing, consecutive except across the wrap, so at most two runs; each run has
+// its accumulator columns, B offset (16-byte units) and instruction descriptor (N).
+struct MmaRuns {
+    uint32_t d0, boff0, idesc0, d1, boff1, idesc1;
+    bool two;
+};
+
+__device__ __forceinline__ uint32_t idesc_n(int n) { return kIdescBase | ((uint32_t)n >> 3 << 17); }
+
+__device__ __forceinline__ MmaRuns mma_runs(uint32_t tmem, int t0j, int a, int b) {
+    MmaRuns r;
+    const int sa = (a - t0j) & (kRing - 1);
+    const int len = b - a + 1;
+    const int l1 = min(len, kRing - sa);
+    r.d0 = tmem + (uint32_t)(sa * kF);
+    r.boff0 = (uint32_t)(a * kF * kRowBytes) >> 4;
+    r.idesc0 = idesc_n(l1 * kF);
+    r.two = l1 < len;
+    r.d1 = tmem;  // the wrap continues at slot 0
+    r.boff1 = (uint32_t)((a + l1) * kF * kRowBytes) >> 4;
+    r.idesc1 = idesc_n((len - l1) * kF);
+    return r;
+}
+
+__device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                          uint32_t accumulate) {
     asm volatile(
         "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
         " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
-        "l"(adesc), "l"(bdesc), "r"(kIdesc), "r"(accumulate)
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
         : "memory");
 }
 
@@ -144,17 +169,19 @@ __device__ __forceinline__ void flag_timeout(unsigned int* status) { atomicOr(st
 template <bool FINAL>
 __global__ void __launch_bounds__(kThreads, 1)
 k_conv_tc(const __grid_constant__ CUtensorMap in_map, const unsigned char* __restrict__ net, int layer, int K, int H,
-          int W, int Wp, __nv_bfloat16* __restrict__ out_act, float* __restrict__ out_res,
+          int W, __nv_bfloat16* __restrict__ out_act, float* __restrict__ out_res,
           unsigned int* __restrict__ status) {
-    extern __shared__ __align__(1024) unsigned char smem[];
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    // the swizzled operands assume 1024-byte aligned atoms: align the base (1 KB of slack allocated)
+    unsigned char* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
     unsigned char* sW = smem + SmemLayout::W;
     unsigned char* sA = smem + SmemLayout::A;
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem + SmemLayout::BAR);
     uint64_t* full = bars;
     uint64_t* empty = bars + kRowSlots;
     uint64_t* tfull = bars + 2 * kRowSlots;
-    uint64_t* tempty = tfull + 2;
-    uint64_t* wbar = tempty + 2;
+    uint64_t* tempty = tfull + kRing;
+    uint64_t* wbar = tempty + kRing;
     uint64_t* mma_done = wbar + 1;  // drain of the MMAs on an abort
     uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + SmemLayout::TSLOT);
     float* sBias = reinterpret_cast<float*>(smem + SmemLayout::BIAS);
@@ -174,7 +201,7 @@ k_conv_tc(const __grid_constant__ CUtensorMap in_map, const unsigned char* __res
             mbar_init(&full[i], 1);
             mbar_init(&empty[i], 1);
         }
-        for (int b = 0; b < 2; ++b) {
+        for (int b = 0; b < kRing; ++b) {
             mbar_init(&tfull[b], 1);
             mbar_init(&tempty[b], 4);
         }
@@ -222,8 +249,7 @@ k_conv_tc(const __grid_constant__ CUtensorMap in_map, const unsigned char* __res
                 mbar_expect_tx(&full[slot], kSlotBytes);
                 unsigned char* dst = sA + slot * kSlotBytes;
                 for (int dz = 0; dz < 3; ++dz)
-                    tma_load_5d(dst + dz * kStageBytes, &in_map, &full[slot], 0, tx * (kTileM / 8) - 1, 0, r,
-                                z + dz - 1);
+                    tma_load_4d(dst + dz * kStageBytes, &in_map, &full[slot], 0, tx * kTileM - 8, r, z + dz - 1);
             }
             seg = seg_end;
         }
@@ -243,59 +269,61 @@ k_conv_tc(const __grid_constant__ CUtensorMap in_map, const unsigned char* __res
         // ------------------------------------------------------------- MMA issuer
         bool ok = mbar_wait(wbar, 0);
         const uint32_t abase = smem_u32(sA);
-        const uint64_t wdesc = umma_desc(smem_u32(sW), kF * 16, 128);
-        int irow = 0, t = 0;
+        const uint64_t bdesc0 = umma_desc_sw64(smem_u32(sW));
+        int irow = 0, t0 = 0;  // staged rows and output lines of this CTA before the current run
+        static_assert((kRing & (kRing - 1)) == 0, "ring size is a power of two");
         for (long long seg = r_begin; seg < r_end && ok;) {
             const long long col = seg / H;
             const long long seg_end = min(r_end, (col + 1) * H);
             const int n = (int)(seg_end - seg);
-            for (int o = 0; o < n && ok; ++o, ++t) {
-                const int b = t & 1, u = t >> 1;
-                if (u > 0 && !mbar_wait(&tempty[b], (uint32_t)((u - 1) & 1))) {
+            for (int j = 0; j < n + 2 && ok; ++j) {  // input rows y0 - 1 .. y0 + n
+                const int lo = max(0, j - (n - 1)), hi = min(2, j);
+                if (j < n) {  // line t0 + j starts here: its ring slot must have been drained
+                    const int t = t0 + j;
+                    if (t >= kRing && !mbar_wait(&tempty[(-t) & (kRing - 1)], (uint32_t)((t / kRing - 1) & 1))) {
+                        ok = false;
+                        break;
+                    }
+                }
+                // the row's targets: all of [lo, hi], and for its first product the new line
+                // (dy = 0, initialised) apart from the others
+                const MmaRuns all = mma_runs(tmem, t0 + j, lo, hi);
+                const MmaRuns fresh = mma_runs(tmem, t0 + j, 0, 0);
+                const MmaRuns rest = mma_runs(tmem, t0 + j, 1, max(hi, 1));
+                const int jr = irow + j;
+                if (!mbar_wait(&full[jr % kRowSlots], (uint32_t)((jr / kRowSlots) & 1)) || *(volatile int*)&s_abort) {
                     ok = false;
                     break;
                 }
-                // input rows y-1, y, y+1 of output line o: staged rows irow + o .. irow + o + 2
-                for (int dy = 0; dy < 3 && ok; ++dy) {
-                    const int j = irow + o + dy;
-                    if (!mbar_wait(&full[j % kRowSlots], (uint32_t)((j / kRowSlots) & 1)) ||
-                        *(volatile int*)&s_abort)
-                        ok = false;
-                }
-                if (!ok) break;
                 tc_fence_after();
-                const uint32_t d = tmem + (uint32_t)b * kAccStride;
-                // descriptors of the three staged rows; every operand below is one of them (or the
-                // weights' descriptor) advanced by a compile-time offset in 16-byte units
-                uint64_t arow[3];
+                const uint64_t adesc0 = umma_desc_sw64(abase + (uint32_t)((jr % kRowSlots) * kSlotBytes));
 #pragma unroll
-                for (int dy = 0; dy < 3; ++dy)
-                    arow[dy] = umma_desc(abase + (uint32_t)(((irow + o + dy) % kRowSlots) * kSlotBytes),
-                                         kChunkBytes, 128);
+                for (int g = 0; g < 9; ++g)
 #pragma unroll
-                for (int hh = 0; hh < 9; ++hh)
-#pragma unroll
-                    for (int dx = 0; dx < 3; ++dx)
-#pragma unroll
-                        for (int kk = 0; kk < 2; ++kk) {
-                            const uint32_t aoff =
-                                (uint32_t)((hh / 3) * kStageBytes + kk * 2 * kChunkBytes + (7 + dx) * 16);
-                            const uint32_t boff = (uint32_t)((hh * 3 + dx) * kTapBytes + kk * 2 * kF * 16);
-                            // consecutive MMAs go to different accumulators so that they do not
-                            // wait on one another; the epilogue adds the four partial sums
-                            const int idx = (hh * 3 + dx) * 2 + kk;
-                            umma_bf16(d + (uint32_t)((idx % kNAcc) * kF), arow[hh % 3] + (aoff >> 4),
-                                      wdesc + (boff >> 4), idx >= kNAcc ? 1u : 0u);
+                    for (int kk = 0; kk < 2; ++kk) {
+                        const int dz = g / 3, dx = g % 3;
+                        const uint64_t ad =
+                            adesc0 + (uint64_t)((uint32_t)(dz * kStageBytes + (7 + dx) * kRowBytes + kk * 32) >> 4);
+                        const uint64_t bd = bdesc0 + (uint64_t)((uint32_t)(g * kGroupBytes + kk * 32) >> 4);
+                        if (g == 0 && kk == 0 && lo == 0) {  // the first product of a new line initialises it
+                            umma_bf16(fresh.d0, ad, bd + fresh.boff0, fresh.idesc0, 0u);
+                            if (hi >= 1) {
+                                umma_bf16(rest.d0, ad, bd + rest.boff0, rest.idesc0, 1u);
+                                if (rest.two) umma_bf16(rest.d1, ad, bd + rest.boff1, rest.idesc1, 1u);
+                            }
+                        } else {
+                            umma_bf16(all.d0, ad, bd + all.boff0, all.idesc0, 1u);
+                            if (all.two) umma_bf16(all.d1, ad, bd + all.boff1, all.idesc1, 1u);
                         }
-                umma_commit(&tfull[b]);
-                // row y-1 is read by no later line of this run
-                umma_commit(&empty[(irow + o) % kRowSlots]);
-                if (o == n - 1) {  // the run's last two rows
-                    umma_commit(&empty[(irow + n) % kRowSlots]);
-                    umma_commit(&empty[(irow + n + 1) % kRowSlots]);
+                    }
+                umma_commit(&empty[jr % kRowSlots]);  // the row is read by no later MMA
+                if (j >= 2) {  // line t0 + j - 2 has all its rows
+                    const int t = t0 + j - 2;
+                    umma_commit(&tfull[(-t) & (kRing - 1)]);
                 }
             }
             irow += n + 2;
+            t0 += n;
             seg = seg_end;
         }
         if (!ok) {
@@ -311,9 +339,9 @@ k_conv_tc(const __grid_constant__ CUtensorMap in_map, const unsigned char* __res
         int t = 0;
         bool run = true;
         for (long long line = r_begin; line < r_end && run; ++line, ++t) {
-            const int b = t & 1, u = t >> 1;
+            const int b = (-t) & (kRing - 1);  // ring slot of line t
             bool ok = true;
-            if (lane == 0) ok = mbar_wait(&tfull[b], (uint32_t)(u & 1)) && !*(volatile int*)&s_abort;
+            if (lane == 0) ok = mbar_wait(&tfull[b], (uint32_t)((t / kRing) & 1)) && !*(volatile int*)&s_abort;
             ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
             if (!ok) {
                 if (lane == 0) {
@@ -325,14 +353,7 @@ k_conv_tc(const __grid_constant__ CUtensorMap in_map, const unsigned char* __res
             }
             tc_fence_after();
             float acc[32];
-            tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)b * kAccStride, acc);
-#pragma unroll
-            for (int a = 1; a < kNAcc; ++a) {
-                float part[32];
-                tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)b * kAccStride + (uint32_t)(a * kF), part);
-#pragma unroll
-                for (int c = 0; c < kF; ++c) acc[c] += part[c];
-            }
+            tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(b * kF), acc);
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(&tempty[b]);
@@ -340,10 +361,9 @@ k_conv_tc(const __grid_constant__ CUtensorMap in_map, const unsigned char* __res
             const int y = (int)(line % H);
             const int tx = (int)(col % tiles_x), z = (int)(col / tiles_x);
             const int x = tx * kTileM + 32 * q + lane;
-            if (x >= (FINAL ? W : Wp)) continue;
-            const bool pad = x >= W;  // padding voxels of a line stay zero
+            if (x >= W) continue;
 #pragma unroll
-            for (int c = 0; c < kF; ++c) acc[c] = pad ? 0.f : fmaxf(acc[c] + sBias[c], 0.f);
+            for (int c = 0; c < kF; ++c) acc[c] = fmaxf(acc[c] + sBias[c], 0.f);
             if constexpr (FINAL) {
                 float4 r;
                 r.x = sOutB[0]; r.y = sOutB[1]; r.z = sOutB[2]; r.w = sOutB[3];
@@ -367,7 +387,7 @@ k_conv_tc(const __grid_constant__ CUtensorMap in_map, const unsigned char* __res
                     pk.y = *reinterpret_cast<uint32_t*>(&p1);
                     pk.z = *reinterpret_cast<uint32_t*>(&p2);
                     pk.w = *reinterpret_cast<uint32_t*>(&p3);
-                    *reinterpret_cast<uint4*>(out_act + ((((size_t)z * H + y) * 4 + ch) * Wp + x) * 8) = pk;
+                    *reinterpret_cast<uint4*>(out_act + (((size_t)z * H + y) * W + x) * kF + ch * 8) = pk;
                 }
             }
         }
@@ -381,23 +401,18 @@ k_conv_tc(const __grid_constant__ CUtensorMap in_map, const unsigned char* __res
     }
 }
 
-// V_s [C][K][H][W] FP32 -> act [K][H][4][Wp][8] BF16 (round to nearest even); channels >= C
-// and voxels x >= W are zero.
-__global__ void k_pack_input(const float* __restrict__ V, int C, int K, int H, int W, int Wp,
-                             __nv_bfloat16* __restrict__ act) {
-    const long long n = (long long)K * H * Wp;
+// V_s [C][K][H][W] FP32 -> act [K][H][W][32] BF16 (round to nearest even); channels >= C zero.
+__global__ void k_pack_input(const float* __restrict__ V, int C, int K, int H, int W, __nv_bfloat16* __restrict__ act) {
+    const long long n = (long long)K * H * W;
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    const int x = (int)(i % Wp);
-    const long long zy = i / Wp;
-    const size_t plane = (size_t)K * H * W;
 #pragma unroll
     for (int ch = 0; ch < 4; ++ch) {
         float v[8];
 #pragma unroll
         for (int e = 0; e < 8; ++e) {
             const int c = ch * 8 + e;
-            v[e] = (c < C && x < W) ? __ldg(V + (size_t)c * plane + (size_t)zy * W + x) : 0.f;
+            v[e] = c < C ? __ldg(V + (size_t)c * n + i) : 0.f;
         }
         uint4 pk;
         __nv_bfloat162 p0 = __floats2bfloat162_rn(v[0], v[1]), p1 = __floats2bfloat162_rn(v[2], v[3]);
@@ -406,12 +421,13 @@ __global__ void k_pack_input(const float* __restrict__ V, int C, int K, int H, i
         pk.y = *reinterpret_cast<uint32_t*>(&p1);
         pk.z = *reinterpret_cast<uint32_t*>(&p2);
         pk.w = *reinterpret_cast<uint32_t*>(&p3);
-        *reinterpret_cast<uint4*>(act + ((zy * 4 + ch) * Wp + x) * 8) = pk;
+        *reinterpret_cast<uint4*>(act + i * kF + ch * 8) = pk;
     }
 }
 
 // Batch-norm folding and packing of one block: w [32][cin][3][3][3] FP32 ->
-// [27 taps][4 chunks][32 out][8 in] BF16 (inputs >= cin zero) and the folded bias.
+// [9 (dz, dx)][3 dy x 32 out][32 in] BF16, 64-byte swizzled (inputs >= cin zero), and the
+// folded bias.
 __global__ void k_prepare_block(const float* __restrict__ w, const float* __restrict__ b, const float* __restrict__ gamma,
                                 const float* __restrict__ beta, const float* __restrict__ mean,
                                 const float* __restrict__ var, float eps, int cin, __nv_bfloat16* __restrict__ wp,
@@ -422,10 +438,15 @@ __global__ void k_prepare_block(const float* __restrict__ w, const float* __rest
         bias[i] = (b[i] - mean[i]) * s + beta[i];
     }
     if (i >= 27 * kF * kF) return;
-    const int ci = i % kF, co = (i / kF) % kF, tap = i / (kF * kF);
+    const int ci = i % kF, co = (i / kF) % kF, tap = i / (kF * kF);  // tap = (dz * 3 + dy) * 3 + dx
+    const int dz = tap / 9, dy = (tap / 3) % 3, dx = tap % 3;
     const float s = gamma[co] / sqrtf(var[co] + eps);
     const float v = ci < cin ? w[((size_t)co * cin + ci) * 27 + tap] * s : 0.f;
-    wp[(((size_t)tap * 4 + ci / 8) * kF + co) * 8 + ci % 8] = __float2bfloat16_rn(v);
+    // row n of group (dz, dx) holds output channel co of tap dy; its 16-byte chunk ci / 8 sits at
+    // chunk (ci / 8) ^ ((n / 2) % 4): the 64-byte swizzle of a 1024-byte aligned group
+    const int n = dy * kF + co;
+    const int chunk = (ci / 8) ^ ((n >> 1) & 3);
+    wp[((size_t)(dz * 3 + dx) * kGroupRows + n) * kF + chunk * 8 + ci % 8] = __float2bfloat16_rn(v);
 }
 
 }  // namespace
@@ -445,29 +466,26 @@ rl_status rl_lgd_prepare(const rl_lgd_params* p, void* net, cudaStream_t s) {
     return rl_check_launch("lgd_prepare");
 }
 
-int lgd_pitch(int W) { return (W + 7) & ~7; }
-
-size_t rl_lgd_act_bytes(int K, int H, int W) { return ((size_t)K * H * lgd_pitch(W) * kF * 2 + 255) & ~(size_t)255; }
+size_t rl_lgd_act_bytes(int K, int H, int W) { return ((size_t)K * H * W * kF * 2 + 1023) & ~(size_t)1023; }
 
 rl_status rl_lgd_forward(const void* net, const float* V, int C, int K, int H, int W, float* residual, void* act0,
                          void* act1, cudaStream_t s) {
-    const int Wp = lgd_pitch(W);
-    const long long n = (long long)K * H * Wp;
+    const long long n = (long long)K * H * W;
     {
         RLTraceScope ts("lgd_pack", s);
-        k_pack_input<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(V, C, K, H, W, Wp, (__nv_bfloat16*)act0);
+        k_pack_input<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(V, C, K, H, W, (__nv_bfloat16*)act0);
     }
     rl_status st = rl_check_launch("lgd_pack");
     if (st) return st;
     CUtensorMap maps[2];
-    if (!rl_encode_act_tmap(&maps[0], act0, K, H, Wp, kHaloCM) || !rl_encode_act_tmap(&maps[1], act1, K, H, Wp, kHaloCM))
+    if (!rl_encode_act_tmap(&maps[0], act0, K, H, W, kHalo) || !rl_encode_act_tmap(&maps[1], act1, K, H, W, kHalo))
         return rl_fail(RL_ECUDA, "lgd: activation tensor maps could not be encoded");
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const long long lines = (long long)K * H * ((W + kTileM - 1) / kTileM);
     const unsigned grid = (unsigned)std::min<long long>(lines, sms > 0 ? sms : 1);
-    const size_t smem = SmemLayout::TOTAL;
+    const size_t smem = SmemLayout::TOTAL + 1024;
     cudaFuncSetAttribute(k_conv_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     cudaFuncSetAttribute(k_conv_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     unsigned int* status = rl_device_status_ptr();
@@ -477,11 +495,11 @@ rl_status rl_lgd_forward(const void* net, const float* V, int C, int K, int H, i
         const int src = l & 1;
         if (l < 4) {
             RLTraceScope ts("lgd_conv_tc", s);
-            k_conv_tc<false><<<grid, kThreads, smem, s>>>(maps[src], (const unsigned char*)net, l, K, H, W, Wp,
+            k_conv_tc<false><<<grid, kThreads, smem, s>>>(maps[src], (const unsigned char*)net, l, K, H, W,
                                                           (__nv_bfloat16*)acts[src ^ 1], nullptr, status);
         } else {
             RLTraceScope ts("lgd_conv_tc_final", s);
-            k_conv_tc<true><<<grid, kThreads, smem, s>>>(maps[src], (const unsigned char*)net, l, K, H, W, Wp,
+            k_conv_tc<true><<<grid, kThreads, smem, s>>>(maps[src], (const unsigned char*)net, l, K, H, W,
                                                          nullptr, residual, status);
         }
         st = rl_check_launch("lgd_conv");

@@ -39,10 +39,9 @@ int rl_kernel_path_setting();
 // layout cannot be described (row pitch not a multiple of 16 bytes, misaligned base).
 bool rl_encode_mpi_tmap(CUtensorMap* map, const void* M, rl_dtype dt, int D, int H, int W);
 
-// TMA descriptor of a chunked BF16 activation volume [K][H][4][Wp][8] (32 channels as four
-// chunks of 8, Wp a multiple of 8) with a box of {one 8x8 core matrix, halo_cm core matrices
-// along x, 4 chunks}; false when it cannot be encoded (misaligned base, bad pitch).
-bool rl_encode_act_tmap(CUtensorMap* map, const void* act, int K, int H, int Wp, int halo_cm);
+// TMA descriptor of a BF16 activation volume [K][H][W][32] (16-byte aligned) with a box of
+// {32 channels, halo voxels along W} and 64-byte swizzling; false when it cannot be encoded.
+bool rl_encode_act_tmap(CUtensorMap* map, const void* act, int K, int H, int W, int halo);
 
 // ----------------------------------------------------------------- launchers
 // All take device pointers and enqueue on `s`; arguments are validated by the caller.

@@ -71,20 +71,18 @@ bool rl_encode_mpi_tmap(CUtensorMap* map, const void* M, rl_dtype dt, int D, int
     return r == CUDA_SUCCESS;
 }
 
-bool rl_encode_act_tmap(CUtensorMap* map, const void* act, int K, int H, int Wp, int halo_cm) {
-    if (((uintptr_t)act & 15) != 0 || K < 1 || H < 1 || Wp < 8 || (Wp & 7) != 0 || halo_cm < 1 || halo_cm > 256)
-        return false;
+bool rl_encode_act_tmap(CUtensorMap* map, const void* act, int K, int H, int W, int halo) {
+    if (((uintptr_t)act & 15) != 0 || K < 1 || H < 1 || W < 1 || halo < 1 || halo > 256) return false;
     PFN_cuTensorMapEncodeTiled_v12000 fn = encoder();
     if (!fn) return false;
-    // [z][y][chunk 4][Wp][8] BF16, innermost first: one core matrix (8 voxels x 8 channels),
-    // core matrices along x, chunk, y, z
-    const cuuint64_t dims[5] = {64, (cuuint64_t)(Wp / 8), 4, (cuuint64_t)H, (cuuint64_t)K};
-    const cuuint64_t cm = 128;  // bytes of one core matrix
-    const cuuint64_t strides[4] = {cm, cm * (Wp / 8), cm * (Wp / 8) * 4, cm * (Wp / 8) * 4 * H};
-    const cuuint32_t box[5] = {64, (cuuint32_t)halo_cm, 4, 1, 1};
-    const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
-    const CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<void*>(act), dims, strides, box, estr,
-                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+    // [z][y][x][32] BF16, innermost first: channel, x, y, z; 64-byte rows swizzled in 512-byte atoms
+    const cuuint64_t dims[4] = {32, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)K};
+    const cuuint64_t row = 64;  // bytes of one voxel
+    const cuuint64_t strides[3] = {row, row * W, row * W * H};
+    const cuuint32_t box[4] = {32, (cuuint32_t)halo, 1, 1};
+    const cuuint32_t estr[4] = {1, 1, 1, 1};
+    const CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void*>(act), dims, strides, box, estr,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS;
 }

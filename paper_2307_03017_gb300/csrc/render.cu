@@ -3,7 +3,10 @@
 // One thread per target pixel: for d = D-1 .. 0 (nearest first) sample plane d at
 // p = q + a(q) + rho_d b(q) (bilinear, zero padding per tap) and accumulate
 // C += T alpha c, T *= (1 - alpha).  The loop stops once T is exactly zero, after which
-// every further term is exactly zero.
+// every further term is exactly zero.  Views that are pure shifts of the reference (no
+// rotation, no depth offset, same focal lengths) take a kernel that computes each plane's
+// shift and weights once per block and renders four pixels of a column per thread, loading
+// each tap row once.
 #include "rl_internal.h"
 
 namespace {
@@ -43,6 +46,111 @@ k_render(const Tm* __restrict__ M, int D, int H, int W, const __grid_constant__ 
     o[2] = c2;
 }
 
+// Views with no rotation relative to the reference, no depth offset and the reference's
+// focal lengths: the warp offset p - q = a + rho_d b is the same for every pixel of a plane,
+// so the taps' integer shift and the bilinear weights are computed once per plane (by the
+// first D threads of a block, with the arithmetic of rl_taps / rl_sample_fast) and read from
+// shared memory.  Same samples, same results as k_render.
+struct RLPlaneShift {
+    int ix, iy, ok;
+    float fx, fy;
+    float w00, w10, w01, w11;
+};
+
+// One thread renders kShiftRows vertically adjacent pixels of a column: for each plane their
+// taps span kShiftRows + 1 rows of two columns, loaded once (kShiftRows + 1 rows x 2 loads
+// instead of kShiftRows x 4).
+constexpr int kShiftRows = 4;
+
+template <typename Tm>
+__global__ void __launch_bounds__(kRenderBX* kRenderBY)
+k_render_shift(const Tm* __restrict__ M, int D, int H, int W, const __grid_constant__ RLViews views,
+               float* __restrict__ out) {
+    __shared__ RLPlaneShift sp[RL_DEV_MAX_PLANES];
+    const int view = blockIdx.x;  // grid (views, tiles_x, tiles_y of kRenderBY * kShiftRows rows)
+    const int tid = threadIdx.y * kRenderBX + threadIdx.x;
+    if (tid < D) {
+        const RLWarp w = rl_warp_coeffs(views.v[view], 0.f, 0.f);  // the same for every pixel
+        const float dx = fmaf(views.rho[tid], w.bx, w.ax), dy = fmaf(views.rho[tid], w.by, w.ay);
+        const float flx = floorf(dx), fly = floorf(dy);
+        RLPlaneShift p;
+        p.ix = (int)flx;
+        p.iy = (int)fly;
+        p.fx = dx - flx;
+        p.fy = dy - fly;
+        p.ok = fabsf(dx) < 1.0e7f && fabsf(dy) < 1.0e7f;  // as rl_taps
+        p.w00 = (1.f - p.fx) * (1.f - p.fy);
+        p.w10 = p.fx * (1.f - p.fy);
+        p.w01 = (1.f - p.fx) * p.fy;
+        p.w11 = p.fx * p.fy;
+        sp[tid] = p;
+    }
+    __syncthreads();
+    const int qx = blockIdx.y * kRenderBX + threadIdx.x;
+    const int qy0 = (blockIdx.z * kRenderBY + threadIdx.y) * kShiftRows;
+    if (qx >= W || qy0 >= H) return;
+    const size_t plane = (size_t)H * W * 4;
+    float T[kShiftRows], c0[kShiftRows], c1[kShiftRows], c2[kShiftRows];
+#pragma unroll
+    for (int r = 0; r < kShiftRows; ++r) { T[r] = 1.f; c0[r] = c1[r] = c2[r] = 0.f; }
+    for (int d = D - 1; d >= 0; --d) {
+        const RLPlaneShift p = sp[d];
+        const int x0 = qx + p.ix, y0 = qy0 + p.iy;
+        float4 m[kShiftRows];
+        if (p.ok && (unsigned)x0 < (unsigned)(W - 1) && y0 >= 0 && y0 + kShiftRows < H) {
+            // all kShiftRows + 1 tap rows inside: load each once
+            const Tm* q = M + d * plane + (unsigned)(y0 * W + x0) * 4u;
+            float4 a0 = RLStore<Tm>::load4(q), a1 = RLStore<Tm>::load4(q + 4);
+#pragma unroll
+            for (int r = 0; r < kShiftRows; ++r) {
+                const Tm* qr = q + (r + 1) * 4 * W;
+                const float4 b0 = RLStore<Tm>::load4(qr), b1 = RLStore<Tm>::load4(qr + 4);
+                float2 lo = __fmul2_rn(make_float2(p.w00, p.w00), make_float2(a0.x, a0.y));
+                float2 hi = __fmul2_rn(make_float2(p.w00, p.w00), make_float2(a0.z, a0.w));
+                lo = __ffma2_rn(make_float2(p.w10, p.w10), make_float2(a1.x, a1.y), lo);
+                hi = __ffma2_rn(make_float2(p.w10, p.w10), make_float2(a1.z, a1.w), hi);
+                lo = __ffma2_rn(make_float2(p.w01, p.w01), make_float2(b0.x, b0.y), lo);
+                hi = __ffma2_rn(make_float2(p.w01, p.w01), make_float2(b0.z, b0.w), hi);
+                lo = __ffma2_rn(make_float2(p.w11, p.w11), make_float2(b1.x, b1.y), lo);
+                hi = __ffma2_rn(make_float2(p.w11, p.w11), make_float2(b1.z, b1.w), hi);
+                m[r] = make_float4(lo.x, lo.y, hi.x, hi.y);
+                a0 = b0;
+                a1 = b1;
+            }
+        } else {
+#pragma unroll
+            for (int r = 0; r < kShiftRows; ++r) {
+                RLTaps t;
+                t.x0 = x0;
+                t.y0 = y0 + r;
+                t.fx = p.fx;
+                t.fy = p.fy;
+                t.ok = p.ok != 0;
+                m[r] = rl_sample(M + d * plane, H, W, t);
+            }
+        }
+        bool any = false;
+#pragma unroll
+        for (int r = 0; r < kShiftRows; ++r) {
+            const float a = T[r] * m[r].w;
+            c0[r] = fmaf(a, m[r].x, c0[r]);
+            c1[r] = fmaf(a, m[r].y, c1[r]);
+            c2[r] = fmaf(a, m[r].z, c2[r]);
+            T[r] = T[r] * (1.f - m[r].w);
+            any |= T[r] != 0.f;
+        }
+        if (!any) break;  // every further term of every pixel is exactly zero
+    }
+#pragma unroll
+    for (int r = 0; r < kShiftRows; ++r) {
+        if (qy0 + r >= H) break;
+        float* o = out + (((size_t)view * H + qy0 + r) * W + qx) * 3;
+        o[0] = c0[r];
+        o[1] = c1[r];
+        o[2] = c2[r];
+    }
+}
+
 __global__ void k_warp_offsets(int D, int H, int W, const __grid_constant__ RLViews views, float* __restrict__ out) {
     const int qx = blockIdx.x * blockDim.x + threadIdx.x;
     const int qy = blockIdx.y;
@@ -70,6 +178,18 @@ rl_status rl_launch_render(const void* M, rl_dtype dt, int D, int H, int W, cons
     dim3 block(kRenderBX, kRenderBY);
     const int tiles_x = (W + kRenderBX - 1) / kRenderBX, tiles_y = (H + kRenderBY - 1) / kRenderBY;
     const dim3 grid((unsigned)views.n, (unsigned)tiles_x, (unsigned)tiles_y);
+    if (rl_views_are_shifts(views)) {
+        const dim3 sgrid((unsigned)views.n, (unsigned)tiles_x,
+                         (unsigned)((H + kRenderBY * kShiftRows - 1) / (kRenderBY * kShiftRows)));
+        if (dt == RL_F32) {
+            RLTraceScope ts("render_shift_f32", s);
+            k_render_shift<float><<<sgrid, block, 0, s>>>((const float*)M, D, H, W, views, out);
+        } else {
+            RLTraceScope ts("render_shift_bf16", s);
+            k_render_shift<__nv_bfloat16><<<sgrid, block, 0, s>>>((const __nv_bfloat16*)M, D, H, W, views, out);
+        }
+        return rl_check_launch("render");
+    }
     if (dt == RL_F32) {
         RLTraceScope ts("render_f32", s);
         k_render<float><<<grid, block, 0, s>>>((const float*)M, D, H, W, views, tiles_x, out);

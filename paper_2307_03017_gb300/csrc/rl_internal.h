@@ -43,6 +43,19 @@ bool rl_encode_mpi_tmap(CUtensorMap* map, const void* M, rl_dtype dt, int D, int
 // {32 channels, halo voxels along W} and 64-byte swizzling; false when it cannot be encoded.
 bool rl_encode_act_tmap(CUtensorMap* map, const void* act, int K, int H, int W, int halo);
 
+// True when every view's warp offset p - q is the same for all pixels of a plane: no
+// rotation relative to the reference (R_rel - I exactly 0 in FP32), no depth offset of the
+// centre and the reference's focal lengths.
+inline bool rl_views_are_shifts(const RLViews& v) {
+    for (int i = 0; i < v.n; ++i) {
+        const RLViewParam& p = v.v[i];
+        for (int j = 0; j < 9; ++j)
+            if (p.E[j] != 0.f) return false;
+        if (p.C[2] != 0.f || p.dfx != 0.f || p.dfy != 0.f) return false;
+    }
+    return v.n > 0;
+}
+
 // ----------------------------------------------------------------- launchers
 // All take device pointers and enqueue on `s`; arguments are validated by the caller.
 

@@ -113,6 +113,24 @@ def test_render_matches_oracle_paper_sampled(rl, kernel_path, paper):
         assert np.abs(out[j][ys, xs] - ref).max() <= TOL32
 
 
+@pytest.mark.parametrize("dtype", [torch.float32, torch.bfloat16], ids=["f32", "bf16"])
+def test_shift_render_equals_general_render(rl, small, dtype):
+    """Views that are pure shifts of the reference take a kernel with per-plane shifts and
+    weights; rendered in one launch with a rotated view they take the general kernel.  Same
+    samples, same arithmetic: the same bits."""
+    rl.reallife_set_kernel_path(2)
+    try:
+        sc = small
+        m = _mpi(rl, sc, dtype)
+        far = sg.Camera(sc.ref.K, np.eye(3), np.array([0.9, -0.4, 0.0]))  # mostly outside the MPI
+        shifts = sc.novel + [far]
+        a = rl.reallife_render(m, shifts).cpu().numpy()
+        b = rl.reallife_render(m, shifts + [sc.src[0]]).cpu().numpy()
+        assert np.array_equal(a, b[:len(shifts)])
+    finally:
+        rl.reallife_set_kernel_path(0)
+
+
 def test_render_edge_cases(rl, kernel_path):
     # ragged tile tails (W % 32, H % 4 != 0), one plane, a view that sees mostly outside the MPI
     sc = sg.make_scene(5, 23, 37, 1, 2, n_layers=(1, 2), f=30.0, n_novel=3)

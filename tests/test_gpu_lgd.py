@@ -101,6 +101,32 @@ def test_learned_step_matches_oracle(rl, level):
     assert np.percentile(err[got != sc.coarse_mpi], 99) <= 2e-3 * scale + 1e-6
 
 
+@pytest.mark.parametrize("level,selection", [(0, 0), (2, 0), (1, 1)], ids=["l0-topk", "l2-topk", "l1-mvs"])
+def test_learned_step_bf16_storage(rl, level, selection):
+    """BF16 MPI storage (the update rounds to BF16), coarse levels and MVS selection."""
+    sc = sg.workload("small", 1)[0]
+    k = 3
+    params = sg.lgd_weights(14, 4 * len(sc.src) + 4)
+    net = rl.LgdNet(params)
+    M = torch.from_numpy(sc.coarse_mpi).cuda().to(torch.bfloat16).contiguous()
+    Mh = M.to(torch.float64).cpu().numpy()
+    m = rl.make_mpi(M, sc.near, sc.far, sc.ref)
+    h, w = sc.H >> level, sc.W >> level
+    S = torch.empty((k, h, w), dtype=torch.uint8, device="cuda")
+    rl.reallife_lgd_step(m, torch.from_numpy(sc.images).cuda(), sc.src, k, net, level=level, selection=selection,
+                         S_out=S)
+    torch.cuda.synchronize()
+    S_h = S.cpu().numpy()
+    M_o, res_o, _ = olgd.lgd_step(Mh, sc.near, sc.far, sc.ref, sc.src, sc.images, params, k, level, selection,
+                                  S_pin=S_h)
+    got = M.to(torch.float64).cpu().numpy()
+    # the level MPI is BF16-rounded on the device (FP64 in the oracle) and the result is stored
+    # in BF16: one BF16 ulp of the values (2^-8 relative) plus the network tolerance
+    scale = float(np.abs(res_o).max())
+    err = np.abs(got - olgd.round_bf16(M_o))
+    assert err.max() <= 1e-2 * scale + 2.0 ** -8, f"max err {err.max()} vs residual scale {scale}"
+
+
 def test_learned_step_rejects_too_many_views(rl):
     sc = sg.make_scene(1, 16, 16, 4, 8, n_layers=(1, 2))
     params = sg.lgd_weights(13, 32)

@@ -43,7 +43,7 @@ L2_FLUSH_BYTES = 512 << 20
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="paper", choices=["paper", "paper_bf16", "display", "small", "serve"])
@@ -83,9 +83,15 @@ def reduce_max(x: float, dist, device) -> float:
     return float(t.item())
 
 
-def csrc_digest() -> str:
+def csrc_digest(files=None) -> str:
+    """Digest of the named source files (paths relative to the repository root), by default
+    every file of the CUDA sources: a stored ncu counter is used only while it matches."""
+    if files is None:
+        paths = sorted(glob.glob(os.path.join(ROOT, "paper_2307_03017_gb300", "csrc", "*")))
+    else:
+        paths = [os.path.join(ROOT, f) for f in files]
     h = hashlib.sha256()
-    for p in sorted(glob.glob(os.path.join(ROOT, "paper_2307_03017_gb300", "csrc", "*"))):
+    for p in paths:
         with open(p, "rb") as f:
             h.update(os.path.basename(p).encode())
             h.update(f.read())
@@ -104,6 +110,7 @@ class ClockSampler:
         self.proc = None
         self.lines = []
         self.t = None
+        self.first = threading.Event()
 
     def start(self):
         try:
@@ -115,10 +122,12 @@ class ClockSampler:
             return
         self.t = threading.Thread(target=self._read, daemon=True)
         self.t.start()
+        self.first.wait(timeout=3.0)  # the samples cover the timed region from its start
 
     def _read(self):
         for line in self.proc.stdout:
             self.lines.append(line.strip())
+            self.first.set()
 
     def stop(self) -> dict | None:
         if self.proc is None:
@@ -299,7 +308,7 @@ def run_ours(args, world, rank, local):
     if os.path.exists(tf):
         try:
             tr = json.load(open(tf)).get(f"{args.workload}:{dom_name}")
-            if tr and tr.get("csrc_digest") == csrc_digest():
+            if tr and tr.get("csrc_digest") == csrc_digest(tr.get("files")):
                 traffic = tr["dram_bytes_per_launch"]
         except Exception:
             traffic = None
@@ -682,13 +691,21 @@ def platform_cpu() -> str:
 
 
 def run_reference(args, world, rank):
-    """The oracle on the host cores, each step a 1/8-height band of the workload (scaled)."""
+    """The oracle on the host cores, each step a horizontal band of the workload (scaled by its
+    share of the pixels).  One untimed step on a 4-row band (the least height the coarsest
+    pyramid level allows) sizes the band so that the warm-up and timed steps take about two
+    minutes: at most 1/8 of the rows, at least 4."""
     if rank != 0:
         return None
     import oracle
     oracle.build()
     sc, cfg = load_scene(args.workload, args.seed)
-    rows = sample_rows(sc, 0.125)
+    unit = 1 << max(cfg["schedule"])
+    t0 = time.perf_counter()
+    oracle_step(crop_scene(sc, unit), cfg)
+    t1 = time.perf_counter() - t0
+    units = int(120.0 / max(1, args.steps + args.warmup) / max(t1, 1e-6))
+    rows = unit * max(1, min(sample_rows(sc, 0.125) // unit, units))
     band = crop_scene(sc, rows)
     share = rows / sc.H
     for _ in range(args.warmup):

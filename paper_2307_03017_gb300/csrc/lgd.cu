@@ -14,16 +14,18 @@
 // Output: lines of 128 consecutive voxels of one (z, y) x 32 channels, accumulated in FP32 in
 // tensor memory.  Persistent CTAs (one per SM) each take a contiguous run of output lines in
 // (z, x-tile, y) order and walk it along y.  Every input row (the halos of planes z-1, z, z+1
-// at one y) is copied once into a ring of staged rows and multiplied once: the weights of one
-// (dz, dx) tap pair are stacked over dy as a 96-row B operand, so that one 128x96x16 MMA adds
-// the row's contribution to the three output lines y+1, y, y-1 that read it (their
-// accumulators sit in consecutive 32-column slots of a 16-line tensor-memory ring, in
-// descending y).  A line is complete after its third input row; 9 (dz, dx) x 2 K steps = 18
-// MMAs per input row (split where the ring wraps, where a line starts, and at the ends of a
-// run).  Warp-specialised: warp 0 issues the TMA copies, warp 1 the MMAs (one lane), warps 2-5
-// drain completed lines: bias, ReLU, BF16 rounding and the store of the next layer's
-// activations; after the last block they also apply the 1x1x1 layer and store the FP32
-// residual [z][y][x][4].
+// at one y) is copied once into a ring of five staged rows and multiplied once: the weights of
+// one (dz, dx) tap pair are stacked over dy as a 96-row B operand, so that one 128x96x16 MMA
+// forms the row's products for the three output lines y+1, y, y-1 that read it.  Each staged
+// row has its own 96-column accumulator window (four windows taken in turn), initialised by
+// its first MMA, so no two MMAs in flight write the same columns; the epilogue adds a line's
+// three partial products from three consecutive windows.  A row inside a run is a fixed,
+// branch-free sequence of 9 (dz, dx) x 2 K steps = 18 MMAs with constant descriptor offsets
+// (a single issuing thread keeps the tensor core fed only with such a lean sequence); the two
+// rows at each end of a run take their taps one by one.  Warp-specialised: warp 0 issues the
+// TMA copies, warp 1 the MMAs (one lane), warps 2-5 drain the windows and finish completed
+// lines: bias, ReLU, BF16 rounding and the store of the next layer's activations; after the
+// last block they also apply the 1x1x1 layer and store the FP32 residual [z][y][x][4].
 //
 // Every mbarrier wait is bounded; a wait that gives up sets RL_DEVFLAG_TIMEOUT, the roles
 // stop, the producer waits (bounded) for its copies in flight and the MMA lane for its MMAs,
@@ -46,8 +48,9 @@ constexpr int kGroupRows = 3 * kF;               // the dy-stacked weights of on
 constexpr int kGroupBytes = kGroupRows * kRowBytes;  // [96][32] BF16, 64-byte swizzled
 constexpr int kWBytes = 9 * kGroupBytes;         // 55296
 constexpr int kThreads = 192;
-constexpr int kRing = 16;                        // line accumulators in tensor memory
-constexpr uint32_t kTmemCols = kRing * kF;       // 512: all of it (one CTA per SM)
+constexpr int kSets = 4;                         // accumulator windows, taken by staged rows in turn
+constexpr uint32_t kSetCols = 128;               // one window: tap dy in columns 32 dy .. 32 dy + 31
+constexpr uint32_t kTmemCols = kSets * kSetCols;  // 512: all of it (one CTA per SM)
 // instruction descriptor: D FP32, A and B BF16, both K-major, M = 128; N in bits 17-22
 constexpr uint32_t kIdescBase = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kTileM >> 4) << 24);
 static_assert((kIdescBase | (4u << 17)) == 0x08080490u, "instruction descriptor (N = 32)");
@@ -64,7 +67,7 @@ struct SmemLayout {
     static constexpr int W = 0;
     static constexpr int A = W + kWBytes;
     static constexpr int BAR = A + kRowSlots * kSlotBytes;
-    static constexpr int NBAR = 2 * kRowSlots + 2 * kRing + 2;
+    static constexpr int NBAR = 2 * kRowSlots + 2 * kSets + 2;
     static constexpr int TSLOT = BAR + NBAR * 8;
     static constexpr int BIAS = TSLOT + 16;
     static constexpr int OUTW = BIAS + kF * 4;
@@ -79,8 +82,8 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
 __device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, uint64_t* bar, int c0, int c1, int c2,
                                             int c3) {
     asm volatile(
-        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5, %6}], "
-        "[%2];" ::"r"(smem_u32(dst)),
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
+        "[%0], [%1, {%3, %4, %5, %6}], [%2];" ::"r"(smem_u32(dst)),
         "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(c0), "r"(c1), "r"(c2), "r"(c3)
         : "memory");
 }
@@ -109,29 +112,15 @@ __device__ __forceinline__ uint64_t umma_desc_sw64(uint32_t saddr) {
     return d;
 }
 
-// MMA targets of an input row for taps dy in [a, b]: lines t0j - dy sit in ring slots
-// (dy - t0j) mod kRing, consecutive except across the wrap, so at most two runs; each run has
-// its accumulator columns, B offset (16-byte units) and instruction descriptor (N).
-struct MmaRuns {
-    uint32_t d0, boff0, idesc0, d1, boff1, idesc1;
-    bool two;
-};
-
 __device__ __forceinline__ uint32_t idesc_n(int n) { return kIdescBase | ((uint32_t)n >> 3 << 17); }
 
-__device__ __forceinline__ MmaRuns mma_runs(uint32_t tmem, int t0j, int a, int b) {
-    MmaRuns r;
-    const int sa = (a - t0j) & (kRing - 1);
-    const int len = b - a + 1;
-    const int l1 = min(len, kRing - sa);
-    r.d0 = tmem + (uint32_t)(sa * kF);
-    r.boff0 = (uint32_t)(a * kF * kRowBytes) >> 4;
-    r.idesc0 = idesc_n(l1 * kF);
-    r.two = l1 < len;
-    r.d1 = tmem;  // the wrap continues at slot 0
-    r.boff1 = (uint32_t)((a + l1) * kF * kRowBytes) >> 4;
-    r.idesc1 = idesc_n((len - l1) * kF);
-    return r;
+// Descriptor steps (16-byte units) of tap pair g = (dz, dx) and K step kk: the A operand is the
+// halo of plane z + dz - 1 from row 7 + dx on, the B operand the weights of group g.
+__device__ __forceinline__ constexpr uint64_t a_step(int g, int kk) {
+    return (uint32_t)((g / 3) * kStageBytes + (7 + g % 3) * kRowBytes + kk * 32) >> 4;
+}
+__device__ __forceinline__ constexpr uint64_t b_step(int g, int kk) {
+    return (uint32_t)(g * kGroupBytes + kk * 32) >> 4;
 }
 
 __device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
@@ -148,9 +137,10 @@ __device__ __forceinline__ void umma_commit(uint64_t* bar) {
                  : "memory");
 }
 
-// 32 lanes x 32 consecutive FP32 columns: thread t of the warp gets lane (base + t).
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
-    uint32_t r[32];
+// 32 lanes x 32 consecutive FP32 columns: thread t of the warp gets lane (base + t).  The
+// registers are valid only after tmem_wait_ld() and tmem_regs_ready() on them: the empty
+// statement ties every later use of the registers to a point after the wait.
+__device__ __forceinline__ void tmem_ld32_async(uint32_t taddr, uint32_t (&r)[32]) {
     asm volatile(
         "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
         "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
@@ -159,9 +149,17 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
           "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
           "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
         : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_regs_ready(uint32_t (&r)[32]) {
+    asm volatile(""
+                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
+                   "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]),
+                   "+r"(r[15]), "+r"(r[16]), "+r"(r[17]), "+r"(r[18]), "+r"(r[19]), "+r"(r[20]), "+r"(r[21]),
+                   "+r"(r[22]), "+r"(r[23]), "+r"(r[24]), "+r"(r[25]), "+r"(r[26]), "+r"(r[27]), "+r"(r[28]),
+                   "+r"(r[29]), "+r"(r[30]), "+r"(r[31]));
 }
 
 __device__ __forceinline__ void flag_timeout(unsigned int* status) { atomicOr(status, RL_DEVFLAG_TIMEOUT); }
@@ -179,10 +177,10 @@ k_conv_tc(const __grid_constant__ CUtensorMap in_map, const unsigned char* __res
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem + SmemLayout::BAR);
     uint64_t* full = bars;
     uint64_t* empty = bars + kRowSlots;
-    uint64_t* tfull = bars + 2 * kRowSlots;
-    uint64_t* tempty = tfull + kRing;
-    uint64_t* wbar = tempty + kRing;
-    uint64_t* mma_done = wbar + 1;  // drain of the MMAs on an abort
+    uint64_t* trow = bars + 2 * kRowSlots;  // [kSets]: the window's staged row has its MMAs done
+    uint64_t* tdrain = trow + kSets;        // [kSets]: the epilogue has read the window
+    uint64_t* wbar = tdrain + kSets;
+    uint64_t* mma_done = wbar + 1;  // every MMA issued has completed
     uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + SmemLayout::TSLOT);
     float* sBias = reinterpret_cast<float*>(smem + SmemLayout::BIAS);
     float* sOutW = reinterpret_cast<float*>(smem + SmemLayout::OUTW);
@@ -201,9 +199,9 @@ k_conv_tc(const __grid_constant__ CUtensorMap in_map, const unsigned char* __res
             mbar_init(&full[i], 1);
             mbar_init(&empty[i], 1);
         }
-        for (int b = 0; b < kRing; ++b) {
-            mbar_init(&tfull[b], 1);
-            mbar_init(&tempty[b], 4);
+        for (int b = 0; b < kSets; ++b) {
+            mbar_init(&trow[b], 1);
+            mbar_init(&tdrain[b], 4);
         }
         mbar_init(wbar, 1);
         mbar_init(mma_done, 1);
@@ -267,129 +265,163 @@ k_conv_tc(const __grid_constant__ CUtensorMap in_map, const unsigned char* __res
         if (!mbar_wait(wbar, 0)) flag_timeout(status);
     } else if (warp == 1 && lane == 0) {
         // ------------------------------------------------------------- MMA issuer
+        // Staged row jr (the CTA's count) writes window jr mod kSets, tap dy into columns
+        // 32 dy of it: row j of a run adds tap dy in [lo, hi] to output line t0 + j - dy.  Every
+        // row initialises what it writes, so no two MMAs in flight share accumulator columns;
+        // the epilogue adds a line's three partial products.  The rows inside a run take all
+        // three taps in one 128x96x16 MMA per (dz, dx, K step), issued as a branch-free
+        // sequence with constant offsets; only the two rows at each end of a run go tap by tap.
         bool ok = mbar_wait(wbar, 0);
         const uint32_t abase = smem_u32(sA);
         const uint64_t bdesc0 = umma_desc_sw64(smem_u32(sW));
-        int irow = 0, t0 = 0;  // staged rows and output lines of this CTA before the current run
-        static_assert((kRing & (kRing - 1)) == 0, "ring size is a power of two");
+        int jr = 0, slot = 0;          // staged rows of this CTA, ring slot of row jr
+        uint32_t slot_phase = 0;       // parity of the slot's current fill
         for (long long seg = r_begin; seg < r_end && ok;) {
             const long long col = seg / H;
             const long long seg_end = min(r_end, (col + 1) * H);
             const int n = (int)(seg_end - seg);
-            for (int j = 0; j < n + 2 && ok; ++j) {  // input rows y0 - 1 .. y0 + n
+            for (int j = 0; j < n + 2; ++j, ++jr) {  // input rows y0 - 1 .. y0 + n
                 const int lo = max(0, j - (n - 1)), hi = min(2, j);
-                if (j < n) {  // line t0 + j starts here: its ring slot must have been drained
-                    const int t = t0 + j;
-                    if (t >= kRing && !mbar_wait(&tempty[(-t) & (kRing - 1)], (uint32_t)((t / kRing - 1) & 1))) {
-                        ok = false;
-                        break;
-                    }
+                const int set = jr & (kSets - 1);
+                // the window was read by the epilogue after row jr - kSets
+                if (jr >= kSets && !mbar_wait(&tdrain[set], (uint32_t)(((jr >> 2) - 1) & 1))) {
+                    ok = false;
+                    break;
                 }
-                // the row's targets: all of [lo, hi], and for its first product the new line
-                // (dy = 0, initialised) apart from the others
-                const MmaRuns all = mma_runs(tmem, t0 + j, lo, hi);
-                const MmaRuns fresh = mma_runs(tmem, t0 + j, 0, 0);
-                const MmaRuns rest = mma_runs(tmem, t0 + j, 1, max(hi, 1));
-                const int jr = irow + j;
-                if (!mbar_wait(&full[jr % kRowSlots], (uint32_t)((jr / kRowSlots) & 1)) || *(volatile int*)&s_abort) {
+                if (!mbar_wait(&full[slot], slot_phase) || *(volatile int*)&s_abort) {
                     ok = false;
                     break;
                 }
                 tc_fence_after();
-                const uint64_t adesc0 = umma_desc_sw64(abase + (uint32_t)((jr % kRowSlots) * kSlotBytes));
+                const uint32_t win = tmem + (uint32_t)set * kSetCols;
+                const uint64_t adesc0 = umma_desc_sw64(abase + (uint32_t)(slot * kSlotBytes));
+                if (lo == 0 && hi == 2) {
 #pragma unroll
-                for (int g = 0; g < 9; ++g)
+                    for (int g = 0; g < 9; ++g)
 #pragma unroll
-                    for (int kk = 0; kk < 2; ++kk) {
-                        const int dz = g / 3, dx = g % 3;
-                        const uint64_t ad =
-                            adesc0 + (uint64_t)((uint32_t)(dz * kStageBytes + (7 + dx) * kRowBytes + kk * 32) >> 4);
-                        const uint64_t bd = bdesc0 + (uint64_t)((uint32_t)(g * kGroupBytes + kk * 32) >> 4);
-                        if (g == 0 && kk == 0 && lo == 0) {  // the first product of a new line initialises it
-                            umma_bf16(fresh.d0, ad, bd + fresh.boff0, fresh.idesc0, 0u);
-                            if (hi >= 1) {
-                                umma_bf16(rest.d0, ad, bd + rest.boff0, rest.idesc0, 1u);
-                                if (rest.two) umma_bf16(rest.d1, ad, bd + rest.boff1, rest.idesc1, 1u);
-                            }
-                        } else {
-                            umma_bf16(all.d0, ad, bd + all.boff0, all.idesc0, 1u);
-                            if (all.two) umma_bf16(all.d1, ad, bd + all.boff1, all.idesc1, 1u);
+                        for (int kk = 0; kk < 2; ++kk) {
+                            umma_bf16(win, adesc0 + a_step(g, kk), bdesc0 + b_step(g, kk), idesc_n(3 * kF),
+                                      (g | kk) != 0 ? 1u : 0u);
                         }
+                } else {
+                    for (int dy = lo; dy <= hi; ++dy) {
+                        const uint32_t d = win + (uint32_t)(dy * kF);
+                        const uint64_t bdy = bdesc0 + (uint64_t)((uint32_t)(dy * kF * kRowBytes) >> 4);
+#pragma unroll
+                        for (int g = 0; g < 9; ++g)
+#pragma unroll
+                            for (int kk = 0; kk < 2; ++kk) {
+                                umma_bf16(d, adesc0 + a_step(g, kk), bdy + b_step(g, kk), idesc_n(kF),
+                                          (g | kk) != 0 ? 1u : 0u);
+                            }
                     }
-                umma_commit(&empty[jr % kRowSlots]);  // the row is read by no later MMA
-                if (j >= 2) {  // line t0 + j - 2 has all its rows
-                    const int t = t0 + j - 2;
-                    umma_commit(&tfull[(-t) & (kRing - 1)]);
+                }
+                umma_commit(&empty[slot]);  // the row is read by no later MMA
+                umma_commit(&trow[set]);    // the window's partial products are ready
+                if (++slot == kRowSlots) {
+                    slot = 0;
+                    slot_phase ^= 1u;
                 }
             }
-            irow += n + 2;
-            t0 += n;
             seg = seg_end;
         }
         if (!ok) {
             flag_timeout(status);
             s_abort = 1;
-            // wait for the MMAs already issued before tensor memory is released
-            umma_commit(mma_done);
-            if (!mbar_wait(mma_done, 0)) flag_timeout(status);
         }
+        // every MMA issued has completed before tensor memory is released (on the normal path the
+        // epilogue has already seen them all; after an abort it may not have)
+        umma_commit(mma_done);
+        if (!mbar_wait(mma_done, 0)) flag_timeout(status);
     } else if (warp >= 2) {
         // ------------------------------------------------------------- epilogue
+        // After staged row j of a run its window holds the tap-0 product of line t0 + j, the
+        // tap-1 product of line t0 + j - 1 and the tap-2 product of line t0 + j - 2, which is
+        // then complete.  The two open lines' running sums stay in registers (sn: the newest).
         const int q = warp & 3;  // tensor-memory lane quarter this warp may access
-        int t = 0;
-        bool run = true;
-        for (long long line = r_begin; line < r_end && run; ++line, ++t) {
-            const int b = (-t) & (kRing - 1);  // ring slot of line t
-            bool ok = true;
-            if (lane == 0) ok = mbar_wait(&tfull[b], (uint32_t)((t / kRing) & 1)) && !*(volatile int*)&s_abort;
-            ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
-            if (!ok) {
-                if (lane == 0) {
-                    flag_timeout(status);
-                    s_abort = 1;
-                }
-                run = false;
-                break;
-            }
-            tc_fence_after();
-            float acc[32];
-            tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(b * kF), acc);
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&tempty[b]);
-            const long long col = line / H;
-            const int y = (int)(line % H);
-            const int tx = (int)(col % tiles_x), z = (int)(col / tiles_x);
-            const int x = tx * kTileM + 32 * q + lane;
-            if (x >= W) continue;
+        const uint32_t lanes = (uint32_t)(32 * q) << 16;
+        float sn[32], sm[32];
 #pragma unroll
-            for (int c = 0; c < kF; ++c) acc[c] = fmaxf(acc[c] + sBias[c], 0.f);
-            if constexpr (FINAL) {
-                float4 r;
-                r.x = sOutB[0]; r.y = sOutB[1]; r.z = sOutB[2]; r.w = sOutB[3];
+        for (int c = 0; c < kF; ++c) sn[c] = sm[c] = 0.f;
+        int irow = 0;
+        bool run = true;
+        for (long long seg = r_begin; seg < r_end && run;) {
+            const long long col = seg / H;
+            const int y0 = (int)(seg % H);
+            const long long seg_end = min(r_end, (col + 1) * H);
+            const int n = (int)(seg_end - seg);
+            const int px = (int)(col % tiles_x), z = (int)(col / tiles_x);
+            for (int j = 0; j < n + 2; ++j) {
+                const int jr = irow + j, set = jr % kSets;
+                const int lo = max(0, j - (n - 1)), hi = min(2, j);
+                bool ok = true;
+                if (lane == 0)
+                    ok = mbar_wait(&trow[set], (uint32_t)((jr / kSets) & 1)) && !*(volatile int*)&s_abort;
+                ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+                if (!ok) {
+                    if (lane == 0) {
+                        flag_timeout(status);
+                        s_abort = 1;
+                    }
+                    run = false;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t win = tmem + lanes + (uint32_t)set * kSetCols;
+                uint32_t r0[32], r1[32], r2[32];
+                tmem_ld32_async(win, r0);
+                tmem_ld32_async(win + kF, r1);
+                tmem_ld32_async(win + 2 * kF, r2);
+                tmem_wait_ld();
+                tmem_regs_ready(r0);
+                tmem_regs_ready(r1);
+                tmem_regs_ready(r2);
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&tdrain[set]);
+                const bool fin = hi == 2;  // line t0 + j - 2 completes
+                float acc[32];
 #pragma unroll
                 for (int c = 0; c < kF; ++c) {
-                    r.x = fmaf(sOutW[0 * kF + c], acc[c], r.x);
-                    r.y = fmaf(sOutW[1 * kF + c], acc[c], r.y);
-                    r.z = fmaf(sOutW[2 * kF + c], acc[c], r.z);
-                    r.w = fmaf(sOutW[3 * kF + c], acc[c], r.w);
+                    acc[c] = __uint_as_float(r2[c]) + sm[c];
+                    if (lo <= 1 && hi >= 1) sm[c] = sn[c] + __uint_as_float(r1[c]);
+                    if (lo == 0) sn[c] = __uint_as_float(r0[c]);
                 }
-                *reinterpret_cast<float4*>(out_res + (((size_t)z * H + y) * W + x) * 4) = r;
-            } else {
+                if (!fin) continue;
+                const int y = y0 + j - 2;
+                const int x = px * kTileM + 32 * q + lane;
+                if (x >= W) continue;
 #pragma unroll
-                for (int ch = 0; ch < 4; ++ch) {
-                    uint4 pk;
-                    __nv_bfloat162 p0 = __floats2bfloat162_rn(acc[ch * 8 + 0], acc[ch * 8 + 1]);
-                    __nv_bfloat162 p1 = __floats2bfloat162_rn(acc[ch * 8 + 2], acc[ch * 8 + 3]);
-                    __nv_bfloat162 p2 = __floats2bfloat162_rn(acc[ch * 8 + 4], acc[ch * 8 + 5]);
-                    __nv_bfloat162 p3 = __floats2bfloat162_rn(acc[ch * 8 + 6], acc[ch * 8 + 7]);
-                    pk.x = *reinterpret_cast<uint32_t*>(&p0);
-                    pk.y = *reinterpret_cast<uint32_t*>(&p1);
-                    pk.z = *reinterpret_cast<uint32_t*>(&p2);
-                    pk.w = *reinterpret_cast<uint32_t*>(&p3);
-                    *reinterpret_cast<uint4*>(out_act + (((size_t)z * H + y) * W + x) * kF + ch * 8) = pk;
+                for (int c = 0; c < kF; ++c) acc[c] = fmaxf(acc[c] + sBias[c], 0.f);
+                if constexpr (FINAL) {
+                    float4 r;
+                    r.x = sOutB[0]; r.y = sOutB[1]; r.z = sOutB[2]; r.w = sOutB[3];
+#pragma unroll
+                    for (int c = 0; c < kF; ++c) {
+                        r.x = fmaf(sOutW[0 * kF + c], acc[c], r.x);
+                        r.y = fmaf(sOutW[1 * kF + c], acc[c], r.y);
+                        r.z = fmaf(sOutW[2 * kF + c], acc[c], r.z);
+                        r.w = fmaf(sOutW[3 * kF + c], acc[c], r.w);
+                    }
+                    *reinterpret_cast<float4*>(out_res + (((size_t)z * H + y) * W + x) * 4) = r;
+                } else {
+#pragma unroll
+                    for (int ch = 0; ch < 4; ++ch) {
+                        uint4 pk;
+                        __nv_bfloat162 p0 = __floats2bfloat162_rn(acc[ch * 8 + 0], acc[ch * 8 + 1]);
+                        __nv_bfloat162 p1 = __floats2bfloat162_rn(acc[ch * 8 + 2], acc[ch * 8 + 3]);
+                        __nv_bfloat162 p2 = __floats2bfloat162_rn(acc[ch * 8 + 4], acc[ch * 8 + 5]);
+                        __nv_bfloat162 p3 = __floats2bfloat162_rn(acc[ch * 8 + 6], acc[ch * 8 + 7]);
+                        pk.x = *reinterpret_cast<uint32_t*>(&p0);
+                        pk.y = *reinterpret_cast<uint32_t*>(&p1);
+                        pk.z = *reinterpret_cast<uint32_t*>(&p2);
+                        pk.w = *reinterpret_cast<uint32_t*>(&p3);
+                        *reinterpret_cast<uint4*>(out_act + (((size_t)z * H + y) * W + x) * kF + ch * 8) = pk;
+                    }
                 }
             }
+            irow += n + 2;
+            seg = seg_end;
         }
     }
     __syncwarp();  // the single-lane roles rejoin their warps
@@ -428,10 +460,10 @@ __global__ void k_pack_input(const float* __restrict__ V, int C, int K, int H, i
 // Batch-norm folding and packing of one block: w [32][cin][3][3][3] FP32 ->
 // [9 (dz, dx)][3 dy x 32 out][32 in] BF16, 64-byte swizzled (inputs >= cin zero), and the
 // folded bias.
-__global__ void k_prepare_block(const float* __restrict__ w, const float* __restrict__ b, const float* __restrict__ gamma,
-                                const float* __restrict__ beta, const float* __restrict__ mean,
-                                const float* __restrict__ var, float eps, int cin, __nv_bfloat16* __restrict__ wp,
-                                float* __restrict__ bias) {
+__global__ void k_prepare_block(const float* __restrict__ w, const float* __restrict__ b,
+                                const float* __restrict__ gamma, const float* __restrict__ beta,
+                                const float* __restrict__ mean, const float* __restrict__ var, float eps, int cin,
+                                __nv_bfloat16* __restrict__ wp, float* __restrict__ bias) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;  // over 27 * 32 * 32
     if (i < kF) {
         const float s = gamma[i] / sqrtf(var[i] + eps);

@@ -367,6 +367,13 @@ def lgd_conv_flops(k: int, h: int, w: int) -> int:
     return 2 * k * h * w * 27 * 32 * 32
 
 
+def lgd_net_flops(k: int, h: int, w: int, c_in: int) -> int:
+    """Algorithmic FLOPs of the whole network over k x h x w voxels: the first 3x3x3 block from
+    the volume's c_in channels, four 32 -> 32 blocks and the 1x1x1 layer to 4 channels."""
+    vox = k * h * w
+    return 2 * vox * 27 * 32 * c_in + 4 * lgd_conv_flops(k, h, w) + 2 * vox * 32 * 4
+
+
 def run_stage(args, world, rank, local):
     """Timed steps of the gradient volume (--stage volume) or the learned refinement (--stage lgd)."""
     import torch
@@ -446,7 +453,8 @@ def run_stage(args, world, rank, local):
     peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
         os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
     if args.stage == "lgd" and dom_name.startswith("lgd_conv"):
-        flops = args.steps * sum(4 * lgd_conv_flops(k, sc.H >> l, sc.W >> l) for l in sched)
+        # one launch runs the whole network of a level
+        flops = args.steps * sum(lgd_net_flops(k, sc.H >> l, sc.W >> l, 4 * len(sc.src) + 4) for l in sched)
         achieved = flops / (dom_ms / 1e3) / 1e12
         peak, src = (peaks["bf16_tflops"], "measured (burst)") if "bf16_tflops" in peaks else (1900.0, "fallback")
         roofline = {"bound": "tensor", "kernel": dom_name, "achieved": round(achieved, 1), "peak": peak,

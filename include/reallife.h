@@ -220,14 +220,17 @@ size_t reallife_lgd_net_bytes(void);
  * written asynchronously on `stream`.  RL_EINVAL for NULL parameters or c_in outside [1, 32]. */
 rl_status reallife_lgd_prepare(const rl_lgd_params* p, void* net, cudaStream_t stream);
 
-/* Workspace of reallife_lgd_forward: two BF16 activation volumes of k x h x w x 32. */
+/* Workspace of reallife_lgd_forward: two BF16 activation volumes of k x h x w x 32 and the
+ * network's grid-barrier counter. */
 size_t reallife_lgd_workspace_bytes(int k, int h, int w);
 
 /* N_w(V): V device [C][k][h][w] FP32 (C <= 32; e.g. the volume of reallife_gradient_volume),
  * residual device [k][h][w][4] FP32 (16-byte aligned, overwritten).  The input is rounded to
  * BF16, every block accumulates in FP32 on the tensor cores and stores BF16 activations; the
  * last block's output feeds the 1x1x1 layer in FP32.  ws: device, 256-byte aligned, at least
- * reallife_lgd_workspace_bytes(k, h, w) bytes (RL_ENOMEM when smaller). */
+ * reallife_lgd_workspace_bytes(k, h, w) bytes (RL_ENOMEM when smaller); calls that run at the
+ * same time need separate workspaces.  The five blocks run in one cooperative launch (one CTA
+ * per SM at most); RL_ECUDA when the device cannot make its CTAs resident together. */
 rl_status reallife_lgd_forward(const void* net, const float* V, int C, int k, int h, int w, float* residual,
                                void* ws, size_t ws_bytes, cudaStream_t stream);
 

@@ -27,6 +27,13 @@
 // lines: bias, ReLU, BF16 rounding and the store of the next layer's activations; after the
 // last block they also apply the 1x1x1 layer and store the FP32 residual [z][y][x][4].
 //
+// All five blocks run in one cooperative launch over the same CTAs.  Tensor memory, barriers
+// and the 1x1x1 layer are set up once, and the barriers' phases carry from block to block.
+// Between blocks each CTA waits for its own MMAs, starts copying the next block's weights, and
+// then meets the others at a grid-wide barrier (a counter in the workspace, bounded wait).
+// Past the barrier a proxy fence orders the other CTAs' stored activations before this CTA's
+// tensor copies of them.
+//
 // Every mbarrier wait is bounded; a wait that gives up sets RL_DEVFLAG_TIMEOUT, the roles
 // stop, the producer waits (bounded) for its copies in flight and the MMA lane for its MMAs,
 // and tensor memory is freed before the CTA exits.
@@ -48,6 +55,7 @@ constexpr int kGroupRows = 3 * kF;               // the dy-stacked weights of on
 constexpr int kGroupBytes = kGroupRows * kRowBytes;  // [96][32] BF16, 64-byte swizzled
 constexpr int kWBytes = 9 * kGroupBytes;         // 55296
 constexpr int kThreads = 192;
+constexpr int kBlocks = 5;                       // 3x3x3 blocks of the network
 constexpr int kSets = 4;                         // accumulator windows, taken by staged rows in turn
 constexpr uint32_t kSetCols = 128;               // one window: tap dy in columns 32 dy .. 32 dy + 31
 constexpr uint32_t kTmemCols = kSets * kSetCols;  // 512: all of it (one CTA per SM)
@@ -164,11 +172,21 @@ __device__ __forceinline__ void tmem_regs_ready(uint32_t (&r)[32]) {
 
 __device__ __forceinline__ void flag_timeout(unsigned int* status) { atomicOr(status, RL_DEVFLAG_TIMEOUT); }
 
-template <bool FINAL>
+__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// The whole network in one cooperative launch: the five 3x3x3 blocks run in turn over the
+// same persistent CTAs (block l reads activations l & 1 and writes the other buffer; the
+// last block writes the residual), separated by a grid-wide barrier on *grid_bar (zero at
+// launch), so that every line of block l is stored before any CTA copies it for block l + 1.
 __global__ void __launch_bounds__(kThreads, 1)
-k_conv_tc(const __grid_constant__ CUtensorMap in_map, const unsigned char* __restrict__ net, int layer, int K, int H,
-          int W, __nv_bfloat16* __restrict__ out_act, float* __restrict__ out_res,
-          unsigned int* __restrict__ status) {
+k_conv_net(const __grid_constant__ CUtensorMap map0, const __grid_constant__ CUtensorMap map1,
+           const unsigned char* __restrict__ net, int K, int H, int W, __nv_bfloat16* __restrict__ act0,
+           __nv_bfloat16* __restrict__ act1, float* __restrict__ out_res, unsigned int* __restrict__ grid_bar,
+           unsigned int* __restrict__ status) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     // the swizzled operands assume 1024-byte aligned atoms: align the base (1 KB of slack allocated)
     unsigned char* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
@@ -179,8 +197,8 @@ k_conv_tc(const __grid_constant__ CUtensorMap in_map, const unsigned char* __res
     uint64_t* empty = bars + kRowSlots;
     uint64_t* trow = bars + 2 * kRowSlots;  // [kSets]: the window's staged row has its MMAs done
     uint64_t* tdrain = trow + kSets;        // [kSets]: the epilogue has read the window
-    uint64_t* wbar = tdrain + kSets;
-    uint64_t* mma_done = wbar + 1;  // every MMA issued has completed
+    uint64_t* wbar = tdrain + kSets;        // a block's weights have landed (one phase a block)
+    uint64_t* mma_done = wbar + 1;          // every MMA of a block has completed (one phase a block)
     uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + SmemLayout::TSLOT);
     float* sBias = reinterpret_cast<float*>(smem + SmemLayout::BIAS);
     float* sOutW = reinterpret_cast<float*>(smem + SmemLayout::OUTW);
@@ -189,10 +207,10 @@ k_conv_tc(const __grid_constant__ CUtensorMap in_map, const unsigned char* __res
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int tiles_x = (W + kTileM - 1) / kTileM;
-    // this CTA's output lines: [r_begin, r_end) of the (z, x-tile, y) order
+    // this CTA's output lines: [r_begin, r_end) of the (z, x-tile, y) order, the same in every block
     const long long R = (long long)K * tiles_x * H;
     const long long r_begin = R * blockIdx.x / gridDim.x, r_end = R * (blockIdx.x + 1) / gridDim.x;
-    const float* bias_g = reinterpret_cast<const float*>(net + kNetBias) + layer * kF;
+    const float* bias_g = reinterpret_cast<const float*>(net + kNetBias);
 
     if (threadIdx.x == 0) {
         for (int i = 0; i < kRowSlots; ++i) {
@@ -209,8 +227,8 @@ k_conv_tc(const __grid_constant__ CUtensorMap in_map, const unsigned char* __res
         s_abort = 0;
     }
     if (threadIdx.x < kF) sBias[threadIdx.x] = bias_g[threadIdx.x];
-    if (FINAL && threadIdx.x < 4 * kF) sOutW[threadIdx.x] = reinterpret_cast<const float*>(net + kNetOutW)[threadIdx.x];
-    if (FINAL && threadIdx.x < 4) sOutB[threadIdx.x] = reinterpret_cast<const float*>(net + kNetOutB)[threadIdx.x];
+    if (threadIdx.x < 4 * kF) sOutW[threadIdx.x] = reinterpret_cast<const float*>(net + kNetOutW)[threadIdx.x];
+    if (threadIdx.x < 4) sOutB[threadIdx.x] = reinterpret_cast<const float*>(net + kNetOutB)[threadIdx.x];
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
                      "r"(kTmemCols)
@@ -221,210 +239,262 @@ k_conv_tc(const __grid_constant__ CUtensorMap in_map, const unsigned char* __res
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tslot;
-
-    if (warp == 0 && lane == 0) {
-        // ------------------------------------------------------------- producer
+    if (threadIdx.x == 0) {  // block 0's weights
         mbar_expect_tx(wbar, kWBytes);
-        bulk_load(sW, net + kNetW + (size_t)layer * kWBytes, kWBytes, wbar);
-        int irow = 0;  // input rows staged by this CTA
-        bool ok = true;
-        for (long long seg = r_begin; seg < r_end && ok;) {
-            const long long col = seg / H;
-            const int y0 = (int)(seg % H);
-            const long long seg_end = min(r_end, (col + 1) * H);
-            const int n = (int)(seg_end - seg);
-            const int tx = (int)(col % tiles_x), z = (int)(col / tiles_x);
-            for (int r = y0 - 1; r <= y0 + n && ok; ++r, ++irow) {  // input rows of outputs y0 .. y0+n-1
-                const int slot = irow % kRowSlots, round = irow / kRowSlots;
-                if (round > 0 && !mbar_wait(&empty[slot], (uint32_t)((round - 1) & 1))) {
-                    ok = false;
-                    break;
+        bulk_load(sW, net + kNetW, kWBytes, wbar);
+    }
+
+    // role state carried from block to block: staged rows and ring slots keep counting, so
+    // every barrier's phases stay in step across the blocks
+    int p_irow = 0;                      // producer: input rows staged
+    int m_jr = 0, m_slot = 0;            // MMA lane: staged rows, ring slot of the next row
+    uint32_t m_slot_phase = 0;
+    int e_irow = 0;                      // epilogue: staged rows drained
+    float sn[32], sm[32];                // epilogue: running sums of the two open lines
+#pragma unroll
+    for (int c = 0; c < kF; ++c) sn[c] = sm[c] = 0.f;
+
+    for (int layer = 0; layer < kBlocks; ++layer) {
+        const CUtensorMap* in_map = (layer & 1) ? &map1 : &map0;
+        __nv_bfloat16* out_act = (layer & 1) ? act0 : act1;
+        const bool last_block = layer == kBlocks - 1;
+        if (warp == 0 && lane == 0) {
+            // ------------------------------------------------------------- producer
+            int& irow = p_irow;
+            bool ok = true;
+            for (long long seg = r_begin; seg < r_end && ok;) {
+                const long long col = seg / H;
+                const int y0 = (int)(seg % H);
+                const long long seg_end = min(r_end, (col + 1) * H);
+                const int n = (int)(seg_end - seg);
+                const int tx = (int)(col % tiles_x), z = (int)(col / tiles_x);
+                for (int r = y0 - 1; r <= y0 + n && ok; ++r, ++irow) {  // input rows of outputs y0 .. y0+n-1
+                    const int slot = irow % kRowSlots, round = irow / kRowSlots;
+                    if (round > 0 && !mbar_wait(&empty[slot], (uint32_t)((round - 1) & 1))) {
+                        ok = false;
+                        break;
+                    }
+                    if (*(volatile int*)&s_abort) {
+                        ok = false;
+                        break;
+                    }
+                    mbar_expect_tx(&full[slot], kSlotBytes);
+                    unsigned char* dst = sA + slot * kSlotBytes;
+                    for (int dz = 0; dz < 3; ++dz)
+                        tma_load_4d(dst + dz * kStageBytes, in_map, &full[slot], 0, tx * kTileM - 8, r, z + dz - 1);
                 }
-                if (*(volatile int*)&s_abort) {
-                    ok = false;
-                    break;
-                }
-                mbar_expect_tx(&full[slot], kSlotBytes);
-                unsigned char* dst = sA + slot * kSlotBytes;
-                for (int dz = 0; dz < 3; ++dz)
-                    tma_load_4d(dst + dz * kStageBytes, &in_map, &full[slot], 0, tx * kTileM - 8, r, z + dz - 1);
+                seg = seg_end;
             }
-            seg = seg_end;
-        }
-        if (!ok) {
-            flag_timeout(status);
-            s_abort = 1;
-        }
-        // copies in flight: the last row of every slot must have landed before exit; on the
-        // normal path also its release by the MMAs (the tensor core's arrival on empty[slot])
-        for (int slot = 0; slot < kRowSlots && slot < irow; ++slot) {
-            const int last = irow - 1 - ((irow - 1 - slot) % kRowSlots);
-            if (!mbar_wait(&full[slot], (uint32_t)((last / kRowSlots) & 1))) flag_timeout(status);
-            if (ok && !mbar_wait(&empty[slot], (uint32_t)((last / kRowSlots) & 1))) flag_timeout(status);
-        }
-        if (!mbar_wait(wbar, 0)) flag_timeout(status);
-    } else if (warp == 1 && lane == 0) {
-        // ------------------------------------------------------------- MMA issuer
-        // Staged row jr (the CTA's count) writes window jr mod kSets, tap dy into columns
-        // 32 dy of it: row j of a run adds tap dy in [lo, hi] to output line t0 + j - dy.  Every
-        // row initialises what it writes, so no two MMAs in flight share accumulator columns;
-        // the epilogue adds a line's three partial products.  The rows inside a run take all
-        // three taps in one 128x96x16 MMA per (dz, dx, K step), issued as a branch-free
-        // sequence with constant offsets; only the two rows at each end of a run go tap by tap.
-        bool ok = mbar_wait(wbar, 0);
-        const uint32_t abase = smem_u32(sA);
-        const uint64_t bdesc0 = umma_desc_sw64(smem_u32(sW));
-        int jr = 0, slot = 0;          // staged rows of this CTA, ring slot of row jr
-        uint32_t slot_phase = 0;       // parity of the slot's current fill
-        for (long long seg = r_begin; seg < r_end && ok;) {
-            const long long col = seg / H;
-            const long long seg_end = min(r_end, (col + 1) * H);
-            const int n = (int)(seg_end - seg);
-            for (int j = 0; j < n + 2; ++j, ++jr) {  // input rows y0 - 1 .. y0 + n
-                const int lo = max(0, j - (n - 1)), hi = min(2, j);
-                const int set = jr & (kSets - 1);
-                // the window was read by the epilogue after row jr - kSets
-                if (jr >= kSets && !mbar_wait(&tdrain[set], (uint32_t)(((jr >> 2) - 1) & 1))) {
-                    ok = false;
-                    break;
-                }
-                if (!mbar_wait(&full[slot], slot_phase) || *(volatile int*)&s_abort) {
-                    ok = false;
-                    break;
-                }
-                tc_fence_after();
-                const uint32_t win = tmem + (uint32_t)set * kSetCols;
-                const uint64_t adesc0 = umma_desc_sw64(abase + (uint32_t)(slot * kSlotBytes));
-                if (lo == 0 && hi == 2) {
-#pragma unroll
-                    for (int g = 0; g < 9; ++g)
-#pragma unroll
-                        for (int kk = 0; kk < 2; ++kk) {
-                            umma_bf16(win, adesc0 + a_step(g, kk), bdesc0 + b_step(g, kk), idesc_n(3 * kF),
-                                      (g | kk) != 0 ? 1u : 0u);
-                        }
-                } else {
-                    for (int dy = lo; dy <= hi; ++dy) {
-                        const uint32_t d = win + (uint32_t)(dy * kF);
-                        const uint64_t bdy = bdesc0 + (uint64_t)((uint32_t)(dy * kF * kRowBytes) >> 4);
+            if (!ok) {
+                flag_timeout(status);
+                s_abort = 1;
+            }
+            // copies in flight: the last row of every slot must have landed before exit; on the
+            // normal path also its release by the MMAs (the tensor core's arrival on empty[slot])
+            for (int slot = 0; slot < kRowSlots && slot < irow; ++slot) {
+                const int last = irow - 1 - ((irow - 1 - slot) % kRowSlots);
+                if (!mbar_wait(&full[slot], (uint32_t)((last / kRowSlots) & 1))) flag_timeout(status);
+                if (ok && !mbar_wait(&empty[slot], (uint32_t)((last / kRowSlots) & 1))) flag_timeout(status);
+            }
+            // block 0's weight copy has landed (later blocks' copies are waited for at the boundary)
+            if (layer == 0 && !mbar_wait(wbar, 0)) flag_timeout(status);
+        } else if (warp == 1 && lane == 0) {
+            // ------------------------------------------------------------- MMA issuer
+            // Staged row jr (the CTA's count) writes window jr mod kSets, tap dy into columns
+            // 32 dy of it: row j of a run adds tap dy in [lo, hi] to output line t0 + j - dy.  Every
+            // row initialises what it writes, so no two MMAs in flight share accumulator columns;
+            // the epilogue adds a line's three partial products.  The rows inside a run take all
+            // three taps in one 128x96x16 MMA per (dz, dx, K step), issued as a branch-free
+            // sequence with constant offsets; only the two rows at each end of a run go tap by tap.
+            bool ok = mbar_wait(wbar, (uint32_t)(layer & 1));
+            const uint32_t abase = smem_u32(sA);
+            const uint64_t bdesc0 = umma_desc_sw64(smem_u32(sW));
+            int& jr = m_jr;
+            int& slot = m_slot;
+            uint32_t& slot_phase = m_slot_phase;
+            for (long long seg = r_begin; seg < r_end && ok;) {
+                const long long col = seg / H;
+                const long long seg_end = min(r_end, (col + 1) * H);
+                const int n = (int)(seg_end - seg);
+                for (int j = 0; j < n + 2; ++j, ++jr) {  // input rows y0 - 1 .. y0 + n
+                    const int lo = max(0, j - (n - 1)), hi = min(2, j);
+                    const int set = jr & (kSets - 1);
+                    // the window was read by the epilogue after row jr - kSets
+                    if (jr >= kSets && !mbar_wait(&tdrain[set], (uint32_t)(((jr >> 2) - 1) & 1))) {
+                        ok = false;
+                        break;
+                    }
+                    if (!mbar_wait(&full[slot], slot_phase) || *(volatile int*)&s_abort) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t win = tmem + (uint32_t)set * kSetCols;
+                    const uint64_t adesc0 = umma_desc_sw64(abase + (uint32_t)(slot * kSlotBytes));
+                    if (lo == 0 && hi == 2) {
 #pragma unroll
                         for (int g = 0; g < 9; ++g)
 #pragma unroll
                             for (int kk = 0; kk < 2; ++kk) {
-                                umma_bf16(d, adesc0 + a_step(g, kk), bdy + b_step(g, kk), idesc_n(kF),
+                                umma_bf16(win, adesc0 + a_step(g, kk), bdesc0 + b_step(g, kk), idesc_n(3 * kF),
                                           (g | kk) != 0 ? 1u : 0u);
                             }
+                    } else {
+                        for (int dy = lo; dy <= hi; ++dy) {
+                            const uint32_t d = win + (uint32_t)(dy * kF);
+                            const uint64_t bdy = bdesc0 + (uint64_t)((uint32_t)(dy * kF * kRowBytes) >> 4);
+#pragma unroll
+                            for (int g = 0; g < 9; ++g)
+#pragma unroll
+                                for (int kk = 0; kk < 2; ++kk) {
+                                    umma_bf16(d, adesc0 + a_step(g, kk), bdy + b_step(g, kk), idesc_n(kF),
+                                              (g | kk) != 0 ? 1u : 0u);
+                                }
+                        }
+                    }
+                    umma_commit(&empty[slot]);  // the row is read by no later MMA
+                    umma_commit(&trow[set]);    // the window's partial products are ready
+                    if (++slot == kRowSlots) {
+                        slot = 0;
+                        slot_phase ^= 1u;
                     }
                 }
-                umma_commit(&empty[slot]);  // the row is read by no later MMA
-                umma_commit(&trow[set]);    // the window's partial products are ready
-                if (++slot == kRowSlots) {
-                    slot = 0;
-                    slot_phase ^= 1u;
-                }
+                seg = seg_end;
             }
-            seg = seg_end;
-        }
-        if (!ok) {
-            flag_timeout(status);
-            s_abort = 1;
-        }
-        // every MMA issued has completed before tensor memory is released (on the normal path the
-        // epilogue has already seen them all; after an abort it may not have)
-        umma_commit(mma_done);
-        if (!mbar_wait(mma_done, 0)) flag_timeout(status);
-    } else if (warp >= 2) {
-        // ------------------------------------------------------------- epilogue
-        // After staged row j of a run its window holds the tap-0 product of line t0 + j, the
-        // tap-1 product of line t0 + j - 1 and the tap-2 product of line t0 + j - 2, which is
-        // then complete.  The two open lines' running sums stay in registers (sn: the newest).
-        const int q = warp & 3;  // tensor-memory lane quarter this warp may access
-        const uint32_t lanes = (uint32_t)(32 * q) << 16;
-        float sn[32], sm[32];
-#pragma unroll
-        for (int c = 0; c < kF; ++c) sn[c] = sm[c] = 0.f;
-        int irow = 0;
-        bool run = true;
-        for (long long seg = r_begin; seg < r_end && run;) {
-            const long long col = seg / H;
-            const int y0 = (int)(seg % H);
-            const long long seg_end = min(r_end, (col + 1) * H);
-            const int n = (int)(seg_end - seg);
-            const int px = (int)(col % tiles_x), z = (int)(col / tiles_x);
-            for (int j = 0; j < n + 2; ++j) {
-                const int jr = irow + j, set = jr % kSets;
-                const int lo = max(0, j - (n - 1)), hi = min(2, j);
-                bool ok = true;
-                if (lane == 0)
-                    ok = mbar_wait(&trow[set], (uint32_t)((jr / kSets) & 1)) && !*(volatile int*)&s_abort;
-                ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
-                if (!ok) {
-                    if (lane == 0) {
-                        flag_timeout(status);
-                        s_abort = 1;
+            if (!ok) {
+                flag_timeout(status);
+                s_abort = 1;
+            }
+            // every MMA of the block has completed before its weights are replaced or tensor memory
+            // is released (on the normal path the epilogue has already seen them all)
+            umma_commit(mma_done);
+            if (!mbar_wait(mma_done, (uint32_t)(layer & 1))) flag_timeout(status);
+        } else if (warp >= 2) {
+            // ------------------------------------------------------------- epilogue
+            // After staged row j of a run its window holds the tap-0 product of line t0 + j, the
+            // tap-1 product of line t0 + j - 1 and the tap-2 product of line t0 + j - 2, which is
+            // then complete.  The two open lines' running sums stay in registers (sn: the newest).
+            const int q = warp & 3;  // tensor-memory lane quarter this warp may access
+            const uint32_t lanes = (uint32_t)(32 * q) << 16;
+            int& irow = e_irow;
+            bool run = true;
+            for (long long seg = r_begin; seg < r_end && run;) {
+                const long long col = seg / H;
+                const int y0 = (int)(seg % H);
+                const long long seg_end = min(r_end, (col + 1) * H);
+                const int n = (int)(seg_end - seg);
+                const int px = (int)(col % tiles_x), z = (int)(col / tiles_x);
+                for (int j = 0; j < n + 2; ++j) {
+                    const int jr = irow + j, set = jr % kSets;
+                    const int lo = max(0, j - (n - 1)), hi = min(2, j);
+                    bool ok = true;
+                    if (lane == 0)
+                        ok = mbar_wait(&trow[set], (uint32_t)((jr / kSets) & 1)) && !*(volatile int*)&s_abort;
+                    ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+                    if (!ok) {
+                        if (lane == 0) {
+                            flag_timeout(status);
+                            s_abort = 1;
+                        }
+                        run = false;
+                        break;
                     }
-                    run = false;
-                    break;
-                }
-                tc_fence_after();
-                const uint32_t win = tmem + lanes + (uint32_t)set * kSetCols;
-                uint32_t r0[32], r1[32], r2[32];
-                tmem_ld32_async(win, r0);
-                tmem_ld32_async(win + kF, r1);
-                tmem_ld32_async(win + 2 * kF, r2);
-                tmem_wait_ld();
-                tmem_regs_ready(r0);
-                tmem_regs_ready(r1);
-                tmem_regs_ready(r2);
-                tc_fence_before();
-                __syncwarp();
-                if (lane == 0) mbar_arrive(&tdrain[set]);
-                const bool fin = hi == 2;  // line t0 + j - 2 completes
-                float acc[32];
-#pragma unroll
-                for (int c = 0; c < kF; ++c) {
-                    acc[c] = __uint_as_float(r2[c]) + sm[c];
-                    if (lo <= 1 && hi >= 1) sm[c] = sn[c] + __uint_as_float(r1[c]);
-                    if (lo == 0) sn[c] = __uint_as_float(r0[c]);
-                }
-                if (!fin) continue;
-                const int y = y0 + j - 2;
-                const int x = px * kTileM + 32 * q + lane;
-                if (x >= W) continue;
-#pragma unroll
-                for (int c = 0; c < kF; ++c) acc[c] = fmaxf(acc[c] + sBias[c], 0.f);
-                if constexpr (FINAL) {
-                    float4 r;
-                    r.x = sOutB[0]; r.y = sOutB[1]; r.z = sOutB[2]; r.w = sOutB[3];
+                    tc_fence_after();
+                    const uint32_t win = tmem + lanes + (uint32_t)set * kSetCols;
+                    uint32_t r0[32], r1[32], r2[32];
+                    tmem_ld32_async(win, r0);
+                    tmem_ld32_async(win + kF, r1);
+                    tmem_ld32_async(win + 2 * kF, r2);
+                    tmem_wait_ld();
+                    tmem_regs_ready(r0);
+                    tmem_regs_ready(r1);
+                    tmem_regs_ready(r2);
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&tdrain[set]);
+                    const bool fin = hi == 2;  // line t0 + j - 2 completes
+                    float acc[32];
 #pragma unroll
                     for (int c = 0; c < kF; ++c) {
-                        r.x = fmaf(sOutW[0 * kF + c], acc[c], r.x);
-                        r.y = fmaf(sOutW[1 * kF + c], acc[c], r.y);
-                        r.z = fmaf(sOutW[2 * kF + c], acc[c], r.z);
-                        r.w = fmaf(sOutW[3 * kF + c], acc[c], r.w);
+                        acc[c] = __uint_as_float(r2[c]) + sm[c];
+                        if (lo <= 1 && hi >= 1) sm[c] = sn[c] + __uint_as_float(r1[c]);
+                        if (lo == 0) sn[c] = __uint_as_float(r0[c]);
                     }
-                    *reinterpret_cast<float4*>(out_res + (((size_t)z * H + y) * W + x) * 4) = r;
-                } else {
+                    if (!fin) continue;
+                    const int y = y0 + j - 2;
+                    const int x = px * kTileM + 32 * q + lane;
+                    if (x >= W) continue;
 #pragma unroll
-                    for (int ch = 0; ch < 4; ++ch) {
-                        uint4 pk;
-                        __nv_bfloat162 p0 = __floats2bfloat162_rn(acc[ch * 8 + 0], acc[ch * 8 + 1]);
-                        __nv_bfloat162 p1 = __floats2bfloat162_rn(acc[ch * 8 + 2], acc[ch * 8 + 3]);
-                        __nv_bfloat162 p2 = __floats2bfloat162_rn(acc[ch * 8 + 4], acc[ch * 8 + 5]);
-                        __nv_bfloat162 p3 = __floats2bfloat162_rn(acc[ch * 8 + 6], acc[ch * 8 + 7]);
-                        pk.x = *reinterpret_cast<uint32_t*>(&p0);
-                        pk.y = *reinterpret_cast<uint32_t*>(&p1);
-                        pk.z = *reinterpret_cast<uint32_t*>(&p2);
-                        pk.w = *reinterpret_cast<uint32_t*>(&p3);
-                        *reinterpret_cast<uint4*>(out_act + (((size_t)z * H + y) * W + x) * kF + ch * 8) = pk;
+                    for (int c = 0; c < kF; ++c) acc[c] = fmaxf(acc[c] + sBias[c], 0.f);
+                    if (last_block) {
+                        float4 r;
+                        r.x = sOutB[0]; r.y = sOutB[1]; r.z = sOutB[2]; r.w = sOutB[3];
+#pragma unroll
+                        for (int c = 0; c < kF; ++c) {
+                            r.x = fmaf(sOutW[0 * kF + c], acc[c], r.x);
+                            r.y = fmaf(sOutW[1 * kF + c], acc[c], r.y);
+                            r.z = fmaf(sOutW[2 * kF + c], acc[c], r.z);
+                            r.w = fmaf(sOutW[3 * kF + c], acc[c], r.w);
+                        }
+                        *reinterpret_cast<float4*>(out_res + (((size_t)z * H + y) * W + x) * 4) = r;
+                    } else {
+#pragma unroll
+                        for (int ch = 0; ch < 4; ++ch) {
+                            uint4 pk;
+                            __nv_bfloat162 p0 = __floats2bfloat162_rn(acc[ch * 8 + 0], acc[ch * 8 + 1]);
+                            __nv_bfloat162 p1 = __floats2bfloat162_rn(acc[ch * 8 + 2], acc[ch * 8 + 3]);
+                            __nv_bfloat162 p2 = __floats2bfloat162_rn(acc[ch * 8 + 4], acc[ch * 8 + 5]);
+                            __nv_bfloat162 p3 = __floats2bfloat162_rn(acc[ch * 8 + 6], acc[ch * 8 + 7]);
+                            pk.x = *reinterpret_cast<uint32_t*>(&p0);
+                            pk.y = *reinterpret_cast<uint32_t*>(&p1);
+                            pk.z = *reinterpret_cast<uint32_t*>(&p2);
+                            pk.w = *reinterpret_cast<uint32_t*>(&p3);
+                            *reinterpret_cast<uint4*>(out_act + (((size_t)z * H + y) * W + x) * kF + ch * 8) = pk;
+                        }
                     }
                 }
+                irow += n + 2;
+                seg = seg_end;
             }
-            irow += n + 2;
-            seg = seg_end;
         }
+        __syncwarp();  // the single-lane roles rejoin their warps
+        tc_fence_before();
+        __syncthreads();
+        if (*(volatile int*)&s_abort || last_block) break;
+        // block boundary: the MMAs of this block have completed (the MMA lane waited for them),
+        // so the weights can be replaced; the epilogue has stored its lines
+        if (threadIdx.x == 0) {
+            mbar_expect_tx(wbar, kWBytes);
+            bulk_load(sW, net + kNetW + (size_t)(layer + 1) * kWBytes, kWBytes, wbar);
+            // grid barrier: this CTA's stores are made visible at GPU scope, then it waits until
+            // every CTA has arrived (bounded)
+            __threadfence();
+            atomicAdd(grid_bar, 1u);
+            const unsigned target = (unsigned)(layer + 1) * gridDim.x;
+            if (ld_acquire_gpu(grid_bar) < target) {
+                const long long t0 = clock64();
+                while (ld_acquire_gpu(grid_bar) < target) {
+                    if (clock64() - t0 > kWaitCycles) {
+                        flag_timeout(status);
+                        s_abort = 1;
+                        break;
+                    }
+                    __nanosleep(64);
+                }
+            }
+            // the next block's copies (async proxy) read what the generic stores wrote
+            asm volatile("fence.proxy.async.global;" ::: "memory");
+            // the weight copy is not left in flight if the CTA stops here
+            if (!mbar_wait(wbar, (uint32_t)((layer + 1) & 1))) {
+                flag_timeout(status);
+                s_abort = 1;
+            }
+        }
+        if (threadIdx.x < kF) sBias[threadIdx.x] = bias_g[(layer + 1) * kF + threadIdx.x];
+        __syncthreads();
+        if (*(volatile int*)&s_abort) break;
+        tc_fence_after();
     }
-    __syncwarp();  // the single-lane roles rejoin their warps
     tc_fence_before();
     __syncthreads();
     if (warp == 0) {
@@ -501,7 +571,7 @@ rl_status rl_lgd_prepare(const rl_lgd_params* p, void* net, cudaStream_t s) {
 size_t rl_lgd_act_bytes(int K, int H, int W) { return ((size_t)K * H * W * kF * 2 + 1023) & ~(size_t)1023; }
 
 rl_status rl_lgd_forward(const void* net, const float* V, int C, int K, int H, int W, float* residual, void* act0,
-                         void* act1, cudaStream_t s) {
+                         void* act1, unsigned* grid_bar, cudaStream_t s) {
     const long long n = (long long)K * H * W;
     {
         RLTraceScope ts("lgd_pack", s);
@@ -516,35 +586,34 @@ rl_status rl_lgd_forward(const void* net, const float* V, int C, int K, int H, i
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const long long lines = (long long)K * H * ((W + kTileM - 1) / kTileM);
+    // one CTA per SM at most: every CTA is resident, as the grid barrier between blocks needs
+    // (the cooperative launch fails rather than run a grid that cannot be)
     const unsigned grid = (unsigned)std::min<long long>(lines, sms > 0 ? sms : 1);
     const size_t smem = SmemLayout::TOTAL + 1024;
-    cudaFuncSetAttribute(k_conv_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    cudaFuncSetAttribute(k_conv_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(k_conv_net, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     unsigned int* status = rl_device_status_ptr();
     if (!status) return rl_fail(RL_ECUDA, "device status word unavailable");
-    void* acts[2] = {act0, act1};
-    for (int l = 0; l < 5; ++l) {
-        const int src = l & 1;
-        if (l < 4) {
-            RLTraceScope ts("lgd_conv_tc", s);
-            k_conv_tc<false><<<grid, kThreads, smem, s>>>(maps[src], (const unsigned char*)net, l, K, H, W,
-                                                          (__nv_bfloat16*)acts[src ^ 1], nullptr, status);
-        } else {
-            RLTraceScope ts("lgd_conv_tc_final", s);
-            k_conv_tc<true><<<grid, kThreads, smem, s>>>(maps[src], (const unsigned char*)net, l, K, H, W,
-                                                         nullptr, residual, status);
-        }
-        st = rl_check_launch("lgd_conv");
-        if (st) return st;
+    if (cudaMemsetAsync(grid_bar, 0, sizeof(unsigned), s) != cudaSuccess)
+        return rl_fail(RL_ECUDA, "lgd: grid barrier reset failed");
+    const unsigned char* netp = (const unsigned char*)net;
+    __nv_bfloat16* a0 = (__nv_bfloat16*)act0;
+    __nv_bfloat16* a1 = (__nv_bfloat16*)act1;
+    void* args[] = {(void*)&maps[0], (void*)&maps[1], (void*)&netp, (void*)&K, (void*)&H, (void*)&W,
+                    (void*)&a0, (void*)&a1, (void*)&residual, (void*)&grid_bar, (void*)&status};
+    {
+        RLTraceScope ts("lgd_conv_net", s);
+        const cudaError_t e = cudaLaunchCooperativeKernel((const void*)k_conv_net, dim3(grid), dim3(kThreads), args,
+                                                          smem, s);
+        if (e != cudaSuccess) return rl_fail(RL_ECUDA, "lgd: cooperative launch: %s", cudaGetErrorString(e));
     }
-    return RL_OK;
+    return rl_check_launch("lgd_conv");
 }
 
 // ------------------------------------------------------------------ C ABI
 
 namespace {
 struct LgdStepLayout {
-    size_t vol, V, res, S, act0, act1, total;
+    size_t vol, V, res, S, act0, act1, gbar, total;
 };
 
 size_t a256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -564,6 +633,8 @@ LgdStepLayout lgd_step_layout(int N, int D, int H, int W, int k, rl_dtype dt) {
     off += rl_lgd_act_bytes(k, H, W);
     L.act1 = off;
     off += rl_lgd_act_bytes(k, H, W);
+    L.gbar = off;  // the network's grid-barrier counter
+    off += 256;
     L.total = off;
     return L;
 }
@@ -584,7 +655,7 @@ extern "C" rl_status reallife_lgd_prepare(const rl_lgd_params* p, void* net, cud
 
 extern "C" size_t reallife_lgd_workspace_bytes(int k, int h, int w) {
     if (k < 1 || h < 1 || w < 1) return 0;
-    return 2 * rl_lgd_act_bytes(k, h, w);
+    return 2 * rl_lgd_act_bytes(k, h, w) + 256;  // two activation buffers, the grid-barrier counter
 }
 
 extern "C" rl_status reallife_lgd_forward(const void* net, const float* V, int C, int k, int h, int w,
@@ -597,7 +668,8 @@ extern "C" rl_status reallife_lgd_forward(const void* net, const float* V, int C
     const size_t need = reallife_lgd_workspace_bytes(k, h, w);
     if (ws_bytes < need) return rl_fail(RL_ENOMEM, "workspace %zu bytes < %zu needed", ws_bytes, need);
     char* b = (char*)ws;
-    return rl_lgd_forward(net, V, C, k, h, w, residual, b, b + rl_lgd_act_bytes(k, h, w), stream);
+    const size_t act = rl_lgd_act_bytes(k, h, w);
+    return rl_lgd_forward(net, V, C, k, h, w, residual, b, b + act, (unsigned*)(b + 2 * act), stream);
 }
 
 extern "C" size_t reallife_lgd_step_workspace_bytes(int N, int D, int H, int W, int k, rl_dtype dtype) {
@@ -623,7 +695,7 @@ extern "C" rl_status reallife_lgd_step(rl_mpi* m, const float* images, const rl_
                                             L.V - L.vol, stream);
     if (st) return st;
     const int h = m->H >> level, w = m->W >> level;
-    st = rl_lgd_forward(net, V, 4 * N + 4, k, h, w, res, b + L.act0, b + L.act1, stream);
+    st = rl_lgd_forward(net, V, 4 * N + 4, k, h, w, res, b + L.act0, b + L.act1, (unsigned*)(b + L.gbar), stream);
     if (st) return st;
     // M <- M + R(residual, S): the masked update with step -1 (and the level's upsampling)
     return rl_launch_update(m->data, m->dtype, m->D, m->H, m->W, level, S, res, k, -1.0f, clamp01, stream);

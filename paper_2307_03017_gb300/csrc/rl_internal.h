@@ -122,9 +122,10 @@ rl_status rl_launch_volume(const void* Ml, rl_dtype dt, int D, int h, int w, int
 
 // Learned update network (lgd.cu): packed parameter bytes, parameter packing, activation
 // buffer bytes and the forward pass (V [C][K][H][W] FP32 -> residual [K][H][W][4] FP32,
-// two activation buffers of rl_lgd_act_bytes each).
+// two activation buffers of rl_lgd_act_bytes each and a 4-byte grid-barrier counter that the
+// call resets on the stream).
 size_t rl_lgd_net_bytes();
 rl_status rl_lgd_prepare(const rl_lgd_params* p, void* net, cudaStream_t s);
 size_t rl_lgd_act_bytes(int K, int H, int W);
 rl_status rl_lgd_forward(const void* net, const float* V, int C, int K, int H, int W, float* residual, void* act0,
-                         void* act1, cudaStream_t s);
+                         void* act1, unsigned* grid_bar, cudaStream_t s);

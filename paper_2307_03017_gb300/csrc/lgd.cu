@@ -579,6 +579,11 @@ rl_status rl_lgd_forward(const void* net, const float* V, int C, int K, int H, i
     }
     rl_status st = rl_check_launch("lgd_pack");
     if (st) return st;
+    return rl_lgd_network(net, K, H, W, residual, act0, act1, grid_bar, s);
+}
+
+rl_status rl_lgd_network(const void* net, int K, int H, int W, float* residual, void* act0, void* act1,
+                         unsigned* grid_bar, cudaStream_t s) {
     CUtensorMap maps[2];
     if (!rl_encode_act_tmap(&maps[0], act0, K, H, W, kHalo) || !rl_encode_act_tmap(&maps[1], act1, K, H, W, kHalo))
         return rl_fail(RL_ECUDA, "lgd: activation tensor maps could not be encoded");
@@ -613,7 +618,7 @@ rl_status rl_lgd_forward(const void* net, const float* V, int C, int K, int H, i
 
 namespace {
 struct LgdStepLayout {
-    size_t vol, V, res, S, act0, act1, gbar, total;
+    size_t vol, res, S, act0, act1, gbar, total;
 };
 
 size_t a256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -623,8 +628,6 @@ LgdStepLayout lgd_step_layout(int N, int D, int H, int W, int k, rl_dtype dt) {
     size_t off = 0;
     L.vol = off;
     off += a256(reallife_gradient_volume_workspace_bytes(N, D, H, W, k, dt));
-    L.V = off;
-    off += a256((size_t)(4 * N + 4) * k * H * W * sizeof(float));
     L.res = off;
     off += a256((size_t)k * H * W * 4 * sizeof(float));
     L.S = off;
@@ -688,14 +691,14 @@ extern "C" rl_status reallife_lgd_step(rl_mpi* m, const float* images, const rl_
     if (ws_bytes < L.total) return rl_fail(RL_ENOMEM, "workspace %zu bytes < %zu needed", ws_bytes, L.total);
     char* b = (char*)ws;
     uint8_t* S = S_out ? S_out : (uint8_t*)(b + L.S);
-    float* V = (float*)(b + L.V);
     float* res = (float*)(b + L.res);
-    // V_s and S (validates the MPI, views, k, level and selection)
-    rl_status st = reallife_gradient_volume(m, images, src, N, k, level, selection, S, V, b + L.vol,
-                                            L.V - L.vol, stream);
+    // V_s and S (validates the MPI, views, k, level and selection), written as the network's
+    // BF16 channels-last input
+    rl_status st = rl_gradient_volume(m, images, src, N, k, level, selection, S, nullptr, b + L.act0, b + L.vol,
+                                      L.res - L.vol, stream);
     if (st) return st;
     const int h = m->H >> level, w = m->W >> level;
-    st = rl_lgd_forward(net, V, 4 * N + 4, k, h, w, res, b + L.act0, b + L.act1, (unsigned*)(b + L.gbar), stream);
+    st = rl_lgd_network(net, k, h, w, res, b + L.act0, b + L.act1, (unsigned*)(b + L.gbar), stream);
     if (st) return st;
     // M <- M + R(residual, S): the masked update with step -1 (and the level's upsampling)
     return rl_launch_update(m->data, m->dtype, m->D, m->H, m->W, level, S, res, k, -1.0f, clamp01, stream);

@@ -481,6 +481,12 @@ extern "C" size_t reallife_gradient_volume_workspace_bytes(int N, int D, int H, 
 extern "C" rl_status reallife_gradient_volume(const rl_mpi* m, const float* images, const rl_camera* src, int N,
                                               int k, int level, int selection, uint8_t* S_out, float* V, void* ws,
                                               size_t ws_bytes, cudaStream_t stream) {
+    return rl_gradient_volume(m, images, src, N, k, level, selection, S_out, V, nullptr, ws, ws_bytes, stream);
+}
+
+rl_status rl_gradient_volume(const rl_mpi* m, const float* images, const rl_camera* src, int N, int k, int level,
+                             int selection, uint8_t* S_out, float* V, void* act, void* ws, size_t ws_bytes,
+                             cudaStream_t stream) {
     rl_hsgd_params p;
     std::memset(&p, 0, sizeof(p));
     p.k = k;
@@ -490,7 +496,8 @@ extern "C" rl_status reallife_gradient_volume(const rl_mpi* m, const float* imag
     // the step's checks (MPI, k, selection, level, images, cameras); its workspace is not used
     rl_status st = check_hsgd(m, images, src, N, &p, level, ws, ~(size_t)0);
     if (st) return st;
-    if (!V || ((uintptr_t)V & 3) != 0) return rl_fail(RL_EINVAL, "V must be a non-NULL, 4-byte aligned device buffer");
+    if (act ? ((uintptr_t)act & 15) != 0 : (!V || ((uintptr_t)V & 3) != 0))
+        return rl_fail(RL_EINVAL, "V must be a non-NULL, 4-byte aligned device buffer");
     if (ws_bytes < need) return rl_fail(RL_ENOMEM, "workspace %zu bytes < %zu needed", ws_bytes, need);
     const VolLayout L = vol_layout(N, m->D, m->H, m->W, k, m->dtype);
     char* base = (char*)ws;
@@ -517,7 +524,7 @@ extern "C" rl_status reallife_gradient_volume(const rl_mpi* m, const float* imag
     if (st) return st;
     st = rl_launch_view_alpha(Ml, m->dtype, m->D, h, w, views, A, stream);
     if (st) return st;
-    return rl_launch_volume(Ml, m->dtype, m->D, h, w, level, S, k, A, images, iv, V, stream);
+    return rl_launch_volume(Ml, m->dtype, m->D, h, w, level, S, k, A, images, iv, V, stream, act);
 }
 
 extern "C" rl_status reallife_downsample_f32(const float* x, int P, int H, int W, int C, int level, float* y,

@@ -117,8 +117,18 @@ rl_status rl_launch_view_alpha(const void* M, rl_dtype dt, int D, int H, int W, 
                                cudaStream_t s);
 // Sparsified gradient volume V [4N+4][k][h][w] from the level MPI Ml [D][h][w][4], the
 // selection S [k][h][w], the view alpha weights A [N][D][h][w] and full-resolution images.
+// With act != NULL the same channels go to act [k][h][w][32] BF16 channels-last (the learned
+// network's input, channels >= 4N+4 zero) instead, and V is not written.
 rl_status rl_launch_volume(const void* Ml, rl_dtype dt, int D, int h, int w, int level, const uint8_t* S, int k,
-                           const float* A, const float* images, const RLInvViews& iv, float* V, cudaStream_t s);
+                           const float* A, const float* images, const RLInvViews& iv, float* V, cudaStream_t s,
+                           void* act = nullptr);
+
+// Gradient volume of Sec. 3.3 at `level`: selection S, view alpha weights and V_s, with the
+// checks of reallife_gradient_volume; with act != NULL it writes the network's packed input
+// instead of V (V may then be NULL).
+rl_status rl_gradient_volume(const rl_mpi* m, const float* images, const rl_camera* src, int N, int k, int level,
+                             int selection, uint8_t* S_out, float* V, void* act, void* ws, size_t ws_bytes,
+                             cudaStream_t stream);
 
 // Learned update network (lgd.cu): packed parameter bytes, parameter packing, activation
 // buffer bytes and the forward pass (V [C][K][H][W] FP32 -> residual [K][H][W][4] FP32,
@@ -129,3 +139,6 @@ rl_status rl_lgd_prepare(const rl_lgd_params* p, void* net, cudaStream_t s);
 size_t rl_lgd_act_bytes(int K, int H, int W);
 rl_status rl_lgd_forward(const void* net, const float* V, int C, int K, int H, int W, float* residual, void* act0,
                          void* act1, unsigned* grid_bar, cudaStream_t s);
+// The network alone, on an input already packed into act0 (act1 and the counter as above).
+rl_status rl_lgd_network(const void* net, int K, int H, int W, float* residual, void* act0, void* act1,
+                         unsigned* grid_bar, cudaStream_t s);

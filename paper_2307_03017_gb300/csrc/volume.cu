@@ -10,6 +10,8 @@
 //   inverse warp (reference -> view) at plane d; a bilinear sample (zero padding) of A_{i,d}
 //   there; the PSV channels as the mean of the full-resolution PSV samples of the 2^l x 2^l
 //   child pixels (Sec. 3.2 downsamples the full-resolution volume); and M_l[d][p].
+// k_volume_packed: the same channels, written as the learned network's BF16 channels-last
+//   input instead of the FP32 [C][k][h][w] volume.
 #include "rl_internal.h"
 
 namespace {
@@ -70,6 +72,35 @@ k_view_alpha(const Tm* __restrict__ M, int D, int H, int W, const __grid_constan
     }
 }
 
+// Channels of kept voxel (p = (x, y), plane d) from view i: the inverse-warped alpha weight a
+// and the PSV colour psv[3] (the mean of the full-resolution samples of p's children).
+__device__ __forceinline__ void voxel_view(const float* __restrict__ A, const float* __restrict__ images,
+                                           const RLInvViews& iv, int D, int h, int w, int level, int x, int y,
+                                           int d, int i, float& a, float (&psv)[3]) {
+    const long long hw = (long long)h * w;
+    const float rho = iv.rho[d];
+    const int s = 1 << level, H = h << level, W = w << level;
+    const float inv_area = 1.f / (float)(s * s);
+    // inverse-warped alpha weight of view i, at level l
+    const RLInvWarp c = rl_inv_coeffs(iv.lv[i], (float)x, (float)y);
+    sample_map<1>(A + ((size_t)i * D + d) * hw, h, w, rl_inv_taps(c, iv.lv[i], rho, x, y), &a);
+    // PSV of view i: mean over the full-resolution children of p
+    float acc[3] = {0.f, 0.f, 0.f};
+    const float* img = images + (size_t)i * H * W * 3;
+    for (int yy = 0; yy < s; ++yy)
+        for (int xx = 0; xx < s; ++xx) {
+            const int X = x * s + xx, Y = y * s + yy;
+            const RLInvWarp cf = rl_inv_coeffs(iv.full[i], (float)X, (float)Y);
+            float v[3];
+            sample_map<3>(img, H, W, rl_inv_taps(cf, iv.full[i], rho, X, Y), v);
+            acc[0] += v[0];
+            acc[1] += v[1];
+            acc[2] += v[2];
+        }
+#pragma unroll
+    for (int ch = 0; ch < 3; ++ch) psv[ch] = acc[ch] * inv_area;
+}
+
 template <typename Tm>
 __global__ void __launch_bounds__(128)
 k_volume(const Tm* __restrict__ Ml, int D, int h, int w, int level, const uint8_t* __restrict__ S, int k,
@@ -94,35 +125,71 @@ k_volume(const Tm* __restrict__ Ml, int D, int h, int w, int level, const uint8_
             for (int c = 0; c < 4; ++c) out[(size_t)(4 * N + c) * cstride] = 0.f;
         return;
     }
-    const float rho = iv.rho[d];
-    const int s = 1 << level, H = h << level, W = w << level;
-    const float inv_area = 1.f / (float)(s * s);
-    // inverse-warped alpha weight of view i, at level l
-    const RLInvWarp c = rl_inv_coeffs(iv.lv[i], (float)x, (float)y);
-    float a;
-    sample_map<1>(A + ((size_t)i * D + d) * hw, h, w, rl_inv_taps(c, iv.lv[i], rho, x, y), &a);
+    float a, psv[3];
+    voxel_view(A, images, iv, D, h, w, level, x, y, d, i, a, psv);
     out[(size_t)(3 * N + i) * cstride] = a;
-    // PSV of view i: mean over the full-resolution children of p
-    float acc[3] = {0.f, 0.f, 0.f};
-    const float* img = images + (size_t)i * H * W * 3;
-    for (int yy = 0; yy < s; ++yy)
-        for (int xx = 0; xx < s; ++xx) {
-            const int X = x * s + xx, Y = y * s + yy;
-            const RLInvWarp cf = rl_inv_coeffs(iv.full[i], (float)X, (float)Y);
-            float v[3];
-            sample_map<3>(img, H, W, rl_inv_taps(cf, iv.full[i], rho, X, Y), v);
-            acc[0] += v[0];
-            acc[1] += v[1];
-            acc[2] += v[2];
-        }
 #pragma unroll
-    for (int ch = 0; ch < 3; ++ch) out[(size_t)(3 * i + ch) * cstride] = acc[ch] * inv_area;
+    for (int ch = 0; ch < 3; ++ch) out[(size_t)(3 * i + ch) * cstride] = psv[ch];
     if (i == 0) {
         const float4 m = RLStore<Tm>::load4(Ml + ((size_t)d * hw + p) * 4);
         out[(size_t)(4 * N + 0) * cstride] = m.x;
         out[(size_t)(4 * N + 1) * cstride] = m.y;
         out[(size_t)(4 * N + 2) * cstride] = m.z;
         out[(size_t)(4 * N + 3) * cstride] = m.w;
+    }
+}
+
+// The same volume as the network's input: act [k][h][w][32] BF16 channels-last (round to
+// nearest even), channels >= 4N + 4 zero.  Block = N warps over 32 consecutive voxels of one
+// slot, warp i computing view i (the gathers of a warp stay those of one view); the voxels'
+// channels meet in shared memory and leave as one contiguous 64-byte record per voxel.
+template <typename Tm>
+__global__ void __launch_bounds__(32 * RL_DEV_MAX_VIEWS)
+k_volume_packed(const Tm* __restrict__ Ml, int D, int h, int w, int level, const uint8_t* __restrict__ S,
+                const float* __restrict__ A, const float* __restrict__ images, const __grid_constant__ RLInvViews iv,
+                __nv_bfloat16* __restrict__ act) {
+    __shared__ float rec[32][33];  // 32 voxels x 32 channels (+1: rows start on different banks)
+    const long long hw = (long long)h * w;
+    const int lane = threadIdx.x & 31, i = threadIdx.x >> 5;
+    const long long p0 = (long long)blockIdx.x * 32;
+    const long long p = p0 + lane;
+    const int j = blockIdx.y;
+    const int N = iv.n;
+    for (int t = threadIdx.x; t < 32 * 32; t += blockDim.x) rec[t >> 5][t & 31] = 0.f;
+    __syncthreads();
+    if (p < hw) {
+        const int d = __ldg(S + (size_t)j * hw + p);
+        if (d < D) {
+            const int y = (int)(p / w), x = (int)(p % w);
+            float a, psv[3];
+            voxel_view(A, images, iv, D, h, w, level, x, y, d, i, a, psv);
+            rec[lane][3 * i] = psv[0];
+            rec[lane][3 * i + 1] = psv[1];
+            rec[lane][3 * i + 2] = psv[2];
+            rec[lane][3 * N + i] = a;
+            if (i == 0) {
+                const float4 m = RLStore<Tm>::load4(Ml + ((size_t)d * hw + p) * 4);
+                rec[lane][4 * N + 0] = m.x;
+                rec[lane][4 * N + 1] = m.y;
+                rec[lane][4 * N + 2] = m.z;
+                rec[lane][4 * N + 3] = m.w;
+            }
+        }
+    }
+    __syncthreads();
+    // 32 voxels x 4 chunks of 8 channels, 16 bytes each
+    for (int t = threadIdx.x; t < 128; t += blockDim.x) {
+        const int v = t >> 2, chunk = t & 3;
+        if (p0 + v >= hw) continue;
+        const float* r = &rec[v][chunk * 8];
+        uint4 pk;
+        __nv_bfloat162 q0 = __floats2bfloat162_rn(r[0], r[1]), q1 = __floats2bfloat162_rn(r[2], r[3]);
+        __nv_bfloat162 q2 = __floats2bfloat162_rn(r[4], r[5]), q3 = __floats2bfloat162_rn(r[6], r[7]);
+        pk.x = *reinterpret_cast<uint32_t*>(&q0);
+        pk.y = *reinterpret_cast<uint32_t*>(&q1);
+        pk.z = *reinterpret_cast<uint32_t*>(&q2);
+        pk.w = *reinterpret_cast<uint32_t*>(&q3);
+        *reinterpret_cast<uint4*>(act + ((size_t)j * hw + p0 + v) * 32 + chunk * 8) = pk;
     }
 }
 
@@ -144,8 +211,23 @@ rl_status rl_launch_view_alpha(const void* M, rl_dtype dt, int D, int H, int W, 
 }
 
 rl_status rl_launch_volume(const void* Ml, rl_dtype dt, int D, int h, int w, int level, const uint8_t* S, int k,
-                           const float* A, const float* images, const RLInvViews& iv, float* V, cudaStream_t s) {
+                           const float* A, const float* images, const RLInvViews& iv, float* V, cudaStream_t s,
+                           void* act) {
     const long long hw = (long long)h * w;
+    if (act) {
+        const dim3 grid((unsigned)((hw + 31) / 32), (unsigned)k);
+        const unsigned block = 32u * (unsigned)iv.n;
+        if (dt == RL_F32) {
+            RLTraceScope ts("volume_packed_f32", s);
+            k_volume_packed<float><<<grid, block, 0, s>>>((const float*)Ml, D, h, w, level, S, A, images, iv,
+                                                          (__nv_bfloat16*)act);
+        } else {
+            RLTraceScope ts("volume_packed_bf16", s);
+            k_volume_packed<__nv_bfloat16><<<grid, block, 0, s>>>((const __nv_bfloat16*)Ml, D, h, w, level, S, A,
+                                                                  images, iv, (__nv_bfloat16*)act);
+        }
+        return rl_check_launch("volume");
+    }
     const dim3 grid((unsigned)((hw + 127) / 128), (unsigned)k, (unsigned)iv.n);
     if (dt == RL_F32) {
         RLTraceScope ts("volume_f32", s);

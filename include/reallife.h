@@ -317,6 +317,13 @@ rl_status reallife_set_kernel_path(int path);
  * clear != 0 resets the word.  Results of launches that timed out are invalid. */
 rl_status reallife_device_status(int clear, unsigned int* flags_out);
 
+/* Self-test of the failure reporting (no fault, no hang): one thread waits on a
+ * shared-memory barrier that nothing completes, for at most wait_us microseconds of the
+ * global timer, then sets the timeout bit of the device status word and returns.  After the
+ * stream has run it, reallife_device_status reports RL_ETIMEOUT; once the word is cleared,
+ * the context is usable.  RL_EINVAL unless 1 <= wait_us <= 1000000. */
+rl_status reallife_selftest_wait_timeout(unsigned int wait_us, cudaStream_t stream);
+
 /* Host-side kernel tracing: when enabled, every kernel launch of this library is
  * bracketed by CUDA events on its stream and counted per kernel name.  Launches made
  * while the stream is being captured into a CUDA graph are bracketed by external event

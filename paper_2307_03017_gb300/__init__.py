@@ -24,7 +24,7 @@ __all__ = [
     "reallife_sparse_update", "reallife_render_backward", "reallife_warp_offsets",
     "reallife_trace_enable", "reallife_trace_read", "reallife_strerror", "workspace", "library_path",
     "reallife_set_kernel_path", "reallife_device_status", "reallife_hsgd_step_noalloc",
-    "reallife_trace_release_captured",
+    "reallife_trace_release_captured", "reallife_selftest_wait_timeout",
 ]
 
 RealLifeError = _lib.RealLifeError
@@ -388,6 +388,13 @@ def reallife_strerror(status: int) -> str:
 def reallife_set_kernel_path(path: int):
     """0: automatic (default); 1: TMA-staged windows; 2: per-pixel gather; 3: plane-parallel."""
     _lib.check("reallife_set_kernel_path", _lib.lib().reallife_set_kernel_path(int(path)))
+
+
+def reallife_selftest_wait_timeout(wait_us: int = 2000, stream=None) -> None:
+    """Enqueue the bounded-wait self-test: a wait that nothing completes gives up after
+    wait_us microseconds and sets the timeout bit that reallife_device_status reports."""
+    _lib.check("reallife_selftest_wait_timeout", _lib.lib().reallife_selftest_wait_timeout(int(wait_us),
+                                                                                             _stream(stream)))
 
 
 def reallife_device_status(clear: bool = True) -> int:

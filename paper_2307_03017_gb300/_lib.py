@@ -21,7 +21,7 @@ EXPORTS = [
     "reallife_device_status", "reallife_hsgd_step_noalloc", "reallife_trace_release_captured",
     "reallife_gradient_volume_workspace_bytes", "reallife_gradient_volume", "reallife_lgd_net_bytes",
     "reallife_lgd_prepare", "reallife_lgd_workspace_bytes", "reallife_lgd_forward",
-    "reallife_lgd_step_workspace_bytes", "reallife_lgd_step",
+    "reallife_lgd_step_workspace_bytes", "reallife_lgd_step", "reallife_selftest_wait_timeout",
 ]
 
 
@@ -99,6 +99,7 @@ def _declare(lib):
         "reallife_strerror": (ctypes.c_char_p, [c_int]),
         "reallife_set_kernel_path": (c_int, [c_int]),
         "reallife_device_status": (c_int, [c_int, ctypes.POINTER(ctypes.c_uint)]),
+        "reallife_selftest_wait_timeout": (c_int, [ctypes.c_uint, vp]),
         "reallife_last_error": (ctypes.c_char_p, []),
         "reallife_gradient_volume_workspace_bytes": (c_size_t, [c_int, c_int, c_int, c_int, c_int, c_int]),
         "reallife_gradient_volume": (c_int, [mpi_p, vp, cam_p, c_int, c_int, c_int, c_int, vp, vp, vp, c_size_t,

@@ -95,6 +95,41 @@ extern "C" rl_status reallife_set_kernel_path(int path) {
     return RL_OK;
 }
 
+namespace {
+
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// One thread waits on a shared-memory barrier that nothing completes, for at most limit_ns
+// of the global timer, then reports the timeout through the status word and returns: the
+// same bounded-wait path every waiting kernel takes.
+__global__ void k_selftest_wait(unsigned long long limit_ns, unsigned int* status) {
+    __shared__ uint64_t bar;
+    if (threadIdx.x != 0) return;
+    rltma::mbar_init(&bar, 1);
+    rltma::fence_mbar_init();
+    const unsigned long long t0 = global_ns();
+    while (!rltma::mbar_try_wait(&bar, 0u)) {
+        if (global_ns() - t0 > limit_ns) {
+            atomicOr(status, RL_DEVFLAG_TIMEOUT);
+            return;
+        }
+    }
+}
+
+}  // namespace
+
+extern "C" rl_status reallife_selftest_wait_timeout(unsigned int wait_us, cudaStream_t stream) {
+    if (wait_us < 1 || wait_us > 1000000u) return rl_fail(RL_EINVAL, "selftest: wait_us=%u outside [1, 1e6]", wait_us);
+    unsigned int* status = rl_device_status_ptr();
+    if (!status) return rl_fail(RL_ECUDA, "device status word unavailable");
+    k_selftest_wait<<<1, 32, 0, stream>>>((unsigned long long)wait_us * 1000ull, status);
+    return rl_check_launch("selftest_wait");
+}
+
 extern "C" rl_status reallife_device_status(int clear, unsigned int* flags_out) {
     unsigned int* p = rl_device_status_ptr();
     if (!p) return rl_fail(RL_ECUDA, "device status word unavailable");

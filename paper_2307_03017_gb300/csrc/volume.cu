@@ -24,9 +24,16 @@ __device__ __forceinline__ float sample_alpha(const Tm* __restrict__ plane, int 
     if (!t.ok) return 0.f;
     const float w00 = (1.f - t.fx) * (1.f - t.fy), w10 = t.fx * (1.f - t.fy);
     const float w01 = (1.f - t.fx) * t.fy, w11 = t.fx * t.fy;
+    const size_t r0 = (size_t)t.y0 * W, r1 = r0 + W;
+    if ((unsigned)t.x0 < (unsigned)(W - 1) && (unsigned)t.y0 < (unsigned)(H - 1)) {
+        // all four taps inside: the same products in the same order, without the per-tap tests
+        float a = fmaf(w00, RLStore<Tm>::load1(plane + (r0 + t.x0) * 4 + 3), 0.f);
+        a = fmaf(w10, RLStore<Tm>::load1(plane + (r0 + t.x0 + 1) * 4 + 3), a);
+        a = fmaf(w01, RLStore<Tm>::load1(plane + (r1 + t.x0) * 4 + 3), a);
+        return fmaf(w11, RLStore<Tm>::load1(plane + (r1 + t.x0 + 1) * 4 + 3), a);
+    }
     const bool x0in = (unsigned)t.x0 < (unsigned)W, x1in = (unsigned)(t.x0 + 1) < (unsigned)W;
     const bool y0in = (unsigned)t.y0 < (unsigned)H, y1in = (unsigned)(t.y0 + 1) < (unsigned)H;
-    const size_t r0 = (size_t)t.y0 * W, r1 = r0 + W;
     float a = 0.f;
     if (y0in && x0in) a = fmaf(w00, RLStore<Tm>::load1(plane + (r0 + t.x0) * 4 + 3), a);
     if (y0in && x1in) a = fmaf(w10, RLStore<Tm>::load1(plane + (r0 + t.x0 + 1) * 4 + 3), a);

@@ -134,3 +134,28 @@ def test_learned_step_rejects_too_many_views(rl):
     m = rl.make_mpi(torch.from_numpy(sc.coarse_mpi).cuda(), sc.near, sc.far, sc.ref)
     with pytest.raises(rl._lib.RealLifeError):
         rl.reallife_lgd_step(m, torch.from_numpy(sc.images).cuda(), sc.src, 2, net)  # 4*8+4 = 36 > 32 channels
+
+
+@pytest.mark.parametrize("level", [0, 2])
+def test_learned_step_equals_its_composition(rl, level):
+    """The learned step writes the network's BF16 input straight from the volume gather; the
+    same step composed from the public calls (FP32 volume, network with its own packing,
+    masked update with step -1) must give the same MPI bit for bit."""
+    sc = sg.workload("small", 2)[0]
+    k, N = 4, len(sc.src)
+    params = sg.lgd_weights(15, 4 * N + 4)
+    net = rl.LgdNet(params)
+    images = torch.from_numpy(sc.images).cuda()
+    M1 = torch.from_numpy(sc.coarse_mpi).cuda()
+    M2 = M1.clone()
+    m1 = rl.make_mpi(M1, sc.near, sc.far, sc.ref)
+    m2 = rl.make_mpi(M2, sc.near, sc.far, sc.ref)
+    h, w = sc.H >> level, sc.W >> level
+    S1 = torch.empty((k, h, w), dtype=torch.uint8, device="cuda")
+    rl.reallife_lgd_step(m1, images, sc.src, k, net, level=level, S_out=S1)
+    V, S2 = rl.reallife_gradient_volume(m2, images, sc.src, k, level)
+    res = rl.reallife_lgd_forward(net, V)
+    rl.reallife_sparse_update(m2, S2, res, k, level, -1.0)
+    torch.cuda.synchronize()
+    assert torch.equal(S1, S2)
+    assert torch.equal(M1, M2)

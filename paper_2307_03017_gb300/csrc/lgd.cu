@@ -75,7 +75,7 @@ struct SmemLayout {
     static constexpr int W = 0;
     static constexpr int A = W + kWBytes;
     static constexpr int BAR = A + kRowSlots * kSlotBytes;
-    static constexpr int NBAR = 2 * kRowSlots + 2 * kSets + 2;
+    static constexpr int NBAR = 2 * kRowSlots + kSets + 2;
     static constexpr int TSLOT = BAR + NBAR * 8;
     static constexpr int BIAS = TSLOT + 16;
     static constexpr int OUTW = BIAS + kF * 4;
@@ -195,8 +195,10 @@ k_conv_net(const __grid_constant__ CUtensorMap map0, const __grid_constant__ CUt
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem + SmemLayout::BAR);
     uint64_t* full = bars;
     uint64_t* empty = bars + kRowSlots;
-    uint64_t* trow = bars + 2 * kRowSlots;  // [kSets]: the window's staged row has its MMAs done
-    uint64_t* tdrain = trow + kSets;        // [kSets]: the epilogue has read the window
+    // empty[slot] also tells the epilogue that the row's products are in its window: row jr + 5
+    // (the slot's next completion) waits for the epilogue to drain row jr + 1, so the epilogue
+    // cannot miss a phase
+    uint64_t* tdrain = bars + 2 * kRowSlots;  // [kSets]: the epilogue has read the window
     uint64_t* wbar = tdrain + kSets;        // a block's weights have landed (one phase a block)
     uint64_t* mma_done = wbar + 1;          // every MMA of a block has completed (one phase a block)
     uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + SmemLayout::TSLOT);
@@ -218,7 +220,6 @@ k_conv_net(const __grid_constant__ CUtensorMap map0, const __grid_constant__ CUt
             mbar_init(&empty[i], 1);
         }
         for (int b = 0; b < kSets; ++b) {
-            mbar_init(&trow[b], 1);
             mbar_init(&tdrain[b], 4);
         }
         mbar_init(wbar, 1);
@@ -352,8 +353,8 @@ k_conv_net(const __grid_constant__ CUtensorMap map0, const __grid_constant__ CUt
                                 }
                         }
                     }
-                    umma_commit(&empty[slot]);  // the row is read by no later MMA
-                    umma_commit(&trow[set]);    // the window's partial products are ready
+                    // the row is read by no later MMA, and its window holds its products
+                    umma_commit(&empty[slot]);
                     if (++slot == kRowSlots) {
                         slot = 0;
                         slot_phase ^= 1u;
@@ -389,7 +390,8 @@ k_conv_net(const __grid_constant__ CUtensorMap map0, const __grid_constant__ CUt
                     const int lo = max(0, j - (n - 1)), hi = min(2, j);
                     bool ok = true;
                     if (lane == 0)
-                        ok = mbar_wait(&trow[set], (uint32_t)((jr / kSets) & 1)) && !*(volatile int*)&s_abort;
+                        ok = mbar_wait(&empty[jr % kRowSlots], (uint32_t)((jr / kRowSlots) & 1)) &&
+                             !*(volatile int*)&s_abort;
                     ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
                     if (!ok) {
                         if (lane == 0) {

@@ -161,34 +161,36 @@ k_volume_packed(const Tm* __restrict__ Ml, int D, int h, int w, int level, const
     const long long p0 = (long long)blockIdx.x * 32;
     const long long p = p0 + lane;
     const int j = blockIdx.y;
-    const int N = iv.n;
-    for (int t = threadIdx.x; t < 32 * 32; t += blockDim.x) rec[t >> 5][t & 31] = 0.f;
-    __syncthreads();
+    const int N = iv.n, C = 4 * N + 4;
     if (p < hw) {
+        // each warp writes every channel it owns, zeros included, so no fill is needed
+        float a = 0.f, psv[3] = {0.f, 0.f, 0.f};
+        float4 m = make_float4(0.f, 0.f, 0.f, 0.f);
         const int d = __ldg(S + (size_t)j * hw + p);
         if (d < D) {
             const int y = (int)(p / w), x = (int)(p % w);
-            float a, psv[3];
             voxel_view(A, images, iv, D, h, w, level, x, y, d, i, a, psv);
-            rec[lane][3 * i] = psv[0];
-            rec[lane][3 * i + 1] = psv[1];
-            rec[lane][3 * i + 2] = psv[2];
-            rec[lane][3 * N + i] = a;
-            if (i == 0) {
-                const float4 m = RLStore<Tm>::load4(Ml + ((size_t)d * hw + p) * 4);
-                rec[lane][4 * N + 0] = m.x;
-                rec[lane][4 * N + 1] = m.y;
-                rec[lane][4 * N + 2] = m.z;
-                rec[lane][4 * N + 3] = m.w;
-            }
+            if (i == 0) m = RLStore<Tm>::load4(Ml + ((size_t)d * hw + p) * 4);
+        }
+        rec[lane][3 * i] = psv[0];
+        rec[lane][3 * i + 1] = psv[1];
+        rec[lane][3 * i + 2] = psv[2];
+        rec[lane][3 * N + i] = a;
+        if (i == 0) {
+            rec[lane][4 * N + 0] = m.x;
+            rec[lane][4 * N + 1] = m.y;
+            rec[lane][4 * N + 2] = m.z;
+            rec[lane][4 * N + 3] = m.w;
         }
     }
     __syncthreads();
-    // 32 voxels x 4 chunks of 8 channels, 16 bytes each
+    // 32 voxels x 4 chunks of 8 channels, 16 bytes each; channels >= C are zero
     for (int t = threadIdx.x; t < 128; t += blockDim.x) {
         const int v = t >> 2, chunk = t & 3;
         if (p0 + v >= hw) continue;
-        const float* r = &rec[v][chunk * 8];
+        float r[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) r[e] = chunk * 8 + e < C ? rec[v][chunk * 8 + e] : 0.f;
         uint4 pk;
         __nv_bfloat162 q0 = __floats2bfloat162_rn(r[0], r[1]), q1 = __floats2bfloat162_rn(r[2], r[3]);
         __nv_bfloat162 q2 = __floats2bfloat162_rn(r[4], r[5]), q3 = __floats2bfloat162_rn(r[6], r[7]);

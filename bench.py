@@ -721,6 +721,15 @@ def platform_cpu() -> str:
         return "unknown"
 
 
+def reference_band_rows(H: int, unit: int, t_unit: float, n_steps: int, budget_s: float = 120.0) -> int:
+    """Rows of the reference arm's band: a multiple of `unit` (the coarsest level's block),
+    at least one unit and at most 1/8 of the H rows (rounded down to units), sized so that
+    n_steps steps of t_unit seconds per unit of rows take about budget_s."""
+    units = int(budget_s / max(1, n_steps) / max(t_unit, 1e-6))
+    cap = max(1, (max(8, H // 8 // 8 * 8)) // unit)
+    return unit * max(1, min(cap, units))
+
+
 def run_reference(args, world, rank):
     """The oracle on the host cores, each step a horizontal band of the workload (scaled by its
     share of the pixels).  One untimed step on a 4-row band (the least height the coarsest
@@ -734,9 +743,7 @@ def run_reference(args, world, rank):
     unit = 1 << max(cfg["schedule"])
     t0 = time.perf_counter()
     oracle_step(crop_scene(sc, unit), cfg)
-    t1 = time.perf_counter() - t0
-    units = int(120.0 / max(1, args.steps + args.warmup) / max(t1, 1e-6))
-    rows = unit * max(1, min(sample_rows(sc, 0.125) // unit, units))
+    rows = reference_band_rows(sc.H, unit, time.perf_counter() - t0, args.steps + args.warmup)
     band = crop_scene(sc, rows)
     share = rows / sc.H
     for _ in range(args.warmup):

@@ -29,7 +29,7 @@ k_render(const Tm* __restrict__ M, int D, int H, int W, const __grid_constant__ 
     const RLWarp w = rl_warp_coeffs(views.v[view], (float)qx, (float)qy);
     const size_t plane = (size_t)H * W * 4;
     float T = 1.f, c0 = 0.f, c1 = 0.f, c2 = 0.f;
-#pragma unroll 2
+#pragma unroll 1
     for (int d = D - 1; d >= 0; --d) {
         const RLTaps t = rl_taps(w, views.rho[d], qx, qy);
         const float4 m = rl_sample_fast(M + d * plane, H, W, t);

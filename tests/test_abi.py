@@ -99,3 +99,25 @@ def test_invalid_arguments_rejected_on_host(cpu_only):
     assert lib.reallife_hsgd_step(ctypes.byref(m), img, cams, 1, ctypes.byref(P), None, None, ws, 1 << 30, None) == 1
     P.selection, P.lambda_s = 0, -1.0
     assert lib.reallife_hsgd_step(ctypes.byref(m), img, cams, 1, ctypes.byref(P), None, None, ws, 1 << 30, None) == 1
+
+
+def test_learned_update_workspace_sizes():
+    """The network's workspace: two BF16 channels-last activation volumes (1 KB aligned)
+    and the 256-byte grid-barrier block; the learned step's holds the gradient volume's
+    workspace, the residual, S, the two activation volumes and the barrier block (no FP32
+    volume: the gather writes the network's input directly)."""
+    import paper_2307_03017_gb300 as rl
+    lib = rl._lib.lib()
+    for k, h, w in ((5, 384, 512), (1, 1, 1), (3, 7, 129)):
+        act = (k * h * w * 64 + 1023) // 1024 * 1024
+        assert lib.reallife_lgd_workspace_bytes(k, h, w) == 2 * act + 256
+    assert lib.reallife_lgd_workspace_bytes(0, 4, 4) == 0
+    N, D, H, W, k = 4, 32, 384, 512, 5
+
+    def a256(x):
+        return (x + 255) // 256 * 256
+
+    vol = lib.reallife_gradient_volume_workspace_bytes(N, D, H, W, k, 0)
+    act = (k * H * W * 64 + 1023) // 1024 * 1024
+    want = a256(vol) + a256(k * H * W * 16) + a256(k * H * W) + 2 * act + 256
+    assert lib.reallife_lgd_step_workspace_bytes(N, D, H, W, k, 0) == want

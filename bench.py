@@ -98,6 +98,21 @@ def csrc_digest(files=None) -> str:
     return h.hexdigest()[:16]
 
 
+def stored_traffic(key: str):
+    """ncu DRAM bytes per launch of a kernel (profiles/traffic.json), or None once the
+    kernel's source files differ from those the counters were taken on."""
+    tf = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(tf):
+        return None
+    try:
+        tr = json.load(open(tf)).get(key)
+        if tr and tr.get("csrc_digest") == csrc_digest(tr.get("files")):
+            return tr["dram_bytes_per_launch"]
+    except Exception:
+        return None
+    return None
+
+
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
 
@@ -303,15 +318,7 @@ def run_ours(args, world, rank, local):
     else:
         alg_bytes = None
     achieved = alg_bytes / (dom_ms / 1e3) / 1e9 if alg_bytes else None
-    traffic = None
-    tf = os.path.join(ROOT, "profiles", "traffic.json")
-    if os.path.exists(tf):
-        try:
-            tr = json.load(open(tf)).get(f"{args.workload}:{dom_name}")
-            if tr and tr.get("csrc_digest") == csrc_digest(tr.get("files")):
-                traffic = tr["dram_bytes_per_launch"]
-        except Exception:
-            traffic = None
+    traffic = stored_traffic(f"{args.workload}:{dom_name}")
     roofline = {"bound": "hbm", "kernel": dom_name, "achieved": round(achieved, 1) if achieved else None,
                 "peak": peak_gbs, "unit": "GB/s", "frac": round(achieved / peak_gbs, 4) if achieved else None,
                 "traffic": traffic, "alg_bytes_per_launch": int(alg_bytes / dom_n) if alg_bytes else None,
@@ -458,7 +465,8 @@ def run_stage(args, world, rank, local):
         achieved = flops / (dom_ms / 1e3) / 1e12
         peak, src = (peaks["bf16_tflops"], "measured (burst)") if "bf16_tflops" in peaks else (1900.0, "fallback")
         roofline = {"bound": "tensor", "kernel": dom_name, "achieved": round(achieved, 1), "peak": peak,
-                    "unit": "TFLOP/s", "frac": round(achieved / peak, 4), "traffic": None,
+                    "unit": "TFLOP/s", "frac": round(achieved / peak, 4),
+                    "traffic": stored_traffic(f"{args.workload}:{dom_name}"),
                     "alg_flops_per_launch": int(flops / dom_n), "avg_launch_us": round(dom_ms / dom_n * 1e3, 2),
                     "peak_source": src}
     else:
@@ -469,7 +477,8 @@ def run_stage(args, world, rank, local):
         peak, src = (peaks["hbm_gbs"], "measured") if "hbm_gbs" in peaks else (6800.0, "fallback")
         roofline = {"bound": "hbm", "kernel": dom_name, "achieved": round(achieved, 1) if achieved else None,
                     "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4) if achieved else None,
-                    "traffic": None, "alg_bytes_per_launch": int(alg / dom_n) if alg else None,
+                    "traffic": stored_traffic(f"{args.workload}:{dom_name}"),
+                    "alg_bytes_per_launch": int(alg / dom_n) if alg else None,
                     "avg_launch_us": round(dom_ms / dom_n * 1e3, 2), "peak_source": src}
     kernels = {n: {"launches": c, "ms_per_step": round(t / args.steps, 4)} for n, (c, t) in sorted(trace.items())}
     result = None

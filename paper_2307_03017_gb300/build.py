@@ -2,7 +2,8 @@
 
 Each CUDA translation unit is compiled in parallel to ``_build/<machine>/`` and linked
 into ``paper_2307_03017_gb300/libreallife.so`` (static CUDA runtime).  Rebuilds only
-when a source or header is newer than the library.
+when a source or header is newer than the library, and then recompiles only the
+translation units whose object is older than the unit or any header.
 """
 from __future__ import annotations
 
@@ -33,9 +34,13 @@ def sources() -> list[str]:
     return sorted(glob.glob(os.path.join(CSRC, "*.cu")))
 
 
-def _deps() -> list[str]:
-    return sources() + glob.glob(os.path.join(CSRC, "*.h")) + glob.glob(os.path.join(CSRC, "*.cuh")) + \
+def _headers() -> list[str]:
+    return glob.glob(os.path.join(CSRC, "*.h")) + glob.glob(os.path.join(CSRC, "*.cuh")) + \
         glob.glob(os.path.join(INCLUDE, "*.h")) + [os.path.abspath(__file__)]
+
+
+def _deps() -> list[str]:
+    return sources() + _headers()
 
 
 def up_to_date() -> bool:
@@ -53,9 +58,13 @@ def build(force: bool = False, verbose: bool = False, extra_flags: list[str] | N
     objdir = os.path.join(HERE, "_build", platform.machine())
     os.makedirs(objdir, exist_ok=True)
     flags = NVCC_FLAGS + (extra_flags or [])
+    newest_header = max(os.path.getmtime(p) for p in _headers())
 
     def compile_one(src):
         obj = os.path.join(objdir, os.path.basename(src)[:-3] + ".o")
+        if not force and not extra_flags and os.path.exists(obj) and \
+                os.path.getmtime(obj) >= max(os.path.getmtime(src), newest_header):
+            return obj
         cmd = [exe] + ARCH + flags + ["-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:

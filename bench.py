@@ -52,6 +52,9 @@ def parse():
     ap.add_argument("--slots", type=int, default=8, help="serve: concurrent request slots")
     ap.add_argument("--arena-gb", type=float, default=24.0, help="serve: device memory arena (GB)")
     ap.add_argument("--graphs", action="store_true", help="serve: replay captured CUDA graphs")
+    ap.add_argument("--serve-mode", choices=["batched", "streams"], default="streams",
+                    help="serve: one batched launch per stage for all active requests, or a stream per slot")
+    ap.add_argument("--lanes", type=int, default=2, help="serve, batched: size classes batched separately")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--graph", action="store_true", help="replay a captured CUDA graph of the step instead of "
                     "launching its kernels directly (measured no faster: the tracer's event nodes cost what "
@@ -592,19 +595,32 @@ SERVE_RES = [(192, 256), (384, 512), (576, 768), (768, 1024)]
 SERVE_D = [16, 32, 48, 64]
 
 
+def _serve_scene(args):
+    import scenegen as sg
+    seed, H, W, D, n_views = args
+    sc = sg.make_scene(seed, H, W, D, n_views, n_layers=(3, 8), novel="none")
+    return (H, W, D), sc
+
+
 def serve_scene_pool(seed: int = 7, n_views: int = 6):
     """One seeded scene per (resolution, D) of the serving workload, with 6 source views
-    (requests with fewer views use the first N), coarse MPI BF16 in pinned host memory."""
-    import scenegen as sg
+    (requests with fewer views use the first N), coarse MPI BF16 in pinned host memory.  The
+    scenes are drawn in parallel processes (spawned: safe beside a CUDA context)."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
     import torch
-    pool = {}
+    jobs = []
     for (H, W) in SERVE_RES:
         for D in SERVE_D:
-            sc = sg.make_scene(seed + len(pool), H, W, D, n_views, n_layers=(3, 8), novel="none")
+            jobs.append((seed + len(jobs), H, W, D, n_views))
+    workers = max(1, min(len(jobs), len(os.sched_getaffinity(0))))
+    pool = {}
+    with cf.ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn")) as ex:
+        for key, sc in ex.map(_serve_scene, jobs):
             M = torch.from_numpy(sc.coarse_mpi).to(torch.bfloat16).pin_memory()
             I = torch.from_numpy(sc.images).pin_memory()
-            pool[(H, W, D)] = (sc, M, I)
             sc.coarse_mpi = None  # host copy no longer needed
+            pool[key] = (sc, M, I)
     return pool
 
 
@@ -630,7 +646,7 @@ def run_serve(args, world, rank, local):
     draws = sg.serve_requests(args.requests, args.rate, seed=12345)
     max_elems = max(M.numel() for (_, M, _) in pool.values())
     eng = ServeEngine(int(args.arena_gb * (1 << 30)), max_slots=args.slots, graphs=args.graphs,
-                      max_result_elems=max_elems)
+                      max_result_elems=max_elems, batched=args.serve_mode == "batched", lanes=args.lanes)
     # warm-up: one request of every (resolution, D) so first-use costs stay out of the run
     warm = serve_requests_from_pool(pool, [dict(id=-1, arrival=0.0, H=H, W=W, D=D, N=4, iters=3)
                                            for (H, W) in SERVE_RES for D in SERVE_D])
@@ -657,9 +673,11 @@ def run_serve(args, world, rank, local):
         "config": {"workload": f"serve: {args.requests} requests, Poisson {args.rate}/s, res in {SERVE_RES}, "
                                f"D in {SERVE_D}, N 2-6, 2-3 iterations, k=5, BF16",
                    "slots": args.slots, "arena_gb": args.arena_gb, "graphs": bool(args.graphs),
+                   "mode": args.serve_mode, "lanes": args.lanes if args.serve_mode == "batched" else None,
                    "latency": "arrival -> refined MPI and losses on the host (queueing, H2D, compute, D2H)",
                    "mean_pixels": mean_px, "scene_pool_s": round(t_gen, 1)},
         "graph_captures": eng.captures, "graph_replays": eng.replays, "clocks": clk,
+        "batched_steps": eng.steps, "max_requests_per_step": eng.max_items_per_step,
     }
 
 

@@ -161,6 +161,46 @@ rl_status reallife_refine(rl_mpi* m, const float* images, const rl_camera* src, 
 rl_status reallife_hsgd_step_noalloc(rl_mpi* m, const float* images, const rl_camera* src, int N,
                                      const rl_hsgd_params* p, float* loss_out, uint8_t* S_out, cudaStream_t stream);
 
+/* ------------------------------------------------------------- batched step */
+
+/* One HSGD iteration of each of many independent requests in one launch per stage, for the
+ * serving pattern in which requests of different sizes are refined concurrently (the paper's
+ * real-time generation for displays, Sec. 1 and Sec. 5.1 "3D display efficiency").  Each item
+ * is one request's iteration with exactly the arguments of reallife_hsgd_step; the results
+ * are those of reallife_hsgd_step on every item, up to FP32 rounding order: the gradient of
+ * every item takes the per-pixel gather kernel family.
+ *
+ * The batch is described by a work table: reallife_batch_prepare writes it (host only) into
+ * page-locked host memory, and reallife_hsgd_step_batch copies it to the device table and
+ * enqueues three persistent launches (selection, gradient, update) whose grids do not depend
+ * on the table.  A CUDA graph captured from one reallife_hsgd_step_batch call therefore serves
+ * any later table of the same storage type and capacity: rewrite the host table with
+ * reallife_batch_prepare (once the previous replay's copy has run) and replay.
+ *
+ *   items:       host array of n items; the MPI structs and cameras are read during the call.
+ *   table_host:  page-locked host memory of table_bytes >= reallife_batch_table_bytes(n).
+ *   table_dev:   device memory of table_bytes, 256-byte aligned.
+ * RL_EINVAL: n outside [1, RL_BATCH_MAX_ITEMS], any item failing the checks of
+ * reallife_hsgd_step (its index in reallife_last_error), items of different storage types,
+ * two items sharing an MPI or overlapping workspaces, a table_host that is not page-locked.
+ * RL_ENOMEM: table_bytes too small, or an item's ws_bytes too small.  Device-side: a table of
+ * another storage type than the captured kernels' sets bit 2 of the device status word
+ * (reallife_device_status) and leaves the MPIs unchanged. */
+#define RL_BATCH_MAX_ITEMS 256
+typedef struct {
+    rl_mpi* mpi;             /* refined in place; caller-owned */
+    const float* images;     /* device [N][H][W][3] FP32, full resolution */
+    const rl_camera* src;    /* host array of N source cameras */
+    int N;
+    rl_hsgd_params params;   /* this iteration's k, lambda, clamp01, level, selection, lambda_s */
+    float* loss_out;         /* device float[1] (loss at the level) or NULL */
+    void* ws;                /* the request's workspace: reallife_workspace_bytes(N, D, H, W, k, dtype) */
+    size_t ws_bytes;
+} rl_batch_item;
+size_t reallife_batch_table_bytes(int max_items);
+rl_status reallife_batch_prepare(const rl_batch_item* items, int n, void* table_host, size_t table_bytes);
+rl_status reallife_hsgd_step_batch(const void* table_host, void* table_dev, size_t table_bytes, cudaStream_t stream);
+
 /* --------------------------------------------------------- gradient volume */
 
 /* Bytes of workspace that reallife_gradient_volume needs for an MPI of D x H x W with N

@@ -25,6 +25,7 @@ __all__ = [
     "reallife_trace_enable", "reallife_trace_read", "reallife_strerror", "workspace", "library_path",
     "reallife_set_kernel_path", "reallife_device_status", "reallife_hsgd_step_noalloc",
     "reallife_trace_release_captured", "reallife_selftest_wait_timeout",
+    "BatchItem", "BatchTable", "batch_c_item", "reallife_batch_table_bytes", "reallife_batch_prepare", "reallife_hsgd_step_batch",
 ]
 
 RealLifeError = _lib.RealLifeError
@@ -186,6 +187,78 @@ def reallife_refine(m: Mpi, images: torch.Tensor, src, k: int, schedule=(2, 1, 0
         ctypes.byref(ms), _ptr(images), _lib.cameras(src), N, ctypes.byref(p), sched, len(schedule),
         _ptr(loss_per_iter), _ptr(ws), ws.numel(), _stream(stream)))
     return loss_per_iter
+
+
+class BatchItem:
+    """One request's HSGD iteration in a batched step: the arguments of ``reallife_hsgd_step``."""
+
+    def __init__(self, m: Mpi, images: torch.Tensor, src, k: int, ws: torch.Tensor, level: int = 0,
+                 loss_out: torch.Tensor | None = None, lam: float = 1.0, clamp: bool = True,
+                 selection: int = SELECT_TOPK, lambda_s: float = 0.0):
+        _check_f32(images, (len(src), m.H, m.W, 3), "images")
+        self.m, self.images, self.src, self.k, self.ws, self.level = m, images, src, int(k), ws, int(level)
+        self.loss_out, self.lam, self.clamp, self.selection, self.lambda_s = loss_out, lam, clamp, selection, lambda_s
+
+
+class BatchTable:
+    """Work table of a batched step for up to ``max_items`` requests: page-locked host memory
+    (written by ``reallife_batch_prepare``) and its device copy."""
+
+    def __init__(self, max_items: int, device="cuda"):
+        self.max_items = int(max_items)
+        self.nbytes = reallife_batch_table_bytes(self.max_items)
+        if self.nbytes == 0:
+            raise ValueError(f"max_items={max_items} outside the library's range")
+        self.host = torch.empty(self.nbytes, dtype=torch.uint8).pin_memory()
+        self.dev = torch.empty(self.nbytes, dtype=torch.uint8, device=device)
+
+
+def reallife_batch_table_bytes(max_items: int) -> int:
+    return int(_lib.lib().reallife_batch_table_bytes(int(max_items)))
+
+
+def batch_c_item(it: BatchItem):
+    """The C struct of one batch item and the host objects it points to (keep them alive while
+    the struct is in use); its ``params.level`` and ``loss_out`` may be changed in place."""
+    ms = it.m.c_struct()
+    cams = _lib.cameras(it.src)
+    b = _lib.RlBatchItem()
+    b.mpi = ctypes.pointer(ms)
+    b.images = _ptr(it.images)
+    b.src = ctypes.cast(cams, ctypes.POINTER(_lib.RlCamera))
+    b.N = len(it.src)
+    b.params = _params(it.k, it.lam, it.clamp, it.level, it.selection, it.lambda_s)
+    b.loss_out = _ptr(it.loss_out)
+    b.ws = _ptr(it.ws)
+    b.ws_bytes = it.ws.numel()
+    return b, (ms, cams)
+
+
+def reallife_batch_prepare(items, table: BatchTable):
+    """Write the work table of one HSGD iteration of every item (host only).  ``items``:
+    ``BatchItem`` objects, or C structs from ``batch_c_item``."""
+    n = len(items)
+    keep = []
+    cs = []
+    for it in items:
+        if isinstance(it, _lib.RlBatchItem):
+            cs.append(it)
+        else:
+            b, k = batch_c_item(it)
+            cs.append(b)
+            keep.append(k)
+    arr = (_lib.RlBatchItem * max(n, 1))(*cs)
+    _lib.check("reallife_batch_prepare", _lib.lib().reallife_batch_prepare(
+        arr, n, ctypes.c_void_p(table.host.data_ptr()), table.nbytes))
+
+
+def reallife_hsgd_step_batch(table: BatchTable, items=None, stream=None):
+    """One HSGD iteration of every request of the table in one launch per stage (selection,
+    gradient, update); with ``items`` the table is first written from them."""
+    if items is not None:
+        reallife_batch_prepare(items, table)
+    _lib.check("reallife_hsgd_step_batch", _lib.lib().reallife_hsgd_step_batch(
+        ctypes.c_void_p(table.host.data_ptr()), _ptr(table.dev), table.nbytes, _stream(stream)))
 
 
 def reallife_gradient_volume_workspace_bytes(N: int, D: int, H: int, W: int, k: int, dtype=torch.float32) -> int:

@@ -22,6 +22,7 @@ EXPORTS = [
     "reallife_gradient_volume_workspace_bytes", "reallife_gradient_volume", "reallife_lgd_net_bytes",
     "reallife_lgd_prepare", "reallife_lgd_workspace_bytes", "reallife_lgd_forward",
     "reallife_lgd_step_workspace_bytes", "reallife_lgd_step", "reallife_selftest_wait_timeout",
+    "reallife_batch_table_bytes", "reallife_batch_prepare", "reallife_hsgd_step_batch",
 ]
 
 
@@ -41,6 +42,12 @@ class RlMpi(ctypes.Structure):
 class RlHsgdParams(ctypes.Structure):
     _fields_ = [("k", ctypes.c_int), ("lambda_", ctypes.c_float), ("clamp01", ctypes.c_int), ("level", ctypes.c_int),
                 ("selection", ctypes.c_int), ("lambda_s", ctypes.c_float)]
+
+
+class RlBatchItem(ctypes.Structure):
+    _fields_ = [("mpi", ctypes.POINTER(RlMpi)), ("images", ctypes.c_void_p), ("src", ctypes.POINTER(RlCamera)),
+                ("N", ctypes.c_int), ("params", RlHsgdParams), ("loss_out", ctypes.c_void_p), ("ws", ctypes.c_void_p),
+                ("ws_bytes", ctypes.c_size_t)]
 
 
 class RlLgdParams(ctypes.Structure):
@@ -104,6 +111,9 @@ def _declare(lib):
         "reallife_gradient_volume_workspace_bytes": (c_size_t, [c_int, c_int, c_int, c_int, c_int, c_int]),
         "reallife_gradient_volume": (c_int, [mpi_p, vp, cam_p, c_int, c_int, c_int, c_int, vp, vp, vp, c_size_t,
                                              vp]),
+        "reallife_batch_table_bytes": (c_size_t, [c_int]),
+        "reallife_batch_prepare": (c_int, [ctypes.POINTER(RlBatchItem), c_int, vp, c_size_t]),
+        "reallife_hsgd_step_batch": (c_int, [vp, vp, c_size_t, vp]),
         "reallife_lgd_net_bytes": (c_size_t, []),
         "reallife_lgd_prepare": (c_int, [ctypes.POINTER(RlLgdParams), vp, vp]),
         "reallife_lgd_workspace_bytes": (c_size_t, [c_int, c_int, c_int]),

@@ -13,6 +13,8 @@
 // Sparse mode adds only into voxels kept by the selection (Sec. 3.3): the slot map
 // slots[d][y][x] gives the compact slot of a kept voxel (its rank among the kept planes of
 // the pixel) or RL_SLOT_NONE.  No division by (1 - alpha).
+#include <type_traits>
+
 #include "rl_internal.h"
 
 namespace {
@@ -64,18 +66,16 @@ __device__ __forceinline__ void scatter4(float* __restrict__ G, const uint8_t* _
     scatter_tap<SPARSE>(G, slots_d, d, hw, H, W, t.x0 + 1, t.y0 + 1, w11, g);
 }
 
+// One block's tile of 32 x 4 view pixels of one view.  bid / nblocks index the block among
+// the launch's (or the batch item's) blocks for the loss epilogue.
 template <typename Tm, bool SPARSE, bool LOSS>
-__global__ void __launch_bounds__(kGradThreads, RL_GRAD_MIN_BLOCKS)
-k_grad(const Tm* __restrict__ M, int D, int H, int W, const __grid_constant__ RLViews views, int tiles_x,
-       const float* __restrict__ images, int img_level, const float* __restrict__ grad_out,
-       const uint8_t* __restrict__ slots, float* __restrict__ G, float inv_n, float* __restrict__ partials,
-       float* __restrict__ loss_out, unsigned* __restrict__ counter, float loss_scale) {
-    extern __shared__ float sT[];  // [D][kGradThreads]
-    // view-fastest block order: the N views of a tile run together and share M through L2
-    const int tid = threadIdx.y * kGradBX + threadIdx.x;
-    const int view = blockIdx.x;  // grid (views, tiles_x, tiles_y)
-    const int qx = blockIdx.y * kGradBX + threadIdx.x;
-    const int qy = blockIdx.z * kGradBY + threadIdx.y;
+__device__ __forceinline__ void grad_tile(const Tm* __restrict__ M, int D, int H, int W, const RLViews& views, int view,
+                                          int qx, int qy, int tid, float* __restrict__ sT,
+                                          const float* __restrict__ images, int img_level,
+                                          const float* __restrict__ grad_out, const uint8_t* __restrict__ slots,
+                                          float* __restrict__ G, float inv_n, float* __restrict__ partials,
+                                          unsigned bid, unsigned nblocks, float* __restrict__ loss_out,
+                                          unsigned* __restrict__ counter, float loss_scale) {
     float lsum = 0.f;
     if (qx < W && qy < H) {
         const RLWarp w = rl_warp_coeffs(views.v[view], (float)qx, (float)qy);
@@ -149,8 +149,53 @@ k_grad(const Tm* __restrict__ M, int D, int H, int W, const __grid_constant__ RL
         if (tid == 0)
             for (int j = 0; j < kGradThreads / 32; ++j) blk += red[j];
         __syncthreads();
-        rl_loss_epilogue(blk, partials, blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z),
-                         gridDim.x * gridDim.y * gridDim.z, loss_out, counter, loss_scale, tid, kGradThreads, red);
+        rl_loss_epilogue(blk, partials, bid, nblocks, loss_out, counter, loss_scale, tid, kGradThreads, red);
+    }
+}
+
+template <typename Tm, bool SPARSE, bool LOSS>
+__global__ void __launch_bounds__(kGradThreads, RL_GRAD_MIN_BLOCKS)
+k_grad(const Tm* __restrict__ M, int D, int H, int W, const __grid_constant__ RLViews views, int tiles_x,
+       const float* __restrict__ images, int img_level, const float* __restrict__ grad_out,
+       const uint8_t* __restrict__ slots, float* __restrict__ G, float inv_n, float* __restrict__ partials,
+       float* __restrict__ loss_out, unsigned* __restrict__ counter, float loss_scale) {
+    extern __shared__ float sT[];  // [D][kGradThreads]
+    // view-fastest block order: the N views of a tile run together and share M through L2
+    grad_tile<Tm, SPARSE, LOSS>(M, D, H, W, views, blockIdx.x, blockIdx.y * kGradBX + threadIdx.x,
+                                blockIdx.z * kGradBY + threadIdx.y, threadIdx.y * kGradBX + threadIdx.x, sT, images,
+                                img_level, grad_out, slots, G, inv_n, partials,
+                                blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z),
+                                gridDim.x * gridDim.y * gridDim.z, loss_out, counter, loss_scale);
+}
+
+// Batched gradient, per-pixel gather family: one persistent launch walks the gradient units of
+// the batch table's items that take this family (a unit is one 32 x 4 tile of one view of one
+// item, in the order of k_grad's grid), each item with its own loss epilogue over its own
+// units.  The dynamic shared memory holds `planes` planes; an item with more sets the batch bit
+// of the status word and is skipped.
+template <typename Tm>
+__global__ void __launch_bounds__(kGradThreads, RL_GRAD_MIN_BLOCKS)
+k_grad_batch(const RLBatchHeader* __restrict__ hdr, const RLBatchItem* __restrict__ items, int planes) {
+    extern __shared__ float sT[];  // [planes][kGradThreads]
+    const unsigned n = hdr->n, total = hdr->grad_units;
+    if (hdr->dtype != (std::is_same<Tm, float>::value ? (unsigned)RL_F32 : (unsigned)RL_BF16)) return;
+    const int tid = threadIdx.y * kGradBX + threadIdx.x;
+    __shared__ unsigned next_slot;
+    for (unsigned u = rl_batch_next(hdr, 1, &next_slot); u < total; u = rl_batch_next(hdr, 1, &next_slot)) {
+        const RLBatchItem& it = items[rl_batch_find(items, n, u, &RLBatchItem::grad_begin)];
+        if (it.D > planes) {
+            if (tid == 0 && hdr->status) atomicOr(hdr->status, RL_DEVFLAG_BATCH);
+            continue;
+        }
+        const unsigned local = u - it.grad_begin;
+        const unsigned view = local % (unsigned)it.N, tile = local / (unsigned)it.N;
+        const int tx = (int)(tile % it.grad_tiles_x), ty = (int)(tile / it.grad_tiles_x);
+        const int h = it.H >> it.level, w = it.W >> it.level;
+        grad_tile<Tm, true, true>(static_cast<const Tm*>(it.Ml), it.D, h, w, it.views, (int)view,
+                                  tx * kGradBX + threadIdx.x, ty * kGradBY + threadIdx.y, tid, sT, it.images,
+                                  it.level, nullptr, it.slots, it.G, it.inv_n, it.partials, local, it.grad_units,
+                                  it.loss_out, it.counter, it.loss_scale);
+        __syncthreads();  // sT is reused by the next unit
     }
 }
 
@@ -222,6 +267,28 @@ rl_status rl_launch_grad(const void* M, rl_dtype dt, int D, int H, int W, const 
     }
 #undef RL_GRAD_CASE
     return rl_check_launch("grad");
+}
+
+unsigned rl_grad_gather_tiles_x(int w) { return (unsigned)((w + kGradBX - 1) / kGradBX); }
+unsigned rl_grad_gather_tiles_y(int h) { return (unsigned)((h + kGradBY - 1) / kGradBY); }
+
+rl_status rl_launch_grad_batch(const void* table, rl_dtype dt, int planes, cudaStream_t s) {
+    const RLBatchHeader* hdr = static_cast<const RLBatchHeader*>(table);
+    const RLBatchItem* items = rl_batch_items(table);
+    planes = planes < 1 ? 1 : (planes > RL_DEV_MAX_PLANES ? RL_DEV_MAX_PLANES : planes);
+    const size_t smem = (size_t)planes * kGradThreads * sizeof(float);
+    // the resident blocks of the largest shared memory, so that any later capacity fits the grid
+    const size_t smem_max = (size_t)RL_DEV_MAX_PLANES * kGradThreads * sizeof(float);
+    const int grid = dt == RL_F32 ? rl_persistent_grid<k_grad_batch<float>>(kGradThreads, smem_max)
+                                  : rl_persistent_grid<k_grad_batch<__nv_bfloat16>>(kGradThreads, smem_max);
+    if (dt == RL_F32) {
+        RLTraceScope ts("grad_batch_f32", s);
+        k_grad_batch<float><<<grid, dim3(kGradBX, kGradBY), smem, s>>>(hdr, items, planes);
+    } else {
+        RLTraceScope ts("grad_batch_bf16", s);
+        k_grad_batch<__nv_bfloat16><<<grid, dim3(kGradBX, kGradBY), smem, s>>>(hdr, items, planes);
+    }
+    return rl_check_launch("grad_batch");
 }
 
 rl_status rl_launch_loss_reduce(const float* partials, int n, float scale, float* out, cudaStream_t s) {

@@ -15,6 +15,8 @@
 // T_d = Tb_g T_d^loc and the running below-composite B_d (B_{d+1} = c_d alpha_d + (1 -
 // alpha_d) B_d, starting from Bb_g) -- no division by (1 - alpha), no second gather.
 // Bilinear weights are applied with packed FP32x2 FMAs (same rounding as scalar FMAs).
+#include <type_traits>
+
 #include "rl_internal.h"
 
 namespace {
@@ -102,16 +104,20 @@ struct PixelCoord {
     bool active;
 };
 
-// grid (views, tiles_x, tiles_y): the views of a tile run together and share M in L2
-__device__ __forceinline__ PixelCoord pixel_coord(int H, int W) {
+__device__ __forceinline__ PixelCoord pixel_coord_at(int H, int W, int view, int tx, int ty) {
     PixelCoord c;
-    c.view = blockIdx.x;
+    c.view = view;
     c.g = threadIdx.x >> 5;
     c.lane = threadIdx.x & 31;
-    c.qx = blockIdx.y * kTX + (c.lane % kTX);
-    c.qy = blockIdx.z * kTY + (c.lane / kTX);
+    c.qx = tx * kTX + (c.lane % kTX);
+    c.qy = ty * kTY + (c.lane / kTX);
     c.active = c.qx < W && c.qy < H;
     return c;
+}
+
+// grid (views, tiles_x, tiles_y): the views of a tile run together and share M in L2
+__device__ __forceinline__ PixelCoord pixel_coord(int H, int W) {
+    return pixel_coord_at(H, W, blockIdx.x, blockIdx.y, blockIdx.z);
 }
 
 template <typename Tm, int C, int kGroups>
@@ -156,15 +162,16 @@ k_render_pp(const Tm* __restrict__ M, int D, int H, int W, const __grid_constant
     }
 }
 
+// One block's tile (kPix view pixels of one view, all planes): the body of k_grad_pp, with the
+// tile, the exchange buffers and the block's index for the loss epilogue given explicitly.
 template <typename Tm, int C, int kGroups, bool SPARSE, bool LOSS>
-__global__ void __launch_bounds__(kGroups * kPix)
-k_grad_pp(const Tm* __restrict__ M, int D, int H, int W, const __grid_constant__ RLViews views, int tiles_x,
-          const float* __restrict__ images, int img_level, const float* __restrict__ grad_out,
-          const uint8_t* __restrict__ slots, float* __restrict__ G, float inv_n, float* __restrict__ partials,
-          float* __restrict__ loss_out, unsigned* __restrict__ counter, float loss_scale) {
-    __shared__ float4 xch[kGroups][kPix];
-    __shared__ float red[kGroups];
-    const PixelCoord pc = pixel_coord(H, W);
+__device__ __forceinline__ void grad_pp_tile(const Tm* __restrict__ M, int D, int H, int W, const RLViews& views,
+                                             const PixelCoord pc, const float* __restrict__ images, int img_level,
+                                             const float* __restrict__ grad_out, const uint8_t* __restrict__ slots,
+                                             float* __restrict__ G, float inv_n, float* __restrict__ partials,
+                                             unsigned bid, unsigned nblocks, float* __restrict__ loss_out,
+                                             unsigned* __restrict__ counter, float loss_scale,
+                                             float4 (*__restrict__ xch)[kPix], float* __restrict__ red) {
     const int qx = min(pc.qx, W - 1), qy = min(pc.qy, H - 1);
     const RLWarp w = rl_warp_coeffs(views.v[pc.view], (float)qx, (float)qy);
     const size_t plane = (size_t)H * W * 4;
@@ -273,9 +280,56 @@ k_grad_pp(const Tm* __restrict__ M, int D, int H, int W, const __grid_constant__
         if (threadIdx.x == 0)
             for (int i = 0; i < kGroups; ++i) blk += red[i];
         __syncthreads();
-        rl_loss_epilogue(blk, partials, blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z),
-                         gridDim.x * gridDim.y * gridDim.z, loss_out, counter, loss_scale, threadIdx.x,
-                         kGroups * kPix, red);
+        rl_loss_epilogue(blk, partials, bid, nblocks, loss_out, counter, loss_scale, threadIdx.x, kGroups * kPix,
+                         red);
+    }
+}
+
+template <typename Tm, int C, int kGroups, bool SPARSE, bool LOSS>
+__global__ void __launch_bounds__(kGroups * kPix)
+k_grad_pp(const Tm* __restrict__ M, int D, int H, int W, const __grid_constant__ RLViews views, int tiles_x,
+          const float* __restrict__ images, int img_level, const float* __restrict__ grad_out,
+          const uint8_t* __restrict__ slots, float* __restrict__ G, float inv_n, float* __restrict__ partials,
+          float* __restrict__ loss_out, unsigned* __restrict__ counter, float loss_scale) {
+    __shared__ float4 xch[kGroups][kPix];
+    __shared__ float red[kGroups];
+    grad_pp_tile<Tm, C, kGroups, SPARSE, LOSS>(M, D, H, W, views, pixel_coord(H, W), images, img_level, grad_out,
+                                               slots, G, inv_n, partials,
+                                               blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z),
+                                               gridDim.x * gridDim.y * gridDim.z, loss_out, counter, loss_scale, xch,
+                                               red);
+}
+
+// Batched gradient, plane-parallel family: one persistent launch of 8-warp blocks walks the
+// gradient units of the batch table's items that take this family (a unit is one 16 x 2 tile of
+// one view of one item, in the order of k_grad_pp's grid; planes per thread from the item's D),
+// each item with its own loss epilogue over its own units.
+template <typename Tm>
+__global__ void __launch_bounds__(8 * kPix, 3)
+k_grad_pp_batch(const RLBatchHeader* __restrict__ hdr, const RLBatchItem* __restrict__ items) {
+    __shared__ float4 xch[8][kPix];
+    __shared__ float red[8];
+    const unsigned n = hdr->n, total = hdr->pp_units;
+    if (hdr->dtype != (std::is_same<Tm, float>::value ? (unsigned)RL_F32 : (unsigned)RL_BF16)) return;
+    __shared__ unsigned next_slot;
+    for (unsigned u = rl_batch_next(hdr, 2, &next_slot); u < total; u = rl_batch_next(hdr, 2, &next_slot)) {
+        const RLBatchItem& it = items[rl_batch_find(items, n, u, &RLBatchItem::pp_begin)];
+        const unsigned local = u - it.pp_begin;
+        const unsigned view = local % (unsigned)it.N, tile = local / (unsigned)it.N;
+        const int h = it.H >> it.level, w = it.W >> it.level;
+        const PixelCoord pc =
+            pixel_coord_at(h, w, (int)view, (int)(tile % it.pp_tiles_x), (int)(tile / it.pp_tiles_x));
+        const Tm* Ml = static_cast<const Tm*>(it.Ml);
+#define RL_PPB(CC) grad_pp_tile<Tm, CC, 8, true, true>(Ml, it.D, h, w, it.views, pc, it.images, it.level, nullptr, \
+                                                      it.slots, it.G, it.inv_n, it.partials, local, it.pp_units, \
+                                                      it.loss_out, it.counter, it.loss_scale, xch, red)
+        const int c = (it.D + 7) / 8;
+        if (c <= 1) RL_PPB(1);
+        else if (c <= 2) RL_PPB(2);
+        else if (c <= 4) RL_PPB(4);
+        else RL_PPB(8);
+#undef RL_PPB
+        __syncthreads();  // the exchange buffers are reused by the next unit
     }
 }
 
@@ -389,4 +443,22 @@ rl_status rl_launch_render_pp(const void* M, rl_dtype dt, int D, int H, int W, c
         launch_render_pp_t<__nv_bfloat16>(G, C, M, D, H, W, views, tiles_x, grid, out, s);
     }
     return rl_check_launch("render_pp");
+}
+
+unsigned rl_grad_pp_tiles_x(int w) { return (unsigned)((w + kTX - 1) / kTX); }
+unsigned rl_grad_pp_tiles_y(int h) { return (unsigned)((h + kTY - 1) / kTY); }
+
+rl_status rl_launch_grad_pp_batch(const void* table, rl_dtype dt, cudaStream_t s) {
+    const RLBatchHeader* hdr = static_cast<const RLBatchHeader*>(table);
+    const RLBatchItem* items = rl_batch_items(table);
+    const int grid = dt == RL_F32 ? rl_persistent_grid<k_grad_pp_batch<float>>(8 * kPix, 0)
+                                  : rl_persistent_grid<k_grad_pp_batch<__nv_bfloat16>>(8 * kPix, 0);
+    if (dt == RL_F32) {
+        RLTraceScope ts("grad_pp_batch_f32", s);
+        k_grad_pp_batch<float><<<grid, 8 * kPix, 0, s>>>(hdr, items);
+    } else {
+        RLTraceScope ts("grad_pp_batch_bf16", s);
+        k_grad_pp_batch<__nv_bfloat16><<<grid, 8 * kPix, 0, s>>>(hdr, items);
+    }
+    return rl_check_launch("grad_pp_batch");
 }

@@ -625,6 +625,141 @@ extern "C" rl_status reallife_warp_offsets(const rl_mpi* m, const rl_camera* vie
     return rl_launch_warp_offsets(m->D, m->H, m->W, views, out, stream);
 }
 
+// ------------------------------------------------------------- batched step
+
+extern "C" size_t reallife_batch_table_bytes(int max_items) {
+    if (max_items < 1 || max_items > RL_BATCH_MAX_ITEMS) return 0;
+    return align_up(sizeof(RLBatchHeader) + (size_t)max_items * sizeof(RLBatchItem));
+}
+
+namespace {
+bool ranges_overlap(uintptr_t a, size_t na, uintptr_t b, size_t nb) { return a < b + nb && b < a + na; }
+}  // namespace
+
+extern "C" rl_status reallife_batch_prepare(const rl_batch_item* items, int n, void* table_host, size_t table_bytes) {
+    if (!items || n < 1 || n > RL_BATCH_MAX_ITEMS)
+        return rl_fail(RL_EINVAL, "batch: n=%d outside [1, %d]", n, RL_BATCH_MAX_ITEMS);
+    if (!table_host) return rl_fail(RL_EINVAL, "batch: table_host is NULL");
+    if (table_bytes < reallife_batch_table_bytes(n))
+        return rl_fail(RL_ENOMEM, "batch: table of %zu bytes < %zu needed", table_bytes, reallife_batch_table_bytes(n));
+    RLBatchHeader* hdr = static_cast<RLBatchHeader*>(table_host);
+    RLBatchItem* out = const_cast<RLBatchItem*>(rl_batch_items(table_host));
+    std::memset(hdr, 0, sizeof(*hdr));
+    unsigned sel = 0, grad = 0, pp = 0, upd = 0, max_gather_D = 0;
+    for (int i = 0; i < n; ++i) {
+        const rl_batch_item& b = items[i];
+        const rl_hsgd_params* p = &b.params;
+        rl_status st = check_hsgd(b.mpi, b.images, b.src, b.N, p, p->level, b.ws, b.ws_bytes);
+        if (st) return rl_fail(st, "batch item %d: %s", i, reallife_last_error());
+        const rl_mpi* m = b.mpi;
+        if (m->dtype != items[0].mpi->dtype) return rl_fail(RL_EINVAL, "batch item %d: storage type differs", i);
+        const size_t mb = (size_t)m->D * m->H * m->W * 4 * elt_size(m->dtype);
+        const WsLayout L = ws_layout(b.N, m->D, m->H, m->W, p->k, m->dtype);
+        for (int j = 0; j < i; ++j) {
+            const rl_mpi* o = items[j].mpi;
+            const size_t ob = (size_t)o->D * o->H * o->W * 4 * elt_size(o->dtype);
+            const size_t ow = ws_layout(items[j].N, o->D, o->H, o->W, items[j].params.k, o->dtype).total;
+            if (ranges_overlap((uintptr_t)m->data, mb, (uintptr_t)o->data, ob) ||
+                ranges_overlap((uintptr_t)b.ws, L.total, (uintptr_t)items[j].ws, ow) ||
+                ranges_overlap((uintptr_t)m->data, mb, (uintptr_t)items[j].ws, ow) ||
+                ranges_overlap((uintptr_t)b.ws, L.total, (uintptr_t)o->data, ob))
+                return rl_fail(RL_EINVAL, "batch items %d and %d share an MPI or workspace", j, i);
+        }
+        RLBatchItem& it = out[i];
+        std::memset(&it, 0, sizeof(it));
+        st = make_views(m, b.src, b.N, p->level, it.views);
+        if (st) return rl_fail(st, "batch item %d: %s", i, reallife_last_error());
+        char* base = static_cast<char*>(b.ws);
+        const int l = p->level, h = m->H >> l, w = m->W >> l;
+        it.M = m->data;
+        it.Ml = l == 0 ? m->data : (void*)(base + L.Ml);
+        it.images = b.images;
+        it.S = (uint8_t*)(base + L.S);
+        it.slots = (uint8_t*)(base + L.slots);
+        it.G = (float*)(base + L.G);
+        it.partials = (float*)(base + L.partials);
+        it.counter = (unsigned*)(base + L.counter);
+        it.loss_out = b.loss_out;
+        it.D = m->D;
+        it.H = m->H;
+        it.W = m->W;
+        it.level = l;
+        it.k = p->k;
+        it.mode = p->selection;
+        it.clamp01 = p->clamp01;
+        it.N = b.N;
+        it.lambda = p->lambda;
+        it.prior_scale = p->lambda_s != 0.f ? (float)((double)p->lambda_s / ((double)h * w * m->D)) : 0.f;
+        it.inv_n = 1.0f / (float)b.N;
+        it.loss_scale = 0.5f / (float)b.N;
+        const unsigned hw = (unsigned)(h * w);
+        it.sel_begin = sel;
+        it.sel_units = l == 0 ? (hw + 255) / 256 : (hw + 31) / 32;
+        const bool gather = rl_kernel_path(h, w, b.N) == 2;
+        it.grad_begin = grad;
+        it.pp_begin = pp;
+        if (gather) {
+            it.grad_tiles_x = rl_grad_gather_tiles_x(w);
+            it.grad_units = (unsigned)b.N * it.grad_tiles_x * rl_grad_gather_tiles_y(h);
+            max_gather_D = std::max(max_gather_D, (unsigned)m->D);
+        } else {
+            it.pp_tiles_x = rl_grad_pp_tiles_x(w);
+            it.pp_units = (unsigned)b.N * it.pp_tiles_x * rl_grad_pp_tiles_y(h);
+        }
+        it.upd_begin = upd;
+        it.upd_tiles_x = (unsigned)((m->W + 127) / 128);
+        it.upd_units = it.upd_tiles_x * (unsigned)m->H;
+        sel += it.sel_units;
+        grad += it.grad_units;
+        pp += it.pp_units;
+        upd += it.upd_units;
+    }
+    hdr->n = (unsigned)n;
+    hdr->dtype = (unsigned)items[0].mpi->dtype;
+    hdr->sel_units = sel;
+    hdr->grad_units = grad;
+    hdr->pp_units = pp;
+    hdr->max_gather_D = max_gather_D;
+    hdr->upd_units = upd;
+    hdr->status = rl_device_status_ptr();
+    return RL_OK;
+}
+
+extern "C" rl_status reallife_hsgd_step_batch(const void* table_host, void* table_dev, size_t table_bytes,
+                                              cudaStream_t stream) {
+    if (!table_host || !table_dev) return rl_fail(RL_EINVAL, "batch: NULL table");
+    if (((uintptr_t)table_dev & 255) != 0) return rl_fail(RL_EINVAL, "batch: table_dev must be 256-byte aligned");
+    const RLBatchHeader* hdr = static_cast<const RLBatchHeader*>(table_host);
+    if (hdr->n < 1 || hdr->n > RL_BATCH_MAX_ITEMS || (hdr->dtype != RL_F32 && hdr->dtype != RL_BF16))
+        return rl_fail(RL_EINVAL, "batch: the table was not written by reallife_batch_prepare");
+    if (table_bytes < reallife_batch_table_bytes((int)hdr->n))
+        return rl_fail(RL_ENOMEM, "batch: table of %zu bytes < %zu needed", table_bytes,
+                       reallife_batch_table_bytes((int)hdr->n));
+    if (!capturing(stream)) {  // while capturing, a copy from pageable memory fails at the copy itself
+        cudaPointerAttributes pa;
+        if (cudaPointerGetAttributes(&pa, table_host) != cudaSuccess || pa.type != cudaMemoryTypeHost) {
+            cudaGetLastError();
+            return rl_fail(RL_EINVAL, "batch: table_host must be page-locked host memory");
+        }
+    }
+    const rl_dtype dt = (rl_dtype)hdr->dtype;
+    cudaError_t e = cudaMemcpyAsync(table_dev, table_host, table_bytes, cudaMemcpyHostToDevice, stream);
+    if (e != cudaSuccess) return rl_fail(RL_ECUDA, "batch: table copy: %s", cudaGetErrorString(e));
+    rl_status st = rl_launch_select_batch(table_dev, dt, stream);
+    if (st) return st;
+    // a captured launch may later serve a table of larger planes: reserve the most then
+    const int planes = capturing(stream) ? RL_DEV_MAX_PLANES : (int)hdr->max_gather_D;
+    if (hdr->grad_units || capturing(stream)) {
+        st = rl_launch_grad_batch(table_dev, dt, planes, stream);
+        if (st) return st;
+    }
+    if (hdr->pp_units || capturing(stream)) {
+        st = rl_launch_grad_pp_batch(table_dev, dt, stream);
+        if (st) return st;
+    }
+    return rl_launch_update_batch(table_dev, dt, stream);
+}
+
 // ------------------------------------------------------ fixed-scratch HSGD step
 //
 // Some callers cannot allocate device memory at all: a plugin running inside a host

@@ -35,6 +35,72 @@ struct RLViews {
     RLViewParam v[RL_DEV_MAX_VIEWS];
 };
 
+// ------------------------------------------------------------------ batch work tables
+//
+// A batch table serves one HSGD iteration of many requests in one launch per stage
+// (selection, gradient, update).  It is a header followed by one item per request, in device
+// memory; the persistent batched kernels take fixed grids and walk the work units of all items
+// (a unit is one block's worth of work of one item), so one captured launch serves any table.
+
+#define RL_DEVFLAG_BATCH 2u  // a batched kernel was given a table of another storage type
+
+struct RLBatchHeader {
+    unsigned n;                                // items
+    unsigned dtype;                            // rl_dtype of every item's MPI
+    unsigned sel_units, grad_units, upd_units;  // work units of the stages (gradient: gather family)
+    unsigned pp_units;                         // gradient units of the plane-parallel family
+    unsigned int* status;                      // device status word
+    unsigned max_gather_D;                     // largest D among the gather family's items
+    unsigned next[4];                          // next unit of each launch (0 in the copied table)
+    unsigned pad1[3];
+};
+
+// The next work unit of a persistent batched launch for the calling block: taken from the
+// launch's counter in the table header, so that blocks finishing early take more units.
+// Every thread of the block calls it; `slot` is block-shared scratch.
+__device__ __forceinline__ unsigned rl_batch_next(const RLBatchHeader* hdr, int which, unsigned* slot) {
+    __syncthreads();  // the previous unit's readers of *slot are done
+    if (threadIdx.x == 0 && threadIdx.y == 0)
+        *slot = atomicAdd(const_cast<unsigned*>(&hdr->next[which]), 1u);
+    __syncthreads();
+    return *slot;
+}
+
+struct RLBatchItem {
+    void* M;                 // full-resolution MPI [D][H][W][4], refined in place
+    void* Ml;                // level-l MPI (M itself at level 0)
+    const float* images;     // full-resolution source images [N][H][W][3]
+    uint8_t* S;              // selection [k][h][w]
+    uint8_t* slots;          // slot map [D][h][w]
+    float* G;                // compact gradient [k][h][w][4]
+    float* partials;         // loss partials, one per gradient unit
+    unsigned* counter;       // last-block counter of the loss epilogue
+    float* loss_out;         // device [1] or NULL
+    int D, H, W, level, k, mode, clamp01, N;
+    float lambda, prior_scale, inv_n, loss_scale;
+    unsigned sel_begin, sel_units;    // first unit and unit count of each stage
+    unsigned grad_begin, grad_units, grad_tiles_x;   // gather family (units 0 for the other items)
+    unsigned pp_begin, pp_units, pp_tiles_x;         // plane-parallel family (units 0 for the others)
+    unsigned upd_begin, upd_units, upd_tiles_x, pad;
+    RLViews views;           // level-l warp parameters of the N views and the plane inverse depths
+};
+
+__host__ __device__ inline const RLBatchItem* rl_batch_items(const void* table) {
+    return reinterpret_cast<const RLBatchItem*>(static_cast<const char*>(table) + sizeof(RLBatchHeader));
+}
+
+// Item owning work unit u of a stage whose first units are items[i].*begin (ascending).
+__device__ __forceinline__ unsigned rl_batch_find(const RLBatchItem* __restrict__ items, unsigned n, unsigned u,
+                                                  unsigned RLBatchItem::*begin) {
+    unsigned lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const unsigned mid = (lo + hi + 1) >> 1;
+        if (items[mid].*begin <= u) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
 // Per-pixel warp coefficients of one view.
 struct RLWarp {
     float ax, ay, bx, by, cz;

@@ -112,6 +112,38 @@ rl_status rl_launch_update(void* M, rl_dtype dt, int D, int H, int W, int level,
                            int k, float lambda, int clamp01, cudaStream_t s, const void* Ml = nullptr,
                            float lambda_s = 0.f);
 
+// Batched stages of one HSGD iteration over a batch table in device memory (header and items
+// of rl_common.cuh), each one persistent launch of one wave of resident blocks.  The gradient
+// stage is two launches: the items that rl_kernel_path sends to the per-pixel gather family
+// (shared memory for `planes` planes) and those it sends to the plane-parallel family.
+rl_status rl_launch_select_batch(const void* table, rl_dtype dt, cudaStream_t s);
+rl_status rl_launch_grad_batch(const void* table, rl_dtype dt, int planes, cudaStream_t s);
+rl_status rl_launch_grad_pp_batch(const void* table, rl_dtype dt, cudaStream_t s);
+rl_status rl_launch_update_batch(const void* table, rl_dtype dt, cudaStream_t s);
+unsigned rl_grad_gather_tiles_x(int w);
+unsigned rl_grad_gather_tiles_y(int h);
+unsigned rl_grad_pp_tiles_x(int w);
+unsigned rl_grad_pp_tiles_y(int h);
+
+// Blocks of a persistent launch of `kernel`: the resident blocks per SM on the current device
+// times its SMs (at least one); computed once per device and kernel instantiation.
+template <auto kernel>
+inline int rl_persistent_grid(int threads, size_t smem) {
+    static int cached[64] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const bool cacheable = dev >= 0 && dev < 64;
+    if (cacheable && cached[dev]) return cached[dev];
+    int sms = 0, per = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, threads, smem) != cudaSuccess) cudaGetLastError();
+    const int grid = (sms > 0 ? sms : 1) * (per > 0 ? per : 1);
+    if (cacheable) cached[dev] = grid;
+    return grid;
+}
+unsigned rl_grad_batch_tiles_x(int w);
+unsigned rl_grad_batch_tiles_y(int h);
+
 // Alpha weights of the MPI warped into each view (Eq. eq_gradient): A device [N][D][H][W].
 rl_status rl_launch_view_alpha(const void* M, rl_dtype dt, int D, int H, int W, const RLViews& views, float* A,
                                cudaStream_t s);

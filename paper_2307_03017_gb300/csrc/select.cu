@@ -18,6 +18,8 @@
 // (ties to the lower d), shifted to stay within [0, D).
 // On the coarse levels of an HSGD step the pyramid and the selection run as one kernel: the
 // level voxels of a tile of pixels go to Ml and, through shared memory, to the selection.
+#include <type_traits>
+
 #include "rl_internal.h"
 
 namespace {
@@ -26,7 +28,8 @@ __device__ __forceinline__ bool beats(float a, int ia, float b, int ib) { return
 
 // Per-pixel selection.  raw_at(d) gives alpha_d (keys mode: the key of plane d).  Returns the
 // 64-bit mask of the kept planes.
-//   K <= 8: a register-resident list sorted by (key descending, d ascending).  The walk
+//   K <= 8: a register-resident list of the K best, sorted by (key descending, d ascending);
+//   its first k <= K entries are kept.  The walk
 //   visits the planes in descending d, so a new plane is below every listed one and wins
 //   every tie: it enters iff key >= the last listed key, and the insertion is a chain of
 //   `>=` compare-exchanges.  Planes that cannot enter cost one comparison.
@@ -97,8 +100,10 @@ __device__ __forceinline__ uint64_t select_mask(const RawFn& raw_at, int D, int 
         start = max(0, min(start, D - k));
         mk = (k >= 64 ? ~0ull : ((1ull << k) - 1ull)) << start;
     } else if constexpr (SMALL) {
+        // the list holds the top K in order; its first k entries are the top k (k <= K)
 #pragma unroll
-        for (int j = 0; j < K; ++j) mk |= 1ull << ki[j];
+        for (int j = 0; j < K; ++j)
+            if (j < k) mk |= 1ull << ki[j];
     } else {
         for (int d = 0; d < D; ++d) {
             int rank = 0;
@@ -189,14 +194,13 @@ __device__ __forceinline__ float4 pyramid_mean(const Tm* __restrict__ M, int H, 
 constexpr int kTile = 32;
 
 template <typename Tm, int K, int LOG>
-__global__ void __launch_bounds__(256)
-k_pyramid_select(const Tm* __restrict__ M, int D, int H, int W, int level, Tm* __restrict__ Ml, int k,
-                 uint8_t* __restrict__ S, uint8_t* __restrict__ slots, float* __restrict__ Gzero,
-                 unsigned* __restrict__ counter_zero, int mode) {
-    __shared__ float alpha[RL_DEV_MAX_PLANES][kTile];
+__device__ __forceinline__ void pyramid_select_tile(const Tm* __restrict__ M, int D, int H, int W, int level,
+                                                    Tm* __restrict__ Ml, int k, uint8_t* __restrict__ S,
+                                                    uint8_t* __restrict__ slots, float* __restrict__ Gzero,
+                                                    unsigned* __restrict__ counter_zero, int mode, long long p0,
+                                                    float (*alpha)[kTile]) {
     const int h = H >> level, w = W >> level;
     const long long hw = (long long)h * w;
-    const long long p0 = (long long)blockIdx.x * kTile;
     if (p0 == 0 && threadIdx.x == 0 && counter_zero) *counter_zero = 0u;
     // level 1: the loads of NB voxels (4 full-resolution voxels each) are issued together
     constexpr int NB = LOG == 1 ? 4 : 1;
@@ -222,9 +226,87 @@ k_pyramid_select(const Tm* __restrict__ M, int D, int H, int W, int level, Tm* _
     __syncthreads();
     const int j = threadIdx.x;
     const long long p = p0 + j;
-    if (j >= kTile || p >= hw) return;
-    const uint64_t mk = select_mask<K, false>([&](int d) { return alpha[d][j]; }, D, k, mode);
-    write_selection(mk, D, k, hw, p, S, nullptr, slots, Gzero);
+    if (j < kTile && p < hw) {
+        const uint64_t mk = select_mask<K, false>([&](int d) { return alpha[d][j]; }, D, k, mode);
+        write_selection(mk, D, k, hw, p, S, nullptr, slots, Gzero);
+    }
+}
+
+template <typename Tm, int K, int LOG>
+__global__ void __launch_bounds__(256)
+k_pyramid_select(const Tm* __restrict__ M, int D, int H, int W, int level, Tm* __restrict__ Ml, int k,
+                 uint8_t* __restrict__ S, uint8_t* __restrict__ slots, float* __restrict__ Gzero,
+                 unsigned* __restrict__ counter_zero, int mode) {
+    __shared__ float alpha[RL_DEV_MAX_PLANES][kTile];
+    pyramid_select_tile<Tm, K, LOG>(M, D, H, W, level, Ml, k, S, slots, Gzero, counter_zero, mode,
+                                    (long long)blockIdx.x * kTile, alpha);
+}
+
+// ------------------------------------------------------------------ batched selection
+//
+// One persistent launch selects for every item of a batch table (the selection stage of one
+// HSGD iteration of each request): a unit is 256 level-0 pixels (one a thread, as k_select)
+// or one 32-pixel pyramid tile (as k_pyramid_select) of one item.  The list holds 8 keys for
+// k <= 8 (its first k entries are kept), so one instantiation serves every k; the rank-count
+// selection of k > 8 is kept out of line so that the common path keeps few registers.
+template <typename Tm>
+__device__ __noinline__ uint64_t select_l0_ranked(const Tm* __restrict__ M, long long hw, long long p, int D, int k,
+                                                 int mode) {
+    return select_mask<64, false>([&](int d) { return RLStore<Tm>::load1(M + ((size_t)d * hw + p) * 4 + 3); }, D, k,
+                                  mode);
+}
+
+template <typename Tm, int LOG>
+__device__ __noinline__ void pyramid_select_tile_ranked(const Tm* __restrict__ M, int D, int H, int W, int level,
+                                                        Tm* __restrict__ Ml, int k, uint8_t* __restrict__ S,
+                                                        uint8_t* __restrict__ slots, float* __restrict__ Gzero,
+                                                        unsigned* __restrict__ counter_zero, int mode, long long p0,
+                                                        float (*alpha)[kTile]) {
+    pyramid_select_tile<Tm, 64, LOG>(M, D, H, W, level, Ml, k, S, slots, Gzero, counter_zero, mode, p0, alpha);
+}
+
+template <typename Tm>
+__global__ void __launch_bounds__(256, 4)
+k_select_batch(const RLBatchHeader* __restrict__ hdr, const RLBatchItem* __restrict__ items) {
+    __shared__ float alpha[RL_DEV_MAX_PLANES][kTile];
+    const unsigned n = hdr->n, total = hdr->sel_units;
+    if (hdr->dtype != (std::is_same<Tm, float>::value ? (unsigned)RL_F32 : (unsigned)RL_BF16)) {
+        if (blockIdx.x == 0 && threadIdx.x == 0 && hdr->status) atomicOr(hdr->status, RL_DEVFLAG_BATCH);
+        return;
+    }
+    __shared__ unsigned next_slot;
+    for (unsigned u = rl_batch_next(hdr, 0, &next_slot); u < total; u = rl_batch_next(hdr, 0, &next_slot)) {
+        const RLBatchItem& it = items[rl_batch_find(items, n, u, &RLBatchItem::sel_begin)];
+        const long long local = (long long)(u - it.sel_begin);
+        const bool ranked = it.mode != 1 && it.k > 8;
+        const Tm* M = static_cast<const Tm*>(it.M);
+        if (it.level == 0) {
+            const long long hw = (long long)it.H * it.W;
+            const long long p = local * 256 + threadIdx.x;
+            if (p == 0) *it.counter = 0u;  // block counter of the loss epilogue that follows
+            if (p < hw) {
+                const uint64_t mk =
+                    ranked ? select_l0_ranked<Tm>(M, hw, p, it.D, it.k, it.mode)
+                           : select_mask<8, false>([&](int d) { return RLStore<Tm>::load1(M + ((size_t)d * hw + p) * 4 + 3); },
+                                                   it.D, it.k, it.mode);
+                write_selection(mk, it.D, it.k, hw, p, it.S, nullptr, it.slots, it.G);
+            }
+        } else {
+            Tm* Ml = static_cast<Tm*>(it.Ml);
+#define RL_PSB(LL)                                                                                                 \
+    if (ranked)                                                                                                    \
+        pyramid_select_tile_ranked<Tm, LL>(M, it.D, it.H, it.W, it.level, Ml, it.k, it.S, it.slots, it.G, it.counter, \
+                                           it.mode, local * kTile, alpha);                                         \
+    else                                                                                                           \
+        pyramid_select_tile<Tm, 8, LL>(M, it.D, it.H, it.W, it.level, Ml, it.k, it.S, it.slots, it.G, it.counter,     \
+                                       it.mode, local * kTile, alpha)
+            if (it.level == 1) { RL_PSB(1); }
+            else if (it.level == 2) { RL_PSB(2); }
+            else { RL_PSB(-1); }
+#undef RL_PSB
+        }
+        __syncthreads();  // alpha is reused by the next unit
+    }
 }
 
 template <typename Tm, bool FROM_KEYS>
@@ -343,6 +425,21 @@ rl_status rl_launch_pyramid_select(const void* M, rl_dtype dt, int D, int H, int
         launch_pyramid_select_t<__nv_bfloat16>(M, D, H, W, level, Ml, k, S, slots, Gzero, counter_zero, mode, s);
     }
     return rl_check_launch("pyramid_select");
+}
+
+rl_status rl_launch_select_batch(const void* table, rl_dtype dt, cudaStream_t s) {
+    const RLBatchHeader* hdr = static_cast<const RLBatchHeader*>(table);
+    const RLBatchItem* items = rl_batch_items(table);
+    const int grid = dt == RL_F32 ? rl_persistent_grid<k_select_batch<float>>(256, 0)
+                                  : rl_persistent_grid<k_select_batch<__nv_bfloat16>>(256, 0);
+    if (dt == RL_F32) {
+        RLTraceScope ts("select_batch_f32", s);
+        k_select_batch<float><<<grid, 256, 0, s>>>(hdr, items);
+    } else {
+        RLTraceScope ts("select_batch_bf16", s);
+        k_select_batch<__nv_bfloat16><<<grid, 256, 0, s>>>(hdr, items);
+    }
+    return rl_check_launch("select_batch");
 }
 
 rl_status rl_launch_mask_to_slots(const uint64_t* mask, int D, int hw, uint8_t* slots, cudaStream_t s) {

@@ -7,17 +7,18 @@
 // Only k of the D planes are read and written.  With lambda_s != 0 the sparsity prior of
 // Sec. 3.4 joins the alpha step: lambda_s sign(0.5 - a) / ((1.5 - |0.5 - a|) h w D), with a
 // the alpha of the level MPI Ml.
+#include <type_traits>
+
 #include "rl_internal.h"
 
 namespace {
 
 template <typename Tm>
-__global__ void __launch_bounds__(128)
-k_update(Tm* __restrict__ M, int D, int H, int W, int level, const uint8_t* __restrict__ S,
-         const float* __restrict__ G, int k, float lambda, int clamp01, const Tm* __restrict__ Ml, float prior_scale) {
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    const int y = blockIdx.y;
-    if (x >= W) return;
+__device__ __forceinline__ void update_pixel(Tm* __restrict__ M, int D, int H, int W, int level,
+                                             const uint8_t* __restrict__ S, const float* __restrict__ G, int k,
+                                             float lambda, int clamp01, const Tm* __restrict__ Ml, float prior_scale,
+                                             int x, int y) {
+    if (x >= W || y >= H) return;
     const int w = W >> level, h = H >> level;
     const size_t hw = (size_t)h * w;
     const size_t p = (size_t)(y >> level) * w + (x >> level);
@@ -46,6 +47,31 @@ k_update(Tm* __restrict__ M, int D, int H, int W, int level, const uint8_t* __re
     }
 }
 
+template <typename Tm>
+__global__ void __launch_bounds__(128)
+k_update(Tm* __restrict__ M, int D, int H, int W, int level, const uint8_t* __restrict__ S,
+         const float* __restrict__ G, int k, float lambda, int clamp01, const Tm* __restrict__ Ml, float prior_scale) {
+    update_pixel<Tm>(M, D, H, W, level, S, G, k, lambda, clamp01, Ml, prior_scale, blockIdx.x * blockDim.x + threadIdx.x,
+                     blockIdx.y);
+}
+
+// Batched update: one persistent launch walks the update units of every item of a batch table
+// (a unit is 128 pixels of one full-resolution row of one item, as k_update's grid).
+template <typename Tm>
+__global__ void __launch_bounds__(128)
+k_update_batch(const RLBatchHeader* __restrict__ hdr, const RLBatchItem* __restrict__ items) {
+    const unsigned n = hdr->n, total = hdr->upd_units;
+    if (hdr->dtype != (std::is_same<Tm, float>::value ? (unsigned)RL_F32 : (unsigned)RL_BF16)) return;
+    __shared__ unsigned next_slot;
+    for (unsigned u = rl_batch_next(hdr, 3, &next_slot); u < total; u = rl_batch_next(hdr, 3, &next_slot)) {
+        const RLBatchItem& it = items[rl_batch_find(items, n, u, &RLBatchItem::upd_begin)];
+        const unsigned local = u - it.upd_begin;
+        const int x = (int)(local % it.upd_tiles_x) * 128 + threadIdx.x, y = (int)(local / it.upd_tiles_x);
+        update_pixel<Tm>(static_cast<Tm*>(it.M), it.D, it.H, it.W, it.level, it.S, it.G, it.k, it.lambda, it.clamp01,
+                         static_cast<const Tm*>(it.Ml), it.prior_scale, x, y);
+    }
+}
+
 }  // namespace
 
 rl_status rl_launch_update(void* M, rl_dtype dt, int D, int H, int W, int level, const uint8_t* S, const float* G,
@@ -64,4 +90,19 @@ rl_status rl_launch_update(void* M, rl_dtype dt, int D, int H, int W, int level,
                                                      (const __nv_bfloat16*)Ml, prior_scale);
     }
     return rl_check_launch("update");
+}
+
+rl_status rl_launch_update_batch(const void* table, rl_dtype dt, cudaStream_t s) {
+    const RLBatchHeader* hdr = static_cast<const RLBatchHeader*>(table);
+    const RLBatchItem* items = rl_batch_items(table);
+    const int grid = dt == RL_F32 ? rl_persistent_grid<k_update_batch<float>>(128, 0)
+                                  : rl_persistent_grid<k_update_batch<__nv_bfloat16>>(128, 0);
+    if (dt == RL_F32) {
+        RLTraceScope ts("update_batch_f32", s);
+        k_update_batch<float><<<grid, 128, 0, s>>>(hdr, items);
+    } else {
+        RLTraceScope ts("update_batch_bf16", s);
+        k_update_batch<__nv_bfloat16><<<grid, 128, 0, s>>>(hdr, items);
+    }
+    return rl_check_launch("update_batch");
 }

@@ -16,8 +16,19 @@ concurrent requests overlaps on the device.
   (slot, request shape, geometry) on buffers pinned to that slot, and replayed as a single
   launch for every later request with the same key in that slot.  The camera constants
   travel in the kernels' parameters, so a graph is only reused for identical geometry.
+- **Batched steps.** With ``batched=True`` the engine schedules by iteration instead: every
+  engine step runs the next HSGD iteration of every active request (each at its own level)
+  in one launch per stage through ``reallife_hsgd_step_batch``, whose work table lists the
+  requests.  Requests join at the next step after their inputs are copied in and leave after
+  their last iteration.  Requests go to ``lanes`` size classes (by pixels x planes x views),
+  each with its own stream and tables, so that small requests are not held behind the steps
+  of large ones.  A lane's table is double-buffered (page-locked host and device copies), at
+  most two of its steps are in flight, and with ``graphs=True`` each buffer's step is one
+  captured graph replayed with the table rewritten, whatever the requests' shapes and cameras.
 - **Latency.** A request's latency is the time from its arrival to the moment the host sees
   its result, including queueing and both copies.
+- **Oversized requests.** A request that needs more memory than the whole arena is never
+  admitted: it is marked failed (``req.error``) and returned with the others.
 """
 from __future__ import annotations
 
@@ -29,7 +40,8 @@ from dataclasses import dataclass, field
 import numpy as np
 import torch
 
-from . import make_mpi, reallife_refine, reallife_workspace_bytes
+from . import (BatchItem, BatchTable, batch_c_item, make_mpi, reallife_batch_prepare, reallife_hsgd_step_batch,
+               reallife_refine, reallife_workspace_bytes)
 
 ALIGN = 256
 
@@ -98,6 +110,7 @@ class Request:
     t_admit: float = -1.0
     t_done: float = -1.0
     slot: int = -1
+    error: str | None = None
     losses: np.ndarray | None = None
     result: torch.Tensor | None = None
     meta: dict = field(default_factory=dict)
@@ -129,10 +142,17 @@ class ServeEngine:
     """Admits requests by device memory into up to ``max_slots`` concurrent slots."""
 
     def __init__(self, arena_bytes: int, max_slots: int = 8, device="cuda", graphs: bool = False,
-                 keep_results: bool = False, max_result_elems: int = 0, result_dtype=torch.bfloat16):
+                 keep_results: bool = False, max_result_elems: int = 0, result_dtype=torch.bfloat16,
+                 batched: bool = False, lanes: int = 2, lane_split: int = 512 * 384 * 32 * 4):
         """``max_result_elems``: preallocate every slot's pinned result buffer for MPIs of up to
-        this many elements, so that no pinned allocation happens while serving."""
+        this many elements, so that no pinned allocation happens while serving.  ``batched``:
+        iteration-level scheduling with one batched launch per stage for all active requests."""
         self.device = torch.device(device)
+        self.batched = batched
+        self.lanes = max(1, int(lanes)) if batched else 1
+        self.lane_split = lane_split  # pixels x planes x views at which a request takes the next lane
+        self.steps = 0  # batched engine steps run
+        self.max_items_per_step = 0
         self.arena = DeviceArena(arena_bytes, self.device)
         self.max_slots = max_slots
         self.streams = [torch.cuda.Stream(device=self.device) for _ in range(max_slots)]
@@ -229,7 +249,19 @@ class ServeEngine:
     def run(self, requests, realtime: bool = True, poll_s: float = 20e-6):
         """Serve ``requests`` (sorted by arrival, seconds).  ``realtime``: admit a request no
         earlier than its arrival time; otherwise all are available at once (closed loop)."""
-        pending = collections.deque(sorted(requests, key=lambda r: r.arrival))
+        requests = sorted(requests, key=lambda r: r.arrival)
+        done = []
+        fits = []
+        for r in requests:
+            if request_bytes(*r.shape[:4], r.k, r.coarse.dtype) > self.arena.size:
+                r.error = "needs more device memory than the whole arena"
+                r.t_done = r.arrival
+                done.append(r)
+            else:
+                fits.append(r)
+        if self.batched:
+            return done + self._run_batched(fits, realtime, poll_s)
+        pending = collections.deque(fits)
         active = {}
         free_slots = list(range(self.max_slots - 1, -1, -1))
         self._busy = set()
@@ -237,7 +269,6 @@ class ServeEngine:
         if not realtime:
             for r in pending:
                 r.arrival = 0.0
-        done = []
         gc_was_enabled = gc.isenabled()
         gc.disable()  # no collector pauses inside the serving loop
         try:
@@ -291,7 +322,166 @@ class ServeEngine:
                     time.sleep(poll_s)
 
 
+    # ------------------------------------------------------------ batched steps
+    def _run_batched(self, requests, realtime, poll_s):
+        if not requests:
+            return []
+        dtypes = {r.coarse.dtype for r in requests}
+        if len(dtypes) != 1:
+            raise ValueError("batched serving takes requests of one storage type")
+        if not hasattr(self, "_lane_state"):
+            self._s_in = torch.cuda.Stream(device=self.device)
+            self._s_out = torch.cuda.Stream(device=self.device)
+            self._lane_state = [{"tables": [BatchTable(self.max_slots, self.device) for _ in range(2)],
+                                 "graphs": [None, None], "ev": [None, None], "steps": 0,
+                                 "stream": torch.cuda.Stream(device=self.device)} for _ in range(self.lanes)]
+            self._table_dtype = None
+        if self._table_dtype not in (None, next(iter(dtypes))):
+            for ln in self._lane_state:
+                ln["graphs"] = [None, None]  # captured for the other storage type
+        self._table_dtype = next(iter(dtypes))
+        pending = collections.deque(requests)
+        t0 = time.perf_counter()
+        if not realtime:
+            for r in pending:
+                r.arrival = 0.0
+        done = []
+        gc_was_enabled = gc.isenabled()
+        gc.disable()
+        try:
+            self._loop_batched(pending, t0, done, poll_s)
+        finally:
+            if gc_was_enabled:
+                gc.enable()
+        return done
+
+    def _lane_of(self, req) -> int:
+        D, H, W, N = req.shape[:4]
+        work = H * W * D * N
+        return min(self.lanes - 1, int(work >= self.lane_split))
+
+    def _admit_batched(self, req, t0):
+        n = request_bytes(*req.shape[:4], req.k, req.coarse.dtype)
+        off = self.arena.alloc(n)
+        if off is None:
+            return None
+        M, images, loss, ws = self._carve(req, off)
+        ev = torch.cuda.Event()
+        with torch.cuda.stream(self._s_in):
+            M.copy_(req.coarse, non_blocking=True)
+            images.copy_(req.images, non_blocking=True)
+            ev.record(self._s_in)
+        req.t_admit = time.perf_counter() - t0
+        mpi = make_mpi(M, req.near, req.far, req.ref)
+        citem, keep = batch_c_item(BatchItem(mpi, images, req.src, req.k, ws, level=req.schedule[0],
+                                             loss_out=loss[0:1]))
+        return {"req": req, "off": off, "n": n, "M": M, "loss": loss, "citem": citem, "keep": keep,
+                "loss_ptr": loss.data_ptr(), "it": 0, "ev_in": ev, "waited": False, "lane": self._lane_of(req)}
+
+    def _step_batched(self, lane, group):
+        ln = self._lane_state[lane]
+        b = ln["steps"] & 1
+        if ln["ev"][b] is not None:
+            ln["ev"][b].synchronize()  # the step that used this table buffer is done
+        comp = ln["stream"]
+        for a in group:
+            if not a["waited"]:
+                comp.wait_event(a["ev_in"])
+                a["waited"] = True
+            c = a["citem"]
+            c.params.level = a["req"].schedule[a["it"]]
+            c.loss_out = a["loss_ptr"] + 4 * a["it"]
+        table = ln["tables"][b]
+        reallife_batch_prepare([a["citem"] for a in group], table)
+        if self.graphs:
+            g = ln["graphs"][b]
+            if g is None:
+                comp.synchronize()
+                g = torch.cuda.CUDAGraph()
+                with torch.cuda.graph(g, stream=comp):
+                    reallife_hsgd_step_batch(table, stream=comp)
+                ln["graphs"][b] = g
+                self.captures += 1
+            with torch.cuda.stream(comp):
+                g.replay()
+            self.replays += 1
+        else:
+            reallife_hsgd_step_batch(table, stream=comp)
+        ev = torch.cuda.Event()
+        ev.record(comp)
+        ln["ev"][b] = ev
+        ln["steps"] += 1
+        self.steps += 1
+        self.max_items_per_step = max(self.max_items_per_step, len(group))
+        return ev
+
+    def _loop_batched(self, pending, t0, done, poll_s):
+        active = []     # requests with iterations left
+        leaving = []    # requests whose result is on its way to the host
+        while pending or active or leaving:
+            now = time.perf_counter() - t0
+            progressed = False
+            for a in list(leaving):
+                if a["ev_out"].query():
+                    req = a["req"]
+                    req.t_done = time.perf_counter() - t0
+                    req.losses = a["host_loss"].numpy().copy()
+                    if self.keep_results:
+                        req.result = a["host_out"].clone()
+                    self.arena.release(a["off"], a["n"])
+                    self.slot_result[a["slot"]] = a["host_buf"]
+                    leaving.remove(a)
+                    done.append(req)
+                    progressed = True
+            used = {x["slot"] for x in active + leaving}
+            free = [i for i in range(self.max_slots) if i not in used]
+            while pending and pending[0].arrival <= now and free:
+                a = self._admit_batched(pending[0], t0)
+                if a is None:
+                    break  # first come, first served: wait for memory
+                pending.popleft()
+                a["slot"] = free.pop()
+                a["req"].slot = a["slot"]
+                active.append(a)
+                progressed = True
+            for lane in range(self.lanes):
+                group = [a for a in active if a["lane"] == lane]
+                ln = self._lane_state[lane]
+                if not group or sum(1 for e in ln["ev"] if e is not None and not e.query()) >= 2:
+                    continue
+                ev = self._step_batched(lane, group)
+                for a in group:
+                    a["it"] += 1
+                    if a["it"] == len(a["req"].schedule):
+                        self._send_result(a, ev)
+                        active.remove(a)
+                        leaving.append(a)
+                progressed = True
+            if not progressed:
+                if pending and not active and not leaving and pending[0].arrival > now:
+                    time.sleep(max(0.0, min(pending[0].arrival - now, 1e-3)))
+                else:
+                    time.sleep(poll_s)
+
+    def _send_result(self, a, ev):
+        req = a["req"]
+        host_buf = self.slot_result[a["slot"]]
+        need = req.coarse.numel()
+        if host_buf is None or host_buf.numel() < need or host_buf.dtype != req.coarse.dtype:
+            host_buf = torch.empty(need, dtype=req.coarse.dtype).pin_memory()
+        a["host_buf"] = host_buf
+        a["host_out"] = host_buf[:need].view(req.coarse.shape)
+        a["host_loss"] = self.slot_loss[a["slot"]][:len(req.schedule)]
+        with torch.cuda.stream(self._s_out):
+            self._s_out.wait_event(ev)
+            a["host_out"].copy_(a["M"], non_blocking=True)
+            a["host_loss"].copy_(a["loss"], non_blocking=True)
+            a["ev_out"] = torch.cuda.Event()
+            a["ev_out"].record(self._s_out)
+
+
 def latency_stats(done) -> dict:
+    done = [r for r in done if r.error is None]
     lat = np.array([r.latency for r in done]) * 1e3
     queue = np.array([r.t_admit - r.arrival for r in done]) * 1e3
     t_first = min(r.arrival for r in done)

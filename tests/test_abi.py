@@ -121,3 +121,54 @@ def test_learned_update_workspace_sizes():
     act = (k * H * W * 64 + 1023) // 1024 * 1024
     want = a256(vol) + a256(k * H * W * 16) + a256(k * H * W) + 2 * act + 256
     assert lib.reallife_lgd_step_workspace_bytes(N, D, H, W, k, 0) == want
+
+
+def test_batch_table_sizes_and_validation(cpu_only):
+    """The batched step's table sizing and the host-side checks of reallife_batch_prepare
+    (placeholder device pointers: nothing is dereferenced or launched)."""
+    import numpy as np
+    import scenegen as sg
+    from paper_2307_03017_gb300 import _lib
+    lib = _lib.lib()
+    one = lib.reallife_batch_table_bytes(1)
+    assert one > 0 and one % 256 == 0
+    assert lib.reallife_batch_table_bytes(256) > lib.reallife_batch_table_bytes(255) > one
+    assert lib.reallife_batch_table_bytes(0) == 0 and lib.reallife_batch_table_bytes(257) == 0
+    cams = _lib.cameras([sg.Camera(sg.intrinsics(16, 16), np.eye(3), np.zeros(3))])
+    need = lib.reallife_workspace_bytes(1, 8, 16, 16, 2, 0)
+    mpis = [_mpi_struct(data=(1 << 24) * (i + 1)) for i in range(3)]
+
+    def item(i, ws, k=2, level=0, mpi=None):
+        b = _lib.RlBatchItem()
+        b.mpi = ctypes.pointer(mpi if mpi is not None else mpis[i])
+        b.images = ctypes.c_void_p(1 << 30)
+        b.src = ctypes.cast(cams, ctypes.POINTER(_lib.RlCamera))
+        b.N = 1
+        b.params.k, b.params.lambda_, b.params.clamp01, b.params.level = k, 1.0, 1, level
+        b.ws, b.ws_bytes = ctypes.c_void_p(ws), need
+        return b
+
+    table = (ctypes.c_uint8 * lib.reallife_batch_table_bytes(4))()
+    tb = ctypes.sizeof(table)
+
+    def prep(*its):
+        arr = (_lib.RlBatchItem * len(its))(*its)
+        return lib.reallife_batch_prepare(arr, len(its), table, tb)
+
+    base = 1 << 34
+    assert prep(item(0, base), item(1, base + (1 << 26)), item(2, base + (2 << 26))) == 0
+    assert lib.reallife_batch_prepare(None, 0, table, tb) == 1
+    arr = (_lib.RlBatchItem * 2)(item(0, base), item(1, base + (1 << 26)))
+    assert lib.reallife_batch_prepare(arr, 2, table, lib.reallife_batch_table_bytes(1)) == 2  # table too small
+    assert prep(item(0, base), item(1, base + 512)) == 1  # overlapping workspaces
+    assert b"share" in lib.reallife_last_error()
+    assert prep(item(0, base), item(1, base + (1 << 26), mpi=mpis[0])) == 1  # one MPI twice
+    m16 = _mpi_struct(dtype=1, data=1 << 28)
+    assert prep(item(0, base), item(1, base + (1 << 26), mpi=m16)) == 1  # storage types differ
+    assert b"storage" in lib.reallife_last_error()
+    assert prep(item(0, base), item(1, base + (1 << 26), k=9)) == 1  # k > D in item 1
+    assert b"batch item 1" in lib.reallife_last_error()
+    assert prep(item(0, base, level=5)) == 1  # level does not divide H
+    # a table that reallife_batch_prepare did not write is refused before anything is enqueued
+    blank = (ctypes.c_uint8 * tb)()
+    assert lib.reallife_hsgd_step_batch(blank, ctypes.c_void_p(1 << 20), tb, None) == 1

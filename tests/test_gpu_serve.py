@@ -96,3 +96,53 @@ def test_realtime_poisson_stream_reports_latency(pool):
     st = latency_stats(done)
     assert st["requests"] == 40 and 0 < st["p50_ms"] <= st["p99_ms"]
     assert all(r.t_done >= r.arrival for r in done)
+
+
+@pytest.mark.parametrize("graphs", [False, True])
+def test_batched_steps_result_alone_equals_result_in_the_mix(pool, graphs):
+    """Iteration-level batching: one batched launch per stage serves the next iteration of every
+    active request; each result equals the request served alone."""
+    from paper_2307_03017_gb300.serve import ServeEngine
+    alone = {}
+    eng1 = ServeEngine(1 << 30, max_slots=1, keep_results=True)
+    for r in _requests(pool, 12, seed=5):
+        (d,) = eng1.run([r], realtime=False)
+        alone[d.id] = (d.result.float().numpy(), d.losses)
+    eng = ServeEngine(1 << 30, max_slots=8, keep_results=True, batched=True, graphs=graphs)
+    mix = eng.run(_requests(pool, 12, seed=5), realtime=False)
+    assert len(mix) == 12 and all(r.error is None for r in mix)
+    iters = sum(len(r.schedule) for r in mix)
+    assert eng.max_items_per_step >= 2 and eng.steps < iters  # launches served several requests
+    if graphs:
+        assert eng.captures <= 2 * eng.lanes and eng.replays == eng.steps
+    for r in mix:
+        ref, ref_losses = alone[r.id]
+        assert np.abs(r.result.float().numpy() - ref).max() <= TOL16
+        np.testing.assert_allclose(r.losses, ref_losses, rtol=1e-3)
+    assert eng.arena.bytes_free() == eng.arena.size
+
+
+def test_batched_realtime_stream_and_oversized_request(pool):
+    """A Poisson stream through the batched engine; a request larger than the whole arena is
+    returned failed while the others are served."""
+    from paper_2307_03017_gb300.serve import ServeEngine, latency_stats, request_bytes
+    reqs = _requests(pool, 30, seed=6)
+    rng = np.random.default_rng(7)
+    t = 0.0
+    for r in reqs:
+        t += rng.exponential(1 / 400.0)
+        r.arrival = t
+    big = max(request_bytes(*r.shape[:4], r.k, r.coarse.dtype) for r in reqs)
+    small = [r for r in reqs if request_bytes(*r.shape[:4], r.k, r.coarse.dtype) < big]
+    eng = ServeEngine(big - 256, max_slots=8, batched=True)
+    done = eng.run(reqs, realtime=True)
+    assert len(done) == 30
+    failed = [r for r in done if r.error is not None]
+    assert failed and all(request_bytes(*r.shape[:4], r.k, r.coarse.dtype) == big for r in failed)
+    assert len(failed) + len(small) == 30
+    st = latency_stats(done)
+    assert st["requests"] == len(small) and 0 < st["p50_ms"] <= st["p99_ms"]
+    assert all(r.t_done >= r.arrival for r in done)
+    # the same for the per-stream engine
+    done2 = ServeEngine(big - 256, max_slots=8).run(_requests(pool, 30, seed=6), realtime=False)
+    assert sum(r.error is not None for r in done2) == len(failed)

@@ -60,6 +60,8 @@ def parse():
                     "launching its kernels directly (measured no faster: the tracer's event nodes cost what "
                     "the launch gaps do)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="paper workload: skip the BF16, display and serving keys of the default line")
     ap.add_argument("--no-clocks", action="store_true")
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--stage", choices=["hsgd", "volume", "lgd"], default="hsgd",
@@ -86,13 +88,13 @@ def reduce_max(x: float, dist, device) -> float:
     return float(t.item())
 
 
-def csrc_digest(files=None) -> str:
-    """Digest of the named source files (paths relative to the repository root), by default
-    every file of the CUDA sources: a stored ncu counter is used only while it matches."""
-    if files is None:
-        paths = sorted(glob.glob(os.path.join(ROOT, "paper_2307_03017_gb300", "csrc", "*")))
-    else:
-        paths = [os.path.join(ROOT, f) for f in files]
+def csrc_digest() -> str:
+    """Digest of everything that decides the compiled kernels: every file of the CUDA sources,
+    the public header and the build script (its nvcc flags).  A stored ncu counter is used only
+    while it matches."""
+    paths = sorted(glob.glob(os.path.join(ROOT, "paper_2307_03017_gb300", "csrc", "*")))
+    paths += sorted(glob.glob(os.path.join(ROOT, "include", "*.h")))
+    paths.append(os.path.join(ROOT, "paper_2307_03017_gb300", "build.py"))
     h = hashlib.sha256()
     for p in paths:
         with open(p, "rb") as f:
@@ -102,14 +104,14 @@ def csrc_digest(files=None) -> str:
 
 
 def stored_traffic(key: str):
-    """ncu DRAM bytes per launch of a kernel (profiles/traffic.json), or None once the
-    kernel's source files differ from those the counters were taken on."""
+    """ncu DRAM bytes per launch of a kernel (profiles/traffic.json), or None once any kernel
+    source, the header or the build flags differ from those the counters were taken on."""
     tf = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(tf):
         return None
     try:
         tr = json.load(open(tf)).get(key)
-        if tr and tr.get("csrc_digest") == csrc_digest(tr.get("files")):
+        if tr and tr.get("csrc_digest") == csrc_digest():
             return tr["dram_bytes_per_launch"]
     except Exception:
         return None
@@ -635,13 +637,14 @@ def serve_requests_from_pool(pool, draws):
     return out
 
 
-def run_serve(args, world, rank, local):
+def run_serve(args, world, rank, local, pool=None):
     import torch
     import scenegen as sg
     from paper_2307_03017_gb300.serve import ServeEngine, latency_stats
     torch.cuda.set_device(local)
     t_gen = time.perf_counter()
-    pool = serve_scene_pool()
+    if pool is None:
+        pool = serve_scene_pool()
     t_gen = time.perf_counter() - t_gen
     draws = sg.serve_requests(args.requests, args.rate, seed=12345)
     max_elems = max(M.numel() for (_, M, _) in pool.values())
@@ -717,21 +720,33 @@ def sample_rows(sc, frac: float) -> int:
     return max(8, int(sc.H * frac) // 8 * 8)
 
 
-def cpu_baseline(sc, cfg, frac: float = 0.5) -> dict:
-    """The FP64 oracle as it stands, single-threaded, on one step of a band of the same
-    workload (about half of its rows), scaled to refinements/s by the band's share of pixels."""
+BASELINE_BAND = 1.0 / 8.0  # share of the rows the oracle's samples take (both legs)
+
+
+def cpu_baseline(sc, cfg, frac: float = BASELINE_BAND) -> dict:
+    """The FP64 oracle as it stands on one step of a band of the same workload (1/8 of its rows,
+    the reference arm's band), timed single-threaded and on all the host cores this process may
+    use (the OpenMP build, bit-identical results), scaled to refinements/s by the band's share of
+    pixels.  ``value`` is the all-core figure."""
     import oracle
     oracle.build()
     rows = sample_rows(sc, frac)
     band = crop_scene(sc, rows)
-    t0 = time.perf_counter()
-    oracle_step(band, cfg)
-    dt = time.perf_counter() - t0
     share = rows / sc.H
-    return {"value": round(share / dt, 5), "unit": UNIT, "cores": 1, "kind": "oracle",
+    out = {}
+    for threads in (False, True):
+        oracle.set_threads(threads)
+        n = oracle.num_threads()
+        t0 = time.perf_counter()
+        oracle_step(band, cfg)
+        out[threads] = (time.perf_counter() - t0, n)
+    oracle.set_threads(False)
+    (t1, _), (tn, n) = out[False], out[True]
+    return {"value": round(share / tn, 5), "unit": UNIT, "cores": n, "kind": "oracle",
             "sample": f"one step ({len(cfg['schedule'])}-level refine + {len(sc.novel)} renders) on a {sc.W}x{rows} "
-                      f"band ({share:.3f} of the pixels) of the same scene, FP64, single thread, {dt:.2f} s; "
+                      f"band ({share:.3f} of the pixels) of the same scene, FP64, OpenMP on {n} cores, {tn:.2f} s; "
                       f"value scaled by the pixel share",
+            "single_thread": {"value": round(share / t1, 5), "cores": 1, "seconds": round(t1, 2)},
             "cpu": platform_cpu()}
 
 
@@ -749,23 +764,26 @@ def platform_cpu() -> str:
 
 
 def reference_band_rows(H: int, unit: int, t_unit: float, n_steps: int, budget_s: float = 120.0) -> int:
-    """Rows of the reference arm's band: a multiple of `unit` (the coarsest level's block),
-    at least one unit and at most 1/8 of the H rows (rounded down to units), sized so that
-    n_steps steps of t_unit seconds per unit of rows take about budget_s."""
+    """Rows of the reference arm's band: the CPU-baseline band (1/8 of the H rows, a multiple of 8),
+    or fewer (a multiple of `unit`, the coarsest level's block, at least one unit) when n_steps
+    steps of t_unit seconds per unit of rows would exceed budget_s."""
     units = int(budget_s / max(1, n_steps) / max(t_unit, 1e-6))
-    cap = max(1, (max(8, H // 8 // 8 * 8)) // unit)
+    cap = max(1, (max(8, int(H * BASELINE_BAND) // 8 * 8)) // unit)
     return unit * max(1, min(cap, units))
 
 
 def run_reference(args, world, rank):
-    """The oracle on the host cores, each step a horizontal band of the workload (scaled by its
-    share of the pixels).  One untimed step on a 4-row band (the least height the coarsest
-    pyramid level allows) sizes the band so that the warm-up and timed steps take about two
-    minutes: at most 1/8 of the rows, at least 4."""
+    """The oracle on the host cores (the OpenMP build on every core this process may use), each
+    step a horizontal band of the workload scaled by its share of the pixels: the CPU-baseline
+    band of 1/8 of the rows, unless an untimed calibration step on a 4-row band (the least height
+    the coarsest pyramid level allows) shows that the warm-up and timed steps would take more
+    than about two minutes, in which case the band is narrowed to fit."""
     if rank != 0:
         return None
     import oracle
     oracle.build()
+    oracle.set_threads(True)
+    cores = oracle.num_threads()
     sc, cfg = load_scene(args.workload, args.seed)
     unit = 1 << max(cfg["schedule"])
     t0 = time.perf_counter()
@@ -786,11 +804,51 @@ def run_reference(args, world, rank):
             "data": "synthetic (seeded ray-cast layered scenes; no dataset)",
             "config": {"workload": f"{args.workload}: {sc.W}x{sc.H} D={sc.D} N={len(sc.src)} k={cfg['k']} "
                                    f"levels={list(cfg['schedule'])} + {len(sc.novel)} novel views"},
-            "cpu_baseline": {"value": round(v, 5), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "cpu_baseline": {"value": round(v, 5), "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": f"each step = one step on a {sc.W}x{rows} band ({share:.3f} of the pixels) "
-                                       f"of the workload, FP64 oracle, single thread; value scaled by the share",
+                                       f"of the workload, FP64 oracle, OpenMP on {cores} cores; value scaled by "
+                                       f"the share",
                              "cpu": platform_cpu()},
             "e2e": {"value": round(v, 5), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def _summary(r: dict) -> dict:
+    """The keys of a secondary workload's line that the default line carries."""
+    keep = ("value", "unit", "ms_per_step", "steps", "dtype", "config", "roofline", "kernels", "gpu_launches",
+            "hbm_gbs_step", "e2e")
+    return {k: r[k] for k in keep if k in r}
+
+
+def run_extras(args, world, rank, local) -> dict:
+    """The default line's secondary keys: the same step with BF16 storage, the 1920x1080 display
+    workload and the serving stream (shortened; per-stream and batched engines)."""
+    import copy
+    out = {}
+    a = copy.copy(args)
+    a.no_clocks = True
+    a.workload = "paper_bf16"
+    out["bf16"] = _summary(run_ours(a, world, rank, local))
+    a = copy.copy(args)
+    a.no_clocks = True
+    a.workload = "display"
+    a.steps = max(20, min(args.steps, 50))
+    a.warmup = max(3, min(args.warmup, 5))
+    out["display"] = _summary(run_ours(a, world, rank, local))
+    a = copy.copy(args)
+    a.no_clocks = True
+    a.requests = min(args.requests, 500)
+    pool = serve_scene_pool()
+    serve = {}
+    for mode in ("streams", "batched"):
+        a.serve_mode = mode
+        r = run_serve(a, world, rank, local, pool=pool)
+        serve[mode] = {k: r[k] for k in ("p50_ms", "p99_ms", "mean_ms", "max_ms", "queue_p50_ms", "queue_p99_ms",
+                                         "reconstructions_per_s", "closed_loop_reconstructions_per_s",
+                                         "batched_steps", "max_requests_per_step")}
+    serve["config"] = r["config"]["workload"]
+    serve["unit"] = "ms (latency), reconstructions/s"
+    out["serve"] = serve
+    return out
 
 
 def main():
@@ -814,6 +872,8 @@ def main():
             res["cpu_baseline"] = cpu_baseline(sc, cfg)
         elif res is not None:
             res["cpu_baseline"] = None
+        if res is not None and world == 1 and args.workload == "paper" and not args.no_extras:
+            res.update(run_extras(args, world, rank, local))
     if res is not None:
         print(json.dumps(res), flush=True)
 

@@ -149,9 +149,10 @@ rl_status reallife_refine(rl_mpi* m, const float* images, const rl_camera* src, 
  *   - RL_ENOMEM (with a message) when the problem needs more scratch than the array
  *     holds (reallife_workspace_bytes > RL_NOALLOC_SCRATCH_BYTES); e.g. 512x384, D=32,
  *     N=4, k=5 needs 48 MB and fits, 1920x1080 D=64 does not.
- *   - The first call on a device looks up the array's device address for that device
- *     (cudaGetSymbolAddress) with the device current; make that first call before any
- *     stream capture.
+ *   - Every call made outside stream capture looks up the array's device address for the
+ *     current device (cudaGetSymbolAddress), so the address stays right after a
+ *     cudaDeviceReset; a call being captured reuses the address of the device's last
+ *     uncaptured call.  Make the first call on a device before any stream capture.
  *   - All calls on a device share the one array, and it keeps what the last call left
  *     in it (every value a call reads is written earlier in the same call).  Calls that
  *     overlap on the GPU -- on different streams, or from different threads -- race on
@@ -353,8 +354,9 @@ rl_status reallife_set_kernel_path(int path);
 
 /* Device-side status: synchronises the device and reports the status word that kernels
  * set when a bounded wait (about one second) gives up; *flags_out receives its bits
- * (1 = timeout).  Returns RL_ETIMEOUT when the timeout bit is set, RL_OK otherwise;
- * clear != 0 resets the word.  Results of launches that timed out are invalid. */
+ * (1 = timeout; 2 = a batched step was given a table it cannot serve, see
+ * reallife_hsgd_step_batch).  Returns RL_ETIMEOUT when the timeout bit is set, RL_OK
+ * otherwise; clear != 0 resets the word.  Results of launches that timed out are invalid. */
 rl_status reallife_device_status(int clear, unsigned int* flags_out);
 
 /* Self-test of the failure reporting (no fault, no hang): one thread waits on a

@@ -34,59 +34,94 @@ class _Cam(ctypes.Structure):
     _fields_ = [("K", ctypes.c_double * 9), ("R", ctypes.c_double * 9), ("t", ctypes.c_double * 3)]
 
 
+_LIB_OMP_PATH = os.path.join(_HERE, "libreallife_oracle_omp.so")
+_lib_omp = None
+_use_threads = False
+
+
+def _compile(path: str, extra: list[str]):
+    tmp = path + f".tmp{os.getpid()}"
+    subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC", *extra,
+                           "-shared", "-o", tmp, _SRC, "-lm"])
+    os.replace(tmp, path)
+
+
 def build(force: bool = False) -> str:
-    """Compile the oracle with gcc (IEEE double, no FMA contraction) if needed."""
-    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
-        tmp = _LIB_PATH + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
-                               "-shared", "-o", tmp, _SRC, "-lm"])
-        os.replace(tmp, _LIB_PATH)
+    """Compile the oracle with gcc (IEEE double, no FMA contraction) if needed: the serial
+    library and the OpenMP one (bit-identical results, all host cores)."""
+    for path, extra in ((_LIB_PATH, []), (_LIB_OMP_PATH, ["-fopenmp"])):
+        if force or not os.path.exists(path) or os.path.getmtime(path) < os.path.getmtime(_SRC):
+            _compile(path, extra)
     return _LIB_PATH
 
 
+def set_threads(on: bool) -> None:
+    """Run the oracle's parallel loops on all host cores (the OpenMP build) or on one."""
+    global _use_threads
+    _use_threads = bool(on)
+
+
+def num_threads() -> int:
+    """Threads of the build in use (OpenMP: OMP_NUM_THREADS or the cores this process may use)."""
+    return int(_load().orc_num_threads())
+
+
 def _load():
-    global _lib
     with _lock:
-        if _lib is None:
-            lib = ctypes.CDLL(build())
-            P = ctypes.POINTER
-            d, i, dp = ctypes.c_double, ctypes.c_int, P(ctypes.c_double)
-            cam = P(_Cam)
-            u8p, u64p = P(ctypes.c_uint8), P(ctypes.c_uint64)
-            lib.orc_plane_inverse_depths.argtypes = [i, d, d, dp]
-            lib.orc_camera_at_level.argtypes = [cam, i, cam]
-            lib.orc_view_to_ref.argtypes = [cam, cam, d, d, d, dp, dp]
-            lib.orc_view_to_ref.restype = i
-            lib.orc_render.argtypes = [dp, i, i, i, d, d, cam, cam, dp]
-            ip = P(ctypes.c_int)
-            lib.orc_render_pixels.argtypes = [dp, i, i, i, d, d, cam, cam, i, ip, ip, dp]
-            lib.orc_vjp.argtypes = [dp, i, i, i, d, d, cam, cam, i, dp, dp]
-            lib.orc_loss_grad.argtypes = [dp, i, i, i, d, d, cam, dp, cam, i, dp, dp]
-            lib.orc_loss_grad.restype = d
-            lib.orc_alpha_weights.argtypes = [dp, i, i, i, dp]
-            lib.orc_select_topk.argtypes = [dp, i, i, i, i, u8p, u64p]
-            lib.orc_downsample2.argtypes = [dp, i, i, i, i, dp]
-            lib.orc_down_levels.argtypes = [dp, i, i, i, i, i, dp]
-            lib.orc_hsgd_step.argtypes = [dp, i, i, i, d, d, cam, dp, cam, i, i, d, i, i, u8p, u8p, dp]
-            lib.orc_hsgd_step.restype = i
-            lib.orc_hsgd_step2.argtypes = [dp, i, i, i, d, d, cam, dp, cam, i, i, d, i, i, i, d, u8p, u8p, dp]
-            lib.orc_hsgd_step2.restype = i
-            lib.orc_select_mvs.argtypes = [dp, i, i, i, i, u8p, u64p]
-            lib.orc_sparsity_grad.argtypes = [d, i, i, i]
-            lib.orc_sparsity_grad.restype = d
-            lib.orc_sparsity_loss.argtypes = [dp, i, i, i]
-            lib.orc_sparsity_loss.restype = d
-            lib.orc_gd_step.argtypes = [dp, i, i, i, d, d, cam, dp, cam, i, d, i, i, dp]
-            lib.orc_gd_step.restype = i
-            lib.orc_ref_to_view.argtypes = [cam, cam, d, d, d, dp, dp]
-            lib.orc_ref_to_view.restype = i
-            lib.orc_view_alpha_weights.argtypes = [dp, i, i, i, d, d, cam, cam, dp]
-            lib.orc_psv_view.argtypes = [dp, i, i, i, d, d, cam, cam, dp]
-            lib.orc_inverse_warp_stack.argtypes = [dp, i, i, i, d, d, cam, cam, dp]
-            lib.orc_gradient_volume.argtypes = [dp, i, i, i, d, d, cam, dp, cam, i, i, i, i, u8p, u8p, dp]
-            lib.orc_gradient_volume.restype = i
-            _lib = lib
+        return _load_locked()
+
+
+def _load_locked():
+    global _lib, _lib_omp
+    if _use_threads:
+        if _lib_omp is None:
+            build()
+            _lib_omp = _declare(ctypes.CDLL(_LIB_OMP_PATH))
+        return _lib_omp
+    if _lib is None:
+        _lib = _declare(ctypes.CDLL(build()))
     return _lib
+
+
+def _declare(lib):
+    P = ctypes.POINTER
+    d, i, dp = ctypes.c_double, ctypes.c_int, P(ctypes.c_double)
+    cam = P(_Cam)
+    u8p, u64p = P(ctypes.c_uint8), P(ctypes.c_uint64)
+    lib.orc_plane_inverse_depths.argtypes = [i, d, d, dp]
+    lib.orc_camera_at_level.argtypes = [cam, i, cam]
+    lib.orc_view_to_ref.argtypes = [cam, cam, d, d, d, dp, dp]
+    lib.orc_view_to_ref.restype = i
+    lib.orc_render.argtypes = [dp, i, i, i, d, d, cam, cam, dp]
+    ip = P(ctypes.c_int)
+    lib.orc_render_pixels.argtypes = [dp, i, i, i, d, d, cam, cam, i, ip, ip, dp]
+    lib.orc_vjp.argtypes = [dp, i, i, i, d, d, cam, cam, i, dp, dp]
+    lib.orc_loss_grad.argtypes = [dp, i, i, i, d, d, cam, dp, cam, i, dp, dp]
+    lib.orc_loss_grad.restype = d
+    lib.orc_alpha_weights.argtypes = [dp, i, i, i, dp]
+    lib.orc_select_topk.argtypes = [dp, i, i, i, i, u8p, u64p]
+    lib.orc_downsample2.argtypes = [dp, i, i, i, i, dp]
+    lib.orc_down_levels.argtypes = [dp, i, i, i, i, i, dp]
+    lib.orc_hsgd_step.argtypes = [dp, i, i, i, d, d, cam, dp, cam, i, i, d, i, i, u8p, u8p, dp]
+    lib.orc_hsgd_step.restype = i
+    lib.orc_hsgd_step2.argtypes = [dp, i, i, i, d, d, cam, dp, cam, i, i, d, i, i, i, d, u8p, u8p, dp]
+    lib.orc_hsgd_step2.restype = i
+    lib.orc_select_mvs.argtypes = [dp, i, i, i, i, u8p, u64p]
+    lib.orc_sparsity_grad.argtypes = [d, i, i, i]
+    lib.orc_sparsity_grad.restype = d
+    lib.orc_sparsity_loss.argtypes = [dp, i, i, i]
+    lib.orc_sparsity_loss.restype = d
+    lib.orc_gd_step.argtypes = [dp, i, i, i, d, d, cam, dp, cam, i, d, i, i, dp]
+    lib.orc_gd_step.restype = i
+    lib.orc_ref_to_view.argtypes = [cam, cam, d, d, d, dp, dp]
+    lib.orc_ref_to_view.restype = i
+    lib.orc_view_alpha_weights.argtypes = [dp, i, i, i, d, d, cam, cam, dp]
+    lib.orc_psv_view.argtypes = [dp, i, i, i, d, d, cam, cam, dp]
+    lib.orc_inverse_warp_stack.argtypes = [dp, i, i, i, d, d, cam, cam, dp]
+    lib.orc_gradient_volume.argtypes = [dp, i, i, i, d, d, cam, dp, cam, i, i, i, i, u8p, u8p, dp]
+    lib.orc_gradient_volume.restype = i
+    lib.orc_num_threads.restype = i
+    return lib
 
 
 def _cam(c) -> _Cam:

@@ -42,12 +42,24 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 typedef struct {
     double K[9]; /* row-major intrinsics */
     double R[9]; /* row-major world->camera rotation */
     double t[3]; /* world->camera translation */
 } orc_camera;
+
+/* Threads the build runs its parallel loops on (1 for the serial build). */
+int orc_num_threads(void) {
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
 
 /* ---------------------------------------------------------------- geometry */
 
@@ -171,6 +183,7 @@ void orc_render(const double* M, int D, int H, int W, double near_, double far_,
                 const orc_camera* view, double* out) {
     double* rho = (double*)malloc(sizeof(double) * D);
     orc_plane_inverse_depths(D, near_, far_, rho);
+#pragma omp parallel for schedule(static)
     for (int y = 0; y < H; ++y)
         for (int x = 0; x < W; ++x) render_pixel(M, D, H, W, rho, ref, view, x, y, out + ((size_t)y * W + x) * 3);
     free(rho);
@@ -193,6 +206,14 @@ void orc_render_pixels(const double* M, int D, int H, int W, double near_, doubl
  * with T_d = prod_{j>d}(1 - alpha_j); then the bilinear transpose scatters the per-sample
  * gradient onto the four taps.  No division by (1 - alpha).
  */
+/* Per-sample gradient of plane d at one view pixel: dC/dc_d and dC/dalpha_d contracted with r. */
+static void sample_gradient(const double* m, double Td, const double* B, const double* r, double g[4]) {
+    for (int c = 0; c < 3; ++c) g[c] = Td * m[3] * r[c];
+    g[3] = 0.0;
+    for (int c = 0; c < 3; ++c) g[3] += Td * (m[c] - B[c]) * r[c];
+}
+
+#ifndef _OPENMP
 void orc_vjp(const double* M, int D, int H, int W, double near_, double far_, const orc_camera* ref,
              const orc_camera* views, int N, const double* g_out, double* grad) {
     double* rho = (double*)malloc(sizeof(double) * D);
@@ -215,9 +236,7 @@ void orc_vjp(const double* M, int D, int H, int W, double near_, double far_, co
                 for (int d = 0; d < D; ++d) {
                     const double* m = smp[d].m;
                     double g[4];
-                    for (int c = 0; c < 3; ++c) g[c] = T[d] * m[3] * r[c];
-                    g[3] = 0.0;
-                    for (int c = 0; c < 3; ++c) g[3] += T[d] * (m[c] - B[c]) * r[c];
+                    sample_gradient(m, T[d], B, r, g);
                     for (int c = 0; c < 3; ++c) B[c] = m[c] * m[3] + (1.0 - m[3]) * B[c];
                     for (int k = 0; k < 4; ++k) {
                         if (smp[d].w[k] == 0.0) continue;
@@ -230,6 +249,67 @@ void orc_vjp(const double* M, int D, int H, int W, double near_, double far_, co
     free(smp);
     free(rho);
 }
+#else
+/*
+ * The same vector-Jacobian product on the host's cores (the OpenMP build, used to time the
+ * oracle on all cores).  Bit-identical to the serial loop above: a voxel of plane d receives
+ * contributions only from samples of plane d, so for each view and each band of rows, phase 1
+ * forms every sample and its per-sample gradient (rows in parallel, the serial arithmetic),
+ * and phase 2 adds them plane by plane (planes in parallel), each plane in the serial order of
+ * (row, column, tap).  Views and bands are taken in order.
+ */
+#define ORC_VJP_BAND 16
+void orc_vjp(const double* M, int D, int H, int W, double near_, double far_, const orc_camera* ref,
+             const orc_camera* views, int N, const double* g_out, double* grad) {
+    double* rho = (double*)malloc(sizeof(double) * D);
+    orc_plane_inverse_depths(D, near_, far_, rho);
+    const size_t band_px = (size_t)ORC_VJP_BAND * W;
+    sample_t* smp = (sample_t*)malloc(sizeof(sample_t) * D * band_px); /* [d][band row][x] */
+    double* gs = (double*)malloc(sizeof(double) * 4 * D * band_px);    /* per-sample gradients */
+    for (int i = 0; i < N; ++i)
+        for (int y0 = 0; y0 < H; y0 += ORC_VJP_BAND) {
+            const int rows = H - y0 < ORC_VJP_BAND ? H - y0 : ORC_VJP_BAND;
+#pragma omp parallel for schedule(static)
+            for (int yy = 0; yy < rows; ++yy) {
+                double* T = (double*)malloc(sizeof(double) * D);
+                const int y = y0 + yy;
+                for (int x = 0; x < W; ++x) {
+                    const double* r = g_out + (((size_t)i * H + y) * W + x) * 3;
+                    const size_t q = (size_t)yy * W + x;
+                    double Tr = 1.0;
+                    for (int d = D - 1; d >= 0; --d) {
+                        double px, py;
+                        int ok = orc_view_to_ref(ref, &views[i], 1.0 / rho[d], x, y, &px, &py);
+                        sample_plane(M, d, H, W, ok, px, py, &smp[d * band_px + q]);
+                        T[d] = Tr;
+                        Tr *= (1.0 - smp[d * band_px + q].m[3]);
+                    }
+                    double B[3] = {0, 0, 0};
+                    for (int d = 0; d < D; ++d) {
+                        const double* m = smp[d * band_px + q].m;
+                        sample_gradient(m, T[d], B, r, gs + (d * band_px + q) * 4);
+                        for (int c = 0; c < 3; ++c) B[c] = m[c] * m[3] + (1.0 - m[3]) * B[c];
+                    }
+                }
+                free(T);
+            }
+#pragma omp parallel for schedule(static)
+            for (int d = 0; d < D; ++d)
+                for (size_t q = 0; q < (size_t)rows * W; ++q) {
+                    const sample_t* s = &smp[d * band_px + q];
+                    const double* g = gs + (d * band_px + q) * 4;
+                    for (int k = 0; k < 4; ++k) {
+                        if (s->w[k] == 0.0) continue;
+                        double* gp = grad + (((size_t)d * H + s->ty[k]) * W + s->tx[k]) * 4;
+                        for (int c = 0; c < 4; ++c) gp[c] += s->w[k] * g[c];
+                    }
+                }
+        }
+    free(gs);
+    free(smp);
+    free(rho);
+}
+#endif
 
 /*
  * Photometric loss of N views and, if grad != NULL, its gradient dL/dM (dense, overwritten).
@@ -262,6 +342,7 @@ double orc_loss_grad(const double* M, int D, int H, int W, double near_, double 
 
 /* Reference-view alpha weights A_d = alpha_d prod_{j>d}(1 - alpha_j)  (Eq. eq_gradient, eq_overA). */
 void orc_alpha_weights(const double* M, int D, int H, int W, double* A) {
+#pragma omp parallel for schedule(static)
     for (int y = 0; y < H; ++y)
         for (int x = 0; x < W; ++x)
             for (int d = 0; d < D; ++d) {
@@ -279,8 +360,9 @@ void orc_alpha_weights(const double* M, int D, int H, int W, double* A) {
  * and keep the first k.
  */
 void orc_select_topk(const double* A, int D, int H, int W, int k, uint8_t* S, uint64_t* mask) {
-    int* order = (int*)malloc(sizeof(int) * D);
-    for (int y = 0; y < H; ++y)
+#pragma omp parallel for schedule(static)
+    for (int y = 0; y < H; ++y) {
+        int* order = (int*)malloc(sizeof(int) * D);
         for (int x = 0; x < W; ++x) {
             size_t p = (size_t)y * W + x;
             for (int d = 0; d < D; ++d) order[d] = d;
@@ -306,7 +388,8 @@ void orc_select_topk(const double* A, int D, int H, int W, int k, uint8_t* S, ui
             for (int d = 0; d < D; ++d)
                 if (mk >> d & 1) S[(size_t)j++ * H * W + p] = (uint8_t)d;
         }
-    free(order);
+        free(order);
+    }
 }
 
 /*
@@ -615,6 +698,7 @@ int orc_hsgd_step2(double* M, int D, int H, int W, double near_, double far_, co
     if (lambda_s != 0.0)
         for (size_t v = 0; v < (size_t)D * h * w; ++v)
             g[v * 4 + 3] += lambda_s * orc_sparsity_grad(Ml[v * 4 + 3], D, h, w);
+#pragma omp parallel for schedule(static)
     for (int yy = 0; yy < h; ++yy)
         for (int xx = 0; xx < w; ++xx)
             for (int j = 0; j < k; ++j) {

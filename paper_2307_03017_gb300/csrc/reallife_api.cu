@@ -769,8 +769,8 @@ extern "C" rl_status reallife_hsgd_step_batch(const void* table_host, void* tabl
 // without asking them for a workspace: its scratch is the array below, a fixed
 // RL_NOALLOC_SCRATCH_BYTES per device that every GPU loading this library keeps until
 // the process exits.  The array's name is only a host-side stand-in in host code, so its
-// device address is looked up with cudaGetSymbolAddress (once per device, on the first
-// call with that device current) and passed to the kernels.
+// device address is looked up with cudaGetSymbolAddress (on every call made outside stream
+// capture, with the call's device current) and passed to the kernels.
 
 static __device__ __align__(256) unsigned char g_rl_noalloc_scratch[RL_NOALLOC_SCRATCH_BYTES];
 
@@ -778,13 +778,17 @@ namespace {
 std::mutex g_noalloc_mu;
 void* g_noalloc_ptr[256] = {};
 
-rl_status noalloc_scratch(void** out) {
+// Device address of the fixed scratch on the current device.  Looked up again on every call
+// made outside stream capture (cheap, and right after a cudaDeviceReset has reloaded the
+// library's device code); a call being captured uses the address of the device's last
+// uncaptured call, or looks it up if there was none.
+rl_status noalloc_scratch(void** out, cudaStream_t s) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return rl_fail(RL_ECUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
     if (dev < 0 || dev >= 256) return rl_fail(RL_ECUDA, "device ordinal %d out of range", dev);
     std::lock_guard<std::mutex> lk(g_noalloc_mu);
-    if (!g_noalloc_ptr[dev]) {
+    if (!g_noalloc_ptr[dev] || !capturing(s)) {
         void* p = nullptr;
         e = cudaGetSymbolAddress(&p, g_rl_noalloc_scratch);
         if (e != cudaSuccess || !p)
@@ -813,7 +817,7 @@ extern "C" rl_status reallife_hsgd_step_noalloc(rl_mpi* m, const float* images, 
         if (g_trace_on) return rl_fail(RL_EINVAL, "kernel tracing creates CUDA events; disable it for this call");
     }
     void* ws = nullptr;
-    st = noalloc_scratch(&ws);
+    st = noalloc_scratch(&ws, stream);
     if (st) return st;
     st = check_hsgd(m, images, src, N, p, p->level, ws, (size_t)RL_NOALLOC_SCRATCH_BYTES);
     if (st) return st;

@@ -121,6 +121,7 @@ def _declare(lib):
     lib.orc_gradient_volume.argtypes = [dp, i, i, i, d, d, cam, dp, cam, i, i, i, i, u8p, u8p, dp]
     lib.orc_gradient_volume.restype = i
     lib.orc_num_threads.restype = i
+    lib.orc_grad_voxels.argtypes = [dp, i, i, i, d, d, cam, dp, cam, i, i, ip, ip, ip, i, dp]
     return lib
 
 
@@ -261,6 +262,25 @@ def down(x, level: int) -> np.ndarray:
     P, H, W, C = x.shape
     out = np.empty((P, H >> level, W >> level, C))
     _load().orc_down_levels(_ptr(x), P, H, W, C, level, _ptr(out))
+    return out
+
+
+def grad_voxels(M, near: float, far: float, ref, views, images, ds, ys, xs, radius: int = 3) -> np.ndarray:
+    """dL/dM of the photometric loss at the voxels (ds[j], ys[j], xs[j]): ``[n][4]``, equal to the
+    dense gradient of ``loss_grad`` there, by brute force over the view pixels near the voxel's
+    projection (for problems whose dense gradient is too large to form)."""
+    M = _f64(M)
+    D, H, W, _ = M.shape
+    images = _f64(images)
+    ds, ys, xs = (np.ascontiguousarray(a, dtype=np.int32) for a in (ds, ys, xs))
+    n = len(ds)
+    assert len(ys) == n and len(xs) == n
+    assert np.all((ds >= 0) & (ds < D) & (ys >= 0) & (ys < H) & (xs >= 0) & (xs < W))
+    out = np.empty((n, 4))
+    ip = ctypes.POINTER(ctypes.c_int)
+    _load().orc_grad_voxels(_ptr(M), D, H, W, near, far, ctypes.byref(_cam(ref)), _ptr(images), _cams(views),
+                            len(views), n, ds.ctypes.data_as(ip), ys.ctypes.data_as(ip), xs.ctypes.data_as(ip),
+                            int(radius), _ptr(out))
     return out
 
 

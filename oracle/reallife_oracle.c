@@ -338,6 +338,78 @@ double orc_loss_grad(const double* M, int D, int H, int W, double near_, double 
     return L;
 }
 
+/*
+ * dL/dM of the photometric loss (the gradient orc_loss_grad returns) at n chosen voxels
+ * (ds[j], ys[j], xs[j]), out[n][4], by brute force over the view pixels: a view pixel q adds
+ * w_tap * dL/dm_d (Eq. eq_gradient, as in orc_vjp) when the voxel is one of the four taps of
+ * its sample of plane d.  The candidates are the view pixels within `radius` of the point
+ * where the voxel's centre on plane d projects into the view (Eq. eq_homo's inverse warp);
+ * every other view pixel's sample of plane d lies more than a pixel away from the voxel for
+ * the near-identity warps of forward-facing views.  Views, then candidates in row-major order,
+ * as orc_vjp visits them, so each voxel's sum is formed in the same order.  For outputs the
+ * dense gradient would be too large to form (one voxel needs N (2 radius + 1)^2 composites).
+ */
+int orc_ref_to_view(const orc_camera* ref, const orc_camera* view, double z, double u, double v, double* x,
+                    double* y);
+
+void orc_grad_voxels(const double* M, int D, int H, int W, double near_, double far_, const orc_camera* ref,
+                     const double* images, const orc_camera* views, int N, int n, const int* ds, const int* ys,
+                     const int* xs, int radius, double* out) {
+    double* rho = (double*)malloc(sizeof(double) * D);
+    orc_plane_inverse_depths(D, near_, far_, rho);
+#pragma omp parallel for schedule(dynamic, 8)
+    for (int j = 0; j < n; ++j) {
+        sample_t* smp = (sample_t*)malloc(sizeof(sample_t) * D);
+        double* T = (double*)malloc(sizeof(double) * D);
+        const int d = ds[j], y = ys[j], x = xs[j];
+        double acc[4] = {0, 0, 0, 0};
+        for (int i = 0; i < N; ++i) {
+            double u0, v0;
+            if (!orc_ref_to_view(ref, &views[i], 1.0 / rho[d], x, y, &u0, &v0)) continue;
+            if (!(fabs(u0) < 1e7) || !(fabs(v0) < 1e7)) continue;
+            const int cu = (int)floor(u0), cv = (int)floor(v0);
+            for (int qy = cv - radius; qy <= cv + radius + 1; ++qy) {
+                if (qy < 0 || qy >= H) continue;
+                for (int qx = cu - radius; qx <= cu + radius + 1; ++qx) {
+                    if (qx < 0 || qx >= W) continue;
+                    double px, py;
+                    int ok = orc_view_to_ref(ref, &views[i], 1.0 / rho[d], qx, qy, &px, &py);
+                    sample_t s;
+                    sample_plane(M, d, H, W, ok, px, py, &s);
+                    int kk = -1;
+                    for (int k = 0; k < 4; ++k)
+                        if (s.w[k] != 0.0 && s.tx[k] == x && s.ty[k] == y) kk = k;
+                    if (kk < 0) continue;
+                    /* the view pixel's composite, residual, transmittances and below-composite */
+                    double C[3];
+                    render_pixel(M, D, H, W, rho, ref, &views[i], qx, qy, C);
+                    double r[3];
+                    for (int c = 0; c < 3; ++c)
+                        r[c] = (C[c] - images[(((size_t)i * H + qy) * W + qx) * 3 + c]) / N;
+                    double Tr = 1.0;
+                    for (int e = D - 1; e >= 0; --e) {
+                        double ex, ey;
+                        int oke = orc_view_to_ref(ref, &views[i], 1.0 / rho[e], qx, qy, &ex, &ey);
+                        sample_plane(M, e, H, W, oke, ex, ey, &smp[e]);
+                        T[e] = Tr;
+                        Tr *= (1.0 - smp[e].m[3]);
+                    }
+                    double B[3] = {0, 0, 0};
+                    for (int e = 0; e < d; ++e)
+                        for (int c = 0; c < 3; ++c) B[c] = smp[e].m[c] * smp[e].m[3] + (1.0 - smp[e].m[3]) * B[c];
+                    double g[4];
+                    sample_gradient(smp[d].m, T[d], B, r, g);
+                    for (int c = 0; c < 4; ++c) acc[c] += smp[d].w[kk] * g[c];
+                }
+            }
+        }
+        for (int c = 0; c < 4; ++c) out[(size_t)j * 4 + c] = acc[c];
+        free(T);
+        free(smp);
+    }
+    free(rho);
+}
+
 /* ------------------------------------------------------------ sparsification */
 
 /* Reference-view alpha weights A_d = alpha_d prod_{j>d}(1 - alpha_j)  (Eq. eq_gradient, eq_overA). */

@@ -305,6 +305,21 @@ def test_refine_bf16_storage_within_tolerance(rl, kernel_path, small):
     np.testing.assert_allclose(losses, L_o, rtol=2e-2)
 
 
+def test_refine_bf16_paper_size_within_tolerance(rl, paper):
+    """BF16 storage at the benchmark's size: 3-level refine (512x384, D=32, N=4, k=5) against the
+    FP64 oracle fed the GPU's selections (the oracle on all host cores, bit-identical)."""
+    sc = paper
+    m, M0, sels, losses = _gpu_refine_steps(rl, sc, 5, (2, 1, 0), torch.bfloat16)
+    oracle.set_threads(True)
+    try:
+        M_o, L_o, _ = oracle.refine(M0, sc.near, sc.far, sc.ref, sc.src, sc.images, 5, (2, 1, 0), S_pins=sels)
+    finally:
+        oracle.set_threads(False)
+    err = np.abs(m.data.float().cpu().numpy() - M_o)
+    assert err.max() <= TOL16, err.max()
+    np.testing.assert_allclose(losses, L_o, rtol=2e-2)
+
+
 def test_degenerate_one_plane_and_one_view(rl):
     sc = sg.make_scene(9, 12, 20, 1, 1, n_layers=(1, 1), f=20.0)
     m = _mpi(rl, sc)

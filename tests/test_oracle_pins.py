@@ -467,3 +467,21 @@ def test_hsgd_with_mvs_selection_updates_only_the_window(tiny_scene):
     S_want, _ = oracle.select_mvs(A, k)
     assert np.array_equal(S, S_want)
     assert np.all(np.diff(S.astype(int), axis=0) == 1)  # consecutive planes
+
+
+@pytest.mark.parametrize("poses", ["random", "grid4x2"])
+def test_voxel_gradient_equals_dense_gradient(poses):
+    """The brute-force gradient at chosen voxels (over the view pixels near each voxel's
+    projection) equals the dense adjoint of loss_grad bit for bit, at every voxel: borders,
+    planes behind nothing, rotated and translated views."""
+    if poses == "random":
+        sc = sg.make_scene(21, 18, 26, 5, 3, n_layers=(2, 3), novel="none")
+    else:
+        sc = sg.make_scene(22, 16, 24, 4, 8, n_layers=(2, 3), src_poses="grid4x2", novel="none", f=24.0)
+    _, G, _ = oracle.loss_grad(sc.coarse_mpi, sc.near, sc.far, sc.ref, sc.src, sc.images)
+    D, H, W = sc.D, sc.H, sc.W
+    dd, yy, xx = np.meshgrid(np.arange(D), np.arange(H), np.arange(W), indexing="ij")
+    g = oracle.grad_voxels(sc.coarse_mpi, sc.near, sc.far, sc.ref, sc.src, sc.images, dd.ravel(), yy.ravel(),
+                           xx.ravel())
+    assert np.array_equal(g.reshape(D, H, W, 4), G)
+    assert np.abs(G).max() > 0

@@ -342,8 +342,7 @@ rl_status reallife_warp_offsets(const rl_mpi* m, const rl_camera* view, float* o
 /* Kernel family for the warp kernels (render, gradient):
  *   0 (default) automatic: plane-parallel for launches of fewer than 2^19 pixel-views,
  *     per-pixel gather otherwise;
- *   1 TMA-staged plane windows wherever the MPI's row pitch is a multiple of 16 bytes
- *     (always for FP32; even W for BF16), plane-parallel elsewhere;
+ *   1 not used (a family of TMA-staged plane windows, measured slower and removed): RL_EINVAL;
  *   2 per-pixel gather (one thread per view pixel walks all planes);
  *   3 plane-parallel (warps own chunks of planes; chunks combined through the
  *     associativity of the over operator), 8 warps per block;

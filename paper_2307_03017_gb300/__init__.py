@@ -18,7 +18,7 @@ import torch
 from . import _lib
 
 __all__ = [
-    "RealLifeError", "Mpi", "make_mpi", "plane_inverse_depths",
+    "RealLifeError", "Mpi", "make_mpi",
     "reallife_workspace_bytes", "reallife_render", "reallife_hsgd_step", "reallife_refine",
     "reallife_downsample_f32", "reallife_select", "reallife_select_keys", "reallife_loss_grad",
     "reallife_sparse_update", "reallife_render_backward", "reallife_warp_offsets",
@@ -36,13 +36,6 @@ _DT = {torch.float32: F32, torch.bfloat16: BF16}
 
 def library_path() -> str:
     return _lib.path()
-
-
-def plane_inverse_depths(D: int, near: float, far: float) -> np.ndarray:
-    """Inverse depths of the planes (d = 0 farthest), uniform between 1/far and 1/near."""
-    if D == 1:
-        return np.array([1.0 / far])
-    return 1.0 / far + np.arange(D) / (D - 1) * (1.0 / near - 1.0 / far)
 
 
 class Mpi:
@@ -459,7 +452,7 @@ def reallife_strerror(status: int) -> str:
 
 
 def reallife_set_kernel_path(path: int):
-    """0: automatic (default); 1: TMA-staged windows; 2: per-pixel gather; 3: plane-parallel."""
+    """0: automatic (default); 2: per-pixel gather; 3-5: plane-parallel (1 is not used)."""
     _lib.check("reallife_set_kernel_path", _lib.lib().reallife_set_kernel_path(int(path)))
 
 

@@ -229,8 +229,8 @@ void launch_grad_t(const void* M, int D, int H, int W, const RLViews& views, con
 
 size_t rl_grad_num_blocks(int H, int W, int N) {
     const size_t own = (size_t)((W + kGradBX - 1) / kGradBX) * ((H + kGradBY - 1) / kGradBY) * N;
-    const size_t a = rl_grad_pp_num_blocks(H, W, N), b = rl_grad_tma_num_blocks(H, W, N);
-    return own > a ? (own > b ? own : b) : (a > b ? a : b);
+    const size_t a = rl_grad_pp_num_blocks(H, W, N);
+    return own > a ? own : a;
 }
 
 rl_status rl_launch_grad(const void* M, rl_dtype dt, int D, int H, int W, const RLViews& views, bool mode_loss,
@@ -238,12 +238,6 @@ rl_status rl_launch_grad(const void* M, rl_dtype dt, int D, int H, int W, const 
                          float inv_n, float* partials, int* nblocks, cudaStream_t s, float* loss_out,
                          unsigned* counter, float loss_scale) {
     const int path = rl_kernel_path(H, W, views.n);
-    if (path == 1) {
-        CUtensorMap map;
-        if (rl_encode_mpi_tmap(&map, M, dt, D, H, W))
-            return rl_launch_grad_tma(map, M, dt, D, H, W, views, mode_loss, images, img_level, grad_out, slots, G,
-                                      inv_n, partials, nblocks, s, loss_out, counter, loss_scale);
-    }
     if (path != 2)
         return rl_launch_grad_pp(M, dt, D, H, W, views, mode_loss, images, img_level, grad_out, slots, G, inv_n,
                                  partials, nblocks, s, loss_out, counter, loss_scale);

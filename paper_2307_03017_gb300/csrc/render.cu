@@ -170,10 +170,6 @@ __global__ void k_warp_offsets(int D, int H, int W, const __grid_constant__ RLVi
 rl_status rl_launch_render(const void* M, rl_dtype dt, int D, int H, int W, const RLViews& views, float* out,
                            cudaStream_t s) {
     const int path = rl_kernel_path(H, W, views.n);
-    if (path == 1) {
-        CUtensorMap map;
-        if (rl_encode_mpi_tmap(&map, M, dt, D, H, W)) return rl_launch_render_tma(map, M, dt, D, H, W, views, out, s);
-    }
     if (path != 2) return rl_launch_render_pp(M, dt, D, H, W, views, out, s);
     dim3 block(kRenderBX, kRenderBY);
     const int tiles_x = (W + kRenderBX - 1) / kRenderBX, tiles_y = (H + kRenderBY - 1) / kRenderBY;

@@ -27,17 +27,13 @@ struct RLTraceScope {
 // Device status word (bit RL_DEVFLAG_TIMEOUT: a bounded wait gave up); address on the
 // current device, or NULL if it cannot be resolved.
 unsigned int* rl_device_status_ptr();
-// Warp-kernel family for a launch over H x W pixels of n views: 1 TMA-staged windows
-// where the layout allows (plane-parallel otherwise), 2 per-pixel gather, 3 plane-parallel.
-// The automatic setting picks plane-parallel for launches of fewer than 2^19 pixel-views
-// (coarse pyramid levels, small requests), where per-pixel threads are too few to hide
-// gather latency, and per-pixel gather otherwise.
+// Warp-kernel family for a launch over H x W pixels of n views: 2 per-pixel gather,
+// 3 plane-parallel.  The automatic setting picks plane-parallel for launches of fewer than
+// 2^19 pixel-views (coarse pyramid levels, small requests), where per-pixel threads are too
+// few to hide gather latency, and per-pixel gather otherwise.
 int rl_kernel_path(int H, int W, int nviews);
-// The raw process-wide setting of reallife_set_kernel_path (0 to 5).
+// The raw process-wide setting of reallife_set_kernel_path (0, 2 to 5).
 int rl_kernel_path_setting();
-// TMA descriptor of an MPI [D][H][W][4] with the staging window box; false when the
-// layout cannot be described (row pitch not a multiple of 16 bytes, misaligned base).
-bool rl_encode_mpi_tmap(CUtensorMap* map, const void* M, rl_dtype dt, int D, int H, int W);
 
 // TMA descriptor of a BF16 activation volume [K][H][W][32] (16-byte aligned) with a box of
 // {32 channels, halo voxels along W} and 64-byte swizzling; false when it cannot be encoded.
@@ -61,8 +57,6 @@ inline bool rl_views_are_shifts(const RLViews& v) {
 
 rl_status rl_launch_render(const void* M, rl_dtype dt, int D, int H, int W, const RLViews& views, float* out,
                            cudaStream_t s);
-rl_status rl_launch_render_tma(const CUtensorMap& tmap, const void* M, rl_dtype dt, int D, int H, int W,
-                               const RLViews& views, float* out, cudaStream_t s);
 rl_status rl_launch_warp_offsets(int D, int H, int W, const RLViews& views, float* out, cudaStream_t s);
 
 // Fused warp + composite + residual + adjoint.  mode_loss: residual from images (full-res
@@ -78,11 +72,6 @@ rl_status rl_launch_grad(const void* M, rl_dtype dt, int D, int H, int W, const 
                          unsigned* counter = nullptr, float loss_scale = 0.f);
 // Largest number of loss partials any gradient kernel family writes.
 size_t rl_grad_num_blocks(int H, int W, int N);
-rl_status rl_launch_grad_tma(const CUtensorMap& tmap, const void* M, rl_dtype dt, int D, int H, int W,
-                             const RLViews& views, bool mode_loss, const float* images, int img_level,
-                             const float* grad_out, const uint8_t* slots, float* G, float inv_n, float* partials,
-                             int* nblocks, cudaStream_t s, float* loss_out, unsigned* counter, float loss_scale);
-size_t rl_grad_tma_num_blocks(int H, int W, int N);
 rl_status rl_launch_grad_pp(const void* M, rl_dtype dt, int D, int H, int W, const RLViews& views, bool mode_loss,
                             const float* images, int img_level, const float* grad_out, const uint8_t* slots, float* G,
                             float inv_n, float* partials, int* nblocks, cudaStream_t s, float* loss_out,

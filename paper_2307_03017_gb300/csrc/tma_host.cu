@@ -1,5 +1,5 @@
-// tma_host.cu -- host-side TMA descriptors, the device status word and the kernel-path
-// switch.
+// tma_host.cu -- host-side TMA descriptors of the learned update's activations, the device
+// status word and the kernel-path switch.
 #include <atomic>
 #include <mutex>
 
@@ -55,22 +55,6 @@ unsigned int* rl_device_status_ptr() {
     return g_status_ptr[dev];
 }
 
-bool rl_encode_mpi_tmap(CUtensorMap* map, const void* M, rl_dtype dt, int D, int H, int W) {
-    const size_t elt = dt == RL_F32 ? 4 : 2;
-    if (((uintptr_t)M & 15) != 0 || ((size_t)W * 4 * elt) % 16 != 0) return false;
-    PFN_cuTensorMapEncodeTiled_v12000 fn = encoder();
-    if (!fn) return false;
-    const cuuint64_t dims[3] = {(cuuint64_t)W * 4, (cuuint64_t)H, (cuuint64_t)D};
-    const cuuint64_t strides[2] = {(cuuint64_t)W * 4 * elt, (cuuint64_t)W * 4 * elt * H};
-    const cuuint32_t box[3] = {(cuuint32_t)rltma::BW * 4, (cuuint32_t)rltma::BH, 1};
-    const cuuint32_t estr[3] = {1, 1, 1};
-    const CUresult r = fn(map, dt == RL_F32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3,
-                          const_cast<void*>(M), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                          CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    return r == CUDA_SUCCESS;
-}
-
 bool rl_encode_act_tmap(CUtensorMap* map, const void* act, int K, int H, int W, int halo) {
     if (((uintptr_t)act & 15) != 0 || K < 1 || H < 1 || W < 1 || halo < 1 || halo > 256) return false;
     PFN_cuTensorMapEncodeTiled_v12000 fn = encoder();
@@ -90,7 +74,7 @@ bool rl_encode_act_tmap(CUtensorMap* map, const void* act, int K, int H, int W, 
 int rl_kernel_path_setting() { return g_path.load(std::memory_order_relaxed); }
 
 extern "C" rl_status reallife_set_kernel_path(int path) {
-    if (path < 0 || path > 5) return rl_fail(RL_EINVAL, "kernel path must be 0 to 5");
+    if (path < 0 || path == 1 || path > 5) return rl_fail(RL_EINVAL, "kernel path must be 0 or 2 to 5");
     g_path.store(path);
     return RL_OK;
 }

@@ -30,9 +30,9 @@ def rl():
     assert rl.reallife_device_status(clear=True) == 0  # no bounded wait gave up
 
 
-@pytest.fixture(params=[3, 4, 5, 1, 2], ids=["planepar", "planepar4", "planepar8", "tma", "gather"])
+@pytest.fixture(params=[3, 4, 5, 2], ids=["planepar", "planepar4", "planepar8", "gather"])
 def kernel_path(request, rl):
-    """Run a test with each warp-kernel family: plane-parallel, TMA-staged windows, per-pixel gather."""
+    """Run a test with each warp-kernel family: plane-parallel (8 or 4 warps a block), per-pixel gather."""
     rl.reallife_set_kernel_path(request.param)
     yield request.param
     rl.reallife_set_kernel_path(0)
@@ -338,13 +338,13 @@ def test_ragged_sizes_and_level_tails(rl, kernel_path):
 
 
 def test_kernel_families_agree_on_extreme_warps(rl):
-    """Large rotations and translations push samples out of the staged windows (fallback loads)."""
+    """Large rotations and translations: far-off taps, planes met behind the views."""
     rng = np.random.default_rng(7)
     sc = sg.make_scene(6, 64, 96, 6, 3, n_layers=(2, 3), f=96.0)
     cams = [sg.Camera(sc.ref.K, sg.random_rotation(rng, 25.0), rng.uniform(-0.6, 0.6, 3)) for _ in range(3)]
     g_out = _dev(rng.normal(size=(3, sc.H, sc.W, 3)).astype(np.float32))
     outs, grads = [], []
-    for path in (3, 4, 5, 1, 2):
+    for path in (3, 4, 5, 2):
         rl.reallife_set_kernel_path(path)
         m = _mpi(rl, sc)
         outs.append(rl.reallife_render(m, cams).cpu().numpy())

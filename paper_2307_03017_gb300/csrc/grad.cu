@@ -68,7 +68,7 @@ __device__ __forceinline__ void scatter4(float* __restrict__ G, const uint8_t* _
 
 // One block's tile of 32 x 4 view pixels of one view.  bid / nblocks index the block among
 // the launch's (or the batch item's) blocks for the loss epilogue.
-template <typename Tm, bool SPARSE, bool LOSS>
+template <typename Tm, bool SPARSE, bool LOSS, bool ANCH>
 __device__ __forceinline__ void grad_tile(const Tm* __restrict__ M, int D, int H, int W, const RLViews& views, int view,
                                           int qx, int qy, int tid, float* __restrict__ sT,
                                           const float* __restrict__ images, int img_level,
@@ -77,13 +77,17 @@ __device__ __forceinline__ void grad_tile(const Tm* __restrict__ M, int D, int H
                                           unsigned bid, unsigned nblocks, float* __restrict__ loss_out,
                                           unsigned* __restrict__ counter, float loss_scale) {
     float lsum = 0.f;
+    __shared__ RLAnchor sA;  // the tile's anchor: its centre pixel
+    if (ANCH)
+        rl_anchor_build(&sA, views, view, (qx & ~(kGradBX - 1)) + kGradBX / 2, qy - qy % kGradBY + kGradBY / 2, D,
+                        tid, kGradThreads);
     if (qx < W && qy < H) {
-        const RLWarp w = rl_warp_coeffs(views.v[view], (float)qx, (float)qy);
+        const RLPixWarp<ANCH> w = rl_pix_warp<ANCH>(sA, views.v[view], qx, qy);
         const size_t plane = (size_t)H * W * 4;
         float T = 1.f, c0 = 0.f, c1 = 0.f, c2 = 0.f;
 #pragma unroll 1
         for (int d = D - 1; d >= 0; --d) {
-            const RLTaps t = rl_taps(w, views.rho[d], qx, qy);
+            const RLTaps t = w.taps(sA, d, views.rho[d], qx, qy);
             const float4 m = rl_sample_fast(M + d * plane, H, W, t);
             sT[d * kGradThreads + tid] = T;
             const float a = T * m.w;
@@ -122,7 +126,7 @@ __device__ __forceinline__ void grad_tile(const Tm* __restrict__ M, int D, int H
         const unsigned hw = (unsigned)(H * W);
 #pragma unroll 1
         for (int d = 0; d < D; ++d) {
-            const RLTaps t = rl_taps(w, views.rho[d], qx, qy);
+            const RLTaps t = w.taps(sA, d, views.rho[d], qx, qy);
             const float4 m = rl_sample_fast(M + d * plane, H, W, t);
             const float Td = sT[d * kGradThreads + tid];
             if (t.ok && Td != 0.f) {
@@ -153,7 +157,7 @@ __device__ __forceinline__ void grad_tile(const Tm* __restrict__ M, int D, int H
     }
 }
 
-template <typename Tm, bool SPARSE, bool LOSS>
+template <typename Tm, bool SPARSE, bool LOSS, bool ANCH>
 __global__ void __launch_bounds__(kGradThreads, RL_GRAD_MIN_BLOCKS)
 k_grad(const Tm* __restrict__ M, int D, int H, int W, const __grid_constant__ RLViews views, int tiles_x,
        const float* __restrict__ images, int img_level, const float* __restrict__ grad_out,
@@ -161,7 +165,7 @@ k_grad(const Tm* __restrict__ M, int D, int H, int W, const __grid_constant__ RL
        float* __restrict__ loss_out, unsigned* __restrict__ counter, float loss_scale) {
     extern __shared__ float sT[];  // [D][kGradThreads]
     // view-fastest block order: the N views of a tile run together and share M through L2
-    grad_tile<Tm, SPARSE, LOSS>(M, D, H, W, views, blockIdx.x, blockIdx.y * kGradBX + threadIdx.x,
+    grad_tile<Tm, SPARSE, LOSS, ANCH>(M, D, H, W, views, blockIdx.x, blockIdx.y * kGradBX + threadIdx.x,
                                 blockIdx.z * kGradBY + threadIdx.y, threadIdx.y * kGradBX + threadIdx.x, sT, images,
                                 img_level, grad_out, slots, G, inv_n, partials,
                                 blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z),
@@ -191,10 +195,13 @@ k_grad_batch(const RLBatchHeader* __restrict__ hdr, const RLBatchItem* __restric
         const unsigned view = local % (unsigned)it.N, tile = local / (unsigned)it.N;
         const int tx = (int)(tile % it.grad_tiles_x), ty = (int)(tile / it.grad_tiles_x);
         const int h = it.H >> it.level, w = it.W >> it.level;
-        grad_tile<Tm, true, true>(static_cast<const Tm*>(it.Ml), it.D, h, w, it.views, (int)view,
-                                  tx * kGradBX + threadIdx.x, ty * kGradBY + threadIdx.y, tid, sT, it.images,
-                                  it.level, nullptr, it.slots, it.G, it.inv_n, it.partials, local, it.grad_units,
-                                  it.loss_out, it.counter, it.loss_scale);
+#define RL_GB(A) grad_tile<Tm, true, true, A>(static_cast<const Tm*>(it.Ml), it.D, h, w, it.views, (int)view,    \
+                                             tx * kGradBX + threadIdx.x, ty * kGradBY + threadIdx.y, tid, sT,       \
+                                             it.images, it.level, nullptr, it.slots, it.G, it.inv_n, it.partials,   \
+                                             local, it.grad_units, it.loss_out, it.counter, it.loss_scale)
+        if (it.views.anchored) RL_GB(true);
+        else RL_GB(false);
+#undef RL_GB
         __syncthreads();  // sT is reused by the next unit
     }
 }
@@ -219,7 +226,7 @@ template <typename Tm, bool SPARSE, bool LOSS>
 void launch_grad_t(const void* M, int D, int H, int W, const RLViews& views, const float* images, int img_level,
                    const float* grad_out, const uint8_t* slots, float* G, float inv_n, float* partials, float* loss_out,
                    unsigned* counter, float loss_scale, int tiles_x, dim3 grid, size_t smem, cudaStream_t s) {
-    auto kern = k_grad<Tm, SPARSE, LOSS>;
+    auto kern = views.anchored ? k_grad<Tm, SPARSE, LOSS, true> : k_grad<Tm, SPARSE, LOSS, false>;
     if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     kern<<<grid, dim3(kGradBX, kGradBY), smem, s>>>((const Tm*)M, D, H, W, views, tiles_x, images, img_level, grad_out,
                                                     slots, G, inv_n, partials, loss_out, counter, loss_scale);

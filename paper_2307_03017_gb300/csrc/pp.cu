@@ -120,21 +120,25 @@ __device__ __forceinline__ PixelCoord pixel_coord(int H, int W) {
     return pixel_coord_at(H, W, blockIdx.x, blockIdx.y, blockIdx.z);
 }
 
-template <typename Tm, int C, int kGroups>
+template <typename Tm, int C, int kGroups, bool ANCH>
 __global__ void __launch_bounds__(kGroups * kPix)
 k_render_pp(const Tm* __restrict__ M, int D, int H, int W, const __grid_constant__ RLViews views, int tiles_x,
             float* __restrict__ out) {
     __shared__ float4 xch[kGroups][kPix];  // per chunk: (Cc.rgb, Tc)
+    __shared__ RLAnchor sA;
     const PixelCoord pc = pixel_coord(H, W);
+    if (ANCH)
+        rl_anchor_build(&sA, views, pc.view, blockIdx.y * kTX + kTX / 2, blockIdx.z * kTY + kTY / 2, D, threadIdx.x,
+                        kGroups * kPix);
     const int qx = min(pc.qx, W - 1), qy = min(pc.qy, H - 1);
-    const RLWarp w = rl_warp_coeffs(views.v[pc.view], (float)qx, (float)qy);
+    const RLPixWarp<ANCH> w = rl_pix_warp<ANCH>(sA, views.v[pc.view], qx, qy);
     const size_t plane = (size_t)H * W * 4;
     float Tl = 1.f, c0 = 0.f, c1 = 0.f, c2 = 0.f;
 #pragma unroll
     for (int i = C - 1; i >= 0; --i) {
         const int d = pc.g * C + i;
         if (d < D) {
-            const RLTaps t = rl_taps(w, views.rho[d], qx, qy);
+            const RLTaps t = w.taps(sA, d, views.rho[d], qx, qy);
             const float4 m = sample_pp(M + d * plane, H, W, t);
             const float a = Tl * m.w;
             c0 = fmaf(a, m.x, c0);
@@ -164,7 +168,7 @@ k_render_pp(const Tm* __restrict__ M, int D, int H, int W, const __grid_constant
 
 // One block's tile (kPix view pixels of one view, all planes): the body of k_grad_pp, with the
 // tile, the exchange buffers and the block's index for the loss epilogue given explicitly.
-template <typename Tm, int C, int kGroups, bool SPARSE, bool LOSS>
+template <typename Tm, int C, int kGroups, bool SPARSE, bool LOSS, bool ANCH>
 __device__ __forceinline__ void grad_pp_tile(const Tm* __restrict__ M, int D, int H, int W, const RLViews& views,
                                              const PixelCoord pc, const float* __restrict__ images, int img_level,
                                              const float* __restrict__ grad_out, const uint8_t* __restrict__ slots,
@@ -172,8 +176,12 @@ __device__ __forceinline__ void grad_pp_tile(const Tm* __restrict__ M, int D, in
                                              unsigned bid, unsigned nblocks, float* __restrict__ loss_out,
                                              unsigned* __restrict__ counter, float loss_scale,
                                              float4 (*__restrict__ xch)[kPix], float* __restrict__ red) {
+    __shared__ RLAnchor sA;
+    if (ANCH)
+        rl_anchor_build(&sA, views, pc.view, (pc.qx - pc.qx % kTX) + kTX / 2, (pc.qy - pc.qy % kTY) + kTY / 2, D,
+                        threadIdx.x, kGroups * kPix);
     const int qx = min(pc.qx, W - 1), qy = min(pc.qy, H - 1);
-    const RLWarp w = rl_warp_coeffs(views.v[pc.view], (float)qx, (float)qy);
+    const RLPixWarp<ANCH> w = rl_pix_warp<ANCH>(sA, views.v[pc.view], qx, qy);
     const size_t plane = (size_t)H * W * 4;
 
     // forward over this thread's chunk, nearest plane first; samples stay in registers
@@ -186,7 +194,7 @@ __device__ __forceinline__ void grad_pp_tile(const Tm* __restrict__ M, int D, in
         m[i] = make_float4(0.f, 0.f, 0.f, 0.f);
         Tloc[i] = Tl;
         if (d < D) {
-            const RLTaps t = rl_taps(w, views.rho[d], qx, qy);
+            const RLTaps t = w.taps(sA, d, views.rho[d], qx, qy);
             m[i] = sample_pp(M + d * plane, H, W, t);
             const float a = Tl * m[i].w;
             c0 = fmaf(a, m[i].x, c0);
@@ -254,7 +262,7 @@ __device__ __forceinline__ void grad_pp_tile(const Tm* __restrict__ M, int D, in
                 const float Td = Tb * Tloc[i];
                 const float4 mi = m[i];
                 if (Td != 0.f) {
-                    const RLTaps t = rl_taps(w, views.rho[d], pc.qx, pc.qy);
+                    const RLTaps t = w.taps(sA, d, views.rho[d], pc.qx, pc.qy);
                     if (t.ok) {
                         const float gc = Td * mi.w;
                         float4 g;
@@ -285,7 +293,7 @@ __device__ __forceinline__ void grad_pp_tile(const Tm* __restrict__ M, int D, in
     }
 }
 
-template <typename Tm, int C, int kGroups, bool SPARSE, bool LOSS>
+template <typename Tm, int C, int kGroups, bool SPARSE, bool LOSS, bool ANCH>
 __global__ void __launch_bounds__(kGroups * kPix)
 k_grad_pp(const Tm* __restrict__ M, int D, int H, int W, const __grid_constant__ RLViews views, int tiles_x,
           const float* __restrict__ images, int img_level, const float* __restrict__ grad_out,
@@ -293,7 +301,7 @@ k_grad_pp(const Tm* __restrict__ M, int D, int H, int W, const __grid_constant__
           float* __restrict__ loss_out, unsigned* __restrict__ counter, float loss_scale) {
     __shared__ float4 xch[kGroups][kPix];
     __shared__ float red[kGroups];
-    grad_pp_tile<Tm, C, kGroups, SPARSE, LOSS>(M, D, H, W, views, pixel_coord(H, W), images, img_level, grad_out,
+    grad_pp_tile<Tm, C, kGroups, SPARSE, LOSS, ANCH>(M, D, H, W, views, pixel_coord(H, W), images, img_level, grad_out,
                                                slots, G, inv_n, partials,
                                                blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z),
                                                gridDim.x * gridDim.y * gridDim.z, loss_out, counter, loss_scale, xch,
@@ -320,14 +328,22 @@ k_grad_pp_batch(const RLBatchHeader* __restrict__ hdr, const RLBatchItem* __rest
         const PixelCoord pc =
             pixel_coord_at(h, w, (int)view, (int)(tile % it.pp_tiles_x), (int)(tile / it.pp_tiles_x));
         const Tm* Ml = static_cast<const Tm*>(it.Ml);
-#define RL_PPB(CC) grad_pp_tile<Tm, CC, 8, true, true>(Ml, it.D, h, w, it.views, pc, it.images, it.level, nullptr, \
-                                                      it.slots, it.G, it.inv_n, it.partials, local, it.pp_units, \
-                                                      it.loss_out, it.counter, it.loss_scale, xch, red)
+#define RL_PPB(CC, A) grad_pp_tile<Tm, CC, 8, true, true, A>(Ml, it.D, h, w, it.views, pc, it.images, it.level,   \
+                                                             nullptr, it.slots, it.G, it.inv_n, it.partials, local, \
+                                                             it.pp_units, it.loss_out, it.counter, it.loss_scale,   \
+                                                             xch, red)
         const int c = (it.D + 7) / 8;
-        if (c <= 1) RL_PPB(1);
-        else if (c <= 2) RL_PPB(2);
-        else if (c <= 4) RL_PPB(4);
-        else RL_PPB(8);
+        if (it.views.anchored) {
+            if (c <= 1) RL_PPB(1, true);
+            else if (c <= 2) RL_PPB(2, true);
+            else if (c <= 4) RL_PPB(4, true);
+            else RL_PPB(8, true);
+        } else {
+            if (c <= 1) RL_PPB(1, false);
+            else if (c <= 2) RL_PPB(2, false);
+            else if (c <= 4) RL_PPB(4, false);
+            else RL_PPB(8, false);
+        }
 #undef RL_PPB
         __syncthreads();  // the exchange buffers are reused by the next unit
     }
@@ -353,8 +369,16 @@ void launch_grad_pp_t(int G, int C, const void* M, int D, int H, int W, const RL
                       cudaStream_t s) {
 #define RL_PP_ARGS (const Tm*)M, D, H, W, views, tiles_x, images, img_level, grad_out, slots, G_, inv_n, partials, \
                    loss_out, counter, loss_scale
-#define RL_PP_LAUNCH(CC, GG) k_grad_pp<Tm, CC, GG, SPARSE, LOSS><<<grid, GG * kPix, 0, s>>>(RL_PP_ARGS)
-    if (G == 4) {
+#define RL_PP_LAUNCH(CC, GG) k_grad_pp<Tm, CC, GG, SPARSE, LOSS, false><<<grid, GG * kPix, 0, s>>>(RL_PP_ARGS)
+#define RL_PP_LAUNCH_A(CC) k_grad_pp<Tm, CC, 8, SPARSE, LOSS, true><<<grid, 8 * kPix, 0, s>>>(RL_PP_ARGS)
+    if (views.anchored) {  // 8 warps a block (the 4-warp option keeps the FP32 coordinates only)
+        switch (C) {
+            case 1: RL_PP_LAUNCH_A(1); break;
+            case 2: RL_PP_LAUNCH_A(2); break;
+            case 4: RL_PP_LAUNCH_A(4); break;
+            default: RL_PP_LAUNCH_A(8); break;
+        }
+    } else if (G == 4) {
         switch (C) {
             case 1: RL_PP_LAUNCH(1, 4); break;
             case 2: RL_PP_LAUNCH(2, 4); break;
@@ -369,6 +393,7 @@ void launch_grad_pp_t(int G, int C, const void* M, int D, int H, int W, const RL
             default: RL_PP_LAUNCH(8, 8); break;
         }
     }
+#undef RL_PP_LAUNCH_A
 #undef RL_PP_LAUNCH
 #undef RL_PP_ARGS
 }
@@ -377,8 +402,17 @@ template <typename Tm>
 void launch_render_pp_t(int G, int C, const void* M, int D, int H, int W, const RLViews& views, int tiles_x,
                         dim3 grid, float* out, cudaStream_t s) {
 #define RL_PP_LAUNCH(CC, GG) \
-    k_render_pp<Tm, CC, GG><<<grid, GG * kPix, 0, s>>>((const Tm*)M, D, H, W, views, tiles_x, out)
-    if (G == 4) {
+    k_render_pp<Tm, CC, GG, false><<<grid, GG * kPix, 0, s>>>((const Tm*)M, D, H, W, views, tiles_x, out)
+#define RL_PP_LAUNCH_A(CC) \
+    k_render_pp<Tm, CC, 8, true><<<grid, 8 * kPix, 0, s>>>((const Tm*)M, D, H, W, views, tiles_x, out)
+    if (views.anchored) {
+        switch (C) {
+            case 1: RL_PP_LAUNCH_A(1); break;
+            case 2: RL_PP_LAUNCH_A(2); break;
+            case 4: RL_PP_LAUNCH_A(4); break;
+            default: RL_PP_LAUNCH_A(8); break;
+        }
+    } else if (G == 4) {
         switch (C) {
             case 1: RL_PP_LAUNCH(1, 4); break;
             case 2: RL_PP_LAUNCH(2, 4); break;
@@ -409,7 +443,7 @@ rl_status rl_launch_grad_pp(const void* M, rl_dtype dt, int D, int H, int W, con
     const int tiles_x = (W + kTX - 1) / kTX;
     const dim3 grid((unsigned)views.n, (unsigned)tiles_x, (unsigned)((H + kTY - 1) / kTY));
     if (nblocks) *nblocks = (int)rl_grad_pp_num_blocks(H, W, views.n);
-    const int G = groups_for(D, rl_kernel_path_setting());
+    const int G = views.anchored ? 8 : groups_for(D, rl_kernel_path_setting());
     const int C = chunk_for(D, G);
     const bool sparse = slots != nullptr;
     const char* name = dt == RL_F32 ? (sparse ? "grad_sparse_f32" : "grad_dense_f32")
@@ -433,7 +467,7 @@ rl_status rl_launch_render_pp(const void* M, rl_dtype dt, int D, int H, int W, c
                               cudaStream_t s) {
     const int tiles_x = (W + kTX - 1) / kTX;
     const dim3 grid((unsigned)views.n, (unsigned)tiles_x, (unsigned)((H + kTY - 1) / kTY));
-    const int G = groups_for(D, rl_kernel_path_setting());
+    const int G = views.anchored ? 8 : groups_for(D, rl_kernel_path_setting());
     const int C = chunk_for(D, G);
     if (dt == RL_F32) {
         RLTraceScope ts("render_f32", s);

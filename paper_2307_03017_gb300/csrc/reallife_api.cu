@@ -208,8 +208,9 @@ rl_camera camera_at_level(const rl_camera& c, int level) {
 }
 
 // Relative pose of `view` w.r.t. the reference camera (Eq. eq_homo's R_i R_r^{-1} and
-// t_i - R_i R_r^{-1} t_r), reduced to the per-pixel warp parameters of rl_common.cuh.
-RLViewParam view_param(const rl_camera& ref, const rl_camera& view) {
+// t_i - R_i R_r^{-1} t_r), reduced to the per-pixel warp parameters of rl_common.cuh, in
+// FP64 (the kernels' per-block anchors) and rounded to FP32 (their per-pixel differences).
+RLViewParam64 view_param64(const rl_camera& ref, const rl_camera& view) {
     double Rrel[9];  // R_v R_r^T
     for (int a = 0; a < 3; ++a)
         for (int b = 0; b < 3; ++b) {
@@ -217,26 +218,77 @@ RLViewParam view_param(const rl_camera& ref, const rl_camera& view) {
             for (int j = 0; j < 3; ++j) s += view.R[a * 3 + j] * ref.R[b * 3 + j];
             Rrel[a * 3 + b] = s;
         }
-    RLViewParam P;
+    RLViewParam64 P;
     for (int a = 0; a < 3; ++a)
-        for (int b = 0; b < 3; ++b) P.E[a * 3 + b] = (float)(Rrel[b * 3 + a] - (a == b ? 1.0 : 0.0));
+        for (int b = 0; b < 3; ++b) P.E[a * 3 + b] = Rrel[b * 3 + a] - (a == b ? 1.0 : 0.0);
     // centre of the view in the reference frame: -R_rel^T t_v + t_r
     for (int a = 0; a < 3; ++a) {
         double s = 0.0;
         for (int j = 0; j < 3; ++j) s += Rrel[j * 3 + a] * view.t[j];
-        P.C[a] = (float)(ref.t[a] - s);
+        P.C[a] = ref.t[a] - s;
     }
-    P.inv_fxv = (float)(1.0 / view.K[0]);
-    P.inv_fyv = (float)(1.0 / view.K[4]);
-    P.cxv = (float)view.K[2];
-    P.cyv = (float)view.K[5];
-    P.fxr = (float)ref.K[0];
-    P.fyr = (float)ref.K[4];
-    P.dcx = (float)(ref.K[2] - view.K[2]);
-    P.dcy = (float)(ref.K[5] - view.K[5]);
-    P.dfx = (float)(ref.K[0] - view.K[0]);
-    P.dfy = (float)(ref.K[4] - view.K[4]);
+    P.inv_fxv = 1.0 / view.K[0];
+    P.inv_fyv = 1.0 / view.K[4];
+    P.cxv = view.K[2];
+    P.cyv = view.K[5];
+    P.fxr = ref.K[0];
+    P.fyr = ref.K[4];
+    P.dcx = ref.K[2] - view.K[2];
+    P.dcy = ref.K[5] - view.K[5];
+    P.dfx = ref.K[0] - view.K[0];
+    P.dfy = ref.K[4] - view.K[4];
     return P;
+}
+
+RLViewParam view_param(const RLViewParam64& Q) {
+    RLViewParam P;
+    for (int j = 0; j < 9; ++j) P.E[j] = (float)Q.E[j];
+    for (int j = 0; j < 3; ++j) P.C[j] = (float)Q.C[j];
+    P.inv_fxv = (float)Q.inv_fxv;
+    P.inv_fyv = (float)Q.inv_fyv;
+    P.cxv = (float)Q.cxv;
+    P.cyv = (float)Q.cyv;
+    P.fxr = (float)Q.fxr;
+    P.fyr = (float)Q.fyr;
+    P.dcx = (float)Q.dcx;
+    P.dcy = (float)Q.dcy;
+    P.dfx = (float)Q.dfx;
+    P.dfy = (float)Q.dfy;
+    return P;
+}
+
+// Largest |p - q| = |a(q) + rho b(q)| over the image's corners and centre and the nearest and
+// farthest planes (FP64): the offsets are smooth in q and linear in rho.
+double max_offset(const RLViewParam64& P, int H, int W, double rho_lo, double rho_hi) {
+    double hi = 0.0;
+    for (int c = 0; c < 5; ++c) {
+        const double u = c == 4 ? 0.5 * W : ((c & 1) ? W - 1.0 : 0.0);
+        const double v = c == 4 ? 0.5 * H : ((c & 2) ? H - 1.0 : 0.0);
+        const double mx = (u - P.cxv) * P.inv_fxv, my = (v - P.cyv) * P.inv_fyv;
+        const double ex = P.E[0] * mx + P.E[1] * my + P.E[2], ey = P.E[3] * mx + P.E[4] * my + P.E[5];
+        const double dz = 1.0 + P.E[6] * mx + P.E[7] * my + P.E[8];
+        const double rmx = (ex - mx * (dz - 1.0)) / dz, rmy = (ey - my * (dz - 1.0)) / dz;
+        const double ax = P.dcx + P.dfx * mx + P.fxr * rmx, ay = P.dcy + P.dfy * my + P.fyr * rmy;
+        const double bx = P.fxr * (P.C[0] - P.C[2] * (mx + rmx)), by = P.fyr * (P.C[1] - P.C[2] * (my + rmy));
+        for (double r : {rho_lo, rho_hi}) hi = std::max(hi, std::max(std::fabs(ax + r * bx), std::fabs(ay + r * by)));
+    }
+    return hi;
+}
+
+// Offsets beyond which the kernels take the anchored coordinates (rl_common.cuh).
+constexpr double kAnchorOffsetPx = 128.0;
+
+// Smallest 1 + e_z (the cosine-like factor of the view's ray direction in the reference
+// frame) over the image of W x H pixels and a margin of half a block: it is linear in the
+// pixel, so the extremes lie at the corners.
+double min_ray_dz(const RLViewParam64& P, int H, int W) {
+    double lo = 1e300;
+    for (int c = 0; c < 4; ++c) {
+        const double u = (c & 1) ? W + 16.0 : -16.0, v = (c & 2) ? H + 4.0 : -4.0;
+        const double mx = (u - P.cxv) * P.inv_fxv, my = (v - P.cyv) * P.inv_fyv;
+        lo = std::min(lo, 1.0 + P.E[6] * mx + P.E[7] * my + P.E[8]);
+    }
+    return lo;
 }
 
 // Inverse warp parameters (reference -> view) of rl_common.cuh for one view.
@@ -270,10 +322,14 @@ RLInvParam inv_view_param(const rl_camera& ref, const rl_camera& view) {
 }
 
 void fill_rho(RLViews& v, int D, double near_, double far_) {
-    for (int d = 0; d < RL_DEV_MAX_PLANES; ++d) v.rho[d] = 0.f;
+    for (int d = 0; d < RL_DEV_MAX_PLANES; ++d) {
+        v.rho[d] = 0.f;
+        v.rho64[d] = 0.0;
+    }
     for (int d = 0; d < D; ++d) {
         const double r = (D == 1) ? 1.0 / far_ : 1.0 / far_ + ((double)d / (double)(D - 1)) * (1.0 / near_ - 1.0 / far_);
         v.rho[d] = (float)r;
+        v.rho64[d] = r;
     }
 }
 
@@ -299,9 +355,17 @@ rl_status make_views(const rl_mpi* m, const rl_camera* cams, int n, int level, R
     v.n = n;
     fill_rho(v, m->D, m->near_, m->far_);
     const rl_camera ref = camera_at_level(m->ref, level);
+    const int H = m->H >> level, W = m->W >> level;
     for (int i = 0; i < n; ++i) {
         if (!camera_ok(cams[i])) return rl_fail(RL_EINVAL, "camera %d invalid (zero-skew K, orthonormal R)", i);
-        v.v[i] = view_param(ref, camera_at_level(cams[i], level));
+        v.v64[i] = view_param64(ref, camera_at_level(cams[i], level));
+        v.v[i] = view_param(v.v64[i]);
+        if (max_offset(v.v64[i], H, W, v.rho64[0], v.rho64[m->D - 1]) > kAnchorOffsetPx) v.anchored = 1;
+        if (!(min_ray_dz(v.v64[i], H, W) > 0.05))
+            return rl_fail(RL_EINVAL,
+                           "camera %d: its rays at the image corners run nearly parallel to the reference planes "
+                           "(1 + e_z <= 0.05); such views are not supported",
+                           i);
     }
     return RL_OK;
 }

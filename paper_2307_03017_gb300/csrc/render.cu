@@ -1,7 +1,8 @@
 // render.cu -- novel-view rendering (Eq. eq_render, Eq. eq_over) and warp diagnostics.
 //
 // One thread per target pixel: for d = D-1 .. 0 (nearest first) sample plane d at
-// p = q + a(q) + rho_d b(q) (bilinear, zero padding per tap) and accumulate
+// p = q + a(q) + rho_d b(q) (bilinear, zero padding per tap; coordinates anchored per block in
+// FP64, rl_common.cuh) and accumulate
 // C += T alpha c, T *= (1 - alpha).  The loop stops once T is exactly zero, after which
 // every further term is exactly zero.  Views that are pure shifts of the reference (no
 // rotation, no depth offset, same focal lengths) take a kernel that computes each plane's
@@ -18,20 +19,25 @@ constexpr int kRenderBX = 32, kRenderBY = 4;
 
 // Blocks are ordered view-fastest (grid x = view) so that the views of a tile, whose plane
 // footprints overlap, run together and share the MPI through L2.
-template <typename Tm>
+template <typename Tm, bool ANCH>
 __global__ void __launch_bounds__(kRenderBX* kRenderBY, RL_RENDER_MIN_BLOCKS)
 k_render(const Tm* __restrict__ M, int D, int H, int W, const __grid_constant__ RLViews views, int tiles_x,
          float* __restrict__ out) {
+    __shared__ RLAnchor sA;
     const int view = blockIdx.x;  // grid (views, tiles_x, tiles_y): views of a tile run together
+    if (ANCH)
+        rl_anchor_build(&sA, views, view, blockIdx.y * kRenderBX + kRenderBX / 2,
+                        blockIdx.z * kRenderBY + kRenderBY / 2, D, threadIdx.y * kRenderBX + threadIdx.x,
+                        kRenderBX * kRenderBY);
     const int qx = blockIdx.y * kRenderBX + threadIdx.x;
     const int qy = blockIdx.z * kRenderBY + threadIdx.y;
     if (qx >= W || qy >= H) return;
-    const RLWarp w = rl_warp_coeffs(views.v[view], (float)qx, (float)qy);
+    const RLPixWarp<ANCH> w = rl_pix_warp<ANCH>(sA, views.v[view], qx, qy);
     const size_t plane = (size_t)H * W * 4;
     float T = 1.f, c0 = 0.f, c1 = 0.f, c2 = 0.f;
 #pragma unroll 1
     for (int d = D - 1; d >= 0; --d) {
-        const RLTaps t = rl_taps(w, views.rho[d], qx, qy);
+        const RLTaps t = w.taps(sA, d, views.rho[d], qx, qy);
         const float4 m = rl_sample_fast(M + d * plane, H, W, t);
         const float a = T * m.w;
         c0 = fmaf(a, m.x, c0);
@@ -48,9 +54,9 @@ k_render(const Tm* __restrict__ M, int D, int H, int W, const __grid_constant__ 
 
 // Views with no rotation relative to the reference, no depth offset and the reference's
 // focal lengths: the warp offset p - q = a + rho_d b is the same for every pixel of a plane,
-// so the taps' integer shift and the bilinear weights are computed once per plane (by the
-// first D threads of a block, with the arithmetic of rl_taps / rl_sample_fast) and read from
-// shared memory.  Same samples, same results as k_render.
+// so the taps' integer shift and the bilinear weights are computed once per plane from the
+// block's FP64 anchor table (rl_common.cuh) and read from shared memory.  Same samples, same
+// results as k_render.
 struct RLPlaneShift {
     int ix, iy, ok;
     float fx, fy;
@@ -63,22 +69,25 @@ struct RLPlaneShift {
 constexpr int kShiftRows = 4;
 
 template <typename Tm>
-__global__ void __launch_bounds__(kRenderBX* kRenderBY)
+__global__ void __launch_bounds__(kRenderBX* kRenderBY, 8)
 k_render_shift(const Tm* __restrict__ M, int D, int H, int W, const __grid_constant__ RLViews views,
                float* __restrict__ out) {
     __shared__ RLPlaneShift sp[RL_DEV_MAX_PLANES];
     const int view = blockIdx.x;  // grid (views, tiles_x, tiles_y of kRenderBY * kShiftRows rows)
     const int tid = threadIdx.y * kRenderBX + threadIdx.x;
     if (tid < D) {
-        const RLWarp w = rl_warp_coeffs(views.v[view], 0.f, 0.f);  // the same for every pixel
-        const float dx = fmaf(views.rho[tid], w.bx, w.ax), dy = fmaf(views.rho[tid], w.by, w.ay);
-        const float flx = floorf(dx), fly = floorf(dy);
+        // a pure shift: p - q = (c_r - c_v) + rho_d f_r C_xy for every pixel, formed in FP64 and
+        // split into an integer and an FP32 fraction (the anchors of rl_common.cuh, exactly)
+        const RLViewParam64& P = views.v64[view];
+        const double rho = views.rho64[tid];
+        const double kx = P.dcx + rho * (P.fxr * P.C[0]), ky = P.dcy + rho * (P.fyr * P.C[1]);
+        const double flx = floor(kx), fly = floor(ky);
         RLPlaneShift p;
-        p.ix = (int)flx;
-        p.iy = (int)fly;
-        p.fx = dx - flx;
-        p.fy = dy - fly;
-        p.ok = fabsf(dx) < 1.0e7f && fabsf(dy) < 1.0e7f;  // as rl_taps
+        p.ok = fabs(kx) < 1e9 && fabs(ky) < 1e9;
+        p.ix = p.ok ? (int)flx : 0;
+        p.iy = p.ok ? (int)fly : 0;
+        p.fx = (float)(kx - flx);
+        p.fy = (float)(ky - fly);
         p.w00 = (1.f - p.fx) * (1.f - p.fy);
         p.w10 = p.fx * (1.f - p.fy);
         p.w01 = (1.f - p.fx) * p.fy;
@@ -188,10 +197,14 @@ rl_status rl_launch_render(const void* M, rl_dtype dt, int D, int H, int W, cons
     }
     if (dt == RL_F32) {
         RLTraceScope ts("render_f32", s);
-        k_render<float><<<grid, block, 0, s>>>((const float*)M, D, H, W, views, tiles_x, out);
+        if (views.anchored) k_render<float, true><<<grid, block, 0, s>>>((const float*)M, D, H, W, views, tiles_x, out);
+        else k_render<float, false><<<grid, block, 0, s>>>((const float*)M, D, H, W, views, tiles_x, out);
     } else {
         RLTraceScope ts("render_bf16", s);
-        k_render<__nv_bfloat16><<<grid, block, 0, s>>>((const __nv_bfloat16*)M, D, H, W, views, tiles_x, out);
+        if (views.anchored)
+            k_render<__nv_bfloat16, true><<<grid, block, 0, s>>>((const __nv_bfloat16*)M, D, H, W, views, tiles_x, out);
+        else
+            k_render<__nv_bfloat16, false><<<grid, block, 0, s>>>((const __nv_bfloat16*)M, D, H, W, views, tiles_x, out);
     }
     return rl_check_launch("render");
 }

@@ -28,11 +28,20 @@ struct RLViewParam {
     float dfx, dfy;      // fx_r - fx_v, fy_r - fy_v
 };
 
+// The same parameters in FP64, for the per-block anchors below.
+struct RLViewParam64 {
+    double E[9], C[3];
+    double inv_fxv, inv_fyv, cxv, cyv, fxr, fyr, dcx, dcy, dfx, dfy;
+};
+
 // Views and plane inverse depths of one launch, passed by value as a kernel parameter.
 struct RLViews {
     int n;
+    int anchored;  // 1: the kernels take the anchored coordinates below (offsets beyond ~128 px)
     float rho[RL_DEV_MAX_PLANES];
     RLViewParam v[RL_DEV_MAX_VIEWS];
+    double rho64[RL_DEV_MAX_PLANES];
+    RLViewParam64 v64[RL_DEV_MAX_VIEWS];
 };
 
 // ------------------------------------------------------------------ batch work tables
@@ -147,6 +156,166 @@ __device__ __forceinline__ RLTaps rl_taps(const RLWarp& w, float rho, int qx, in
     t.y0 = qy + (int)fly;
     t.ok = w.dir_ok && (fmaf(-rho, w.cz, 1.0f) > 0.0f) && fabsf(dx) < 1.0e7f && fabsf(dy) < 1.0e7f;
     return t;
+}
+
+// ------------------------------------------------------------------ anchored warp coordinates
+//
+// The offset p - q = a(q) + rho_d b(q) reaches hundreds of pixels for wide baselines and
+// rotated views (|a|, |b| up to ~400 px at 1920 x 1080), where FP32 spacing is ~3e-5 px.  So
+// each block evaluates the warp once at an anchor pixel q_c in FP64 and keeps, for every
+// plane, the offset at the anchor split into an integer and an FP32 fraction; a pixel of the
+// block adds the small FP32 differences a(q) - a(q_c) and b(q) - b(q_c), formed without
+// cancellation (exact algebra, small terms only):
+//   dm = K_v^{-1} (q - q_c),  de = (R_rel^T - I) dm,
+//   dN = de_xy - m_c de_z - dm (e_zc + de_z),   N = e_xy - m e_z,  Dn = 1 + e_z,
+//   r_m(q) - r_m(q_c) = (dN Dc - N_c de_z) / (Dn Dc),
+//   a(q) - a(q_c) = (f_r - f_v) dm + f_r (r_m(q) - r_m(q_c)),
+//   b(q) - b(q_c) = -f_r C_z (dm + r_m(q) - r_m(q_c)).
+// The sample position's error stays near 1e-7 px at any image size.  The plane is met in
+// front of the view iff 1 - rho_d C_z > 0 (per plane) and the pixel's ray points into the
+// reference frame's half-space, 1 + e_z > 0; the host rejects views whose rays at the image
+// corners run nearly parallel to the planes, so the anchors are always valid.
+//
+// The per-pixel FP32 coefficients of rl_warp_coeffs carry an error near 1.2e-7 times the
+// offset (measured against the FP64 ray/plane intersection): ~1e-5 px at 100 px.  The host
+// therefore takes the anchored path only for launches whose offsets exceed 128 px anywhere
+// (RLViews::anchored), where the per-block FP64 set-up pays for itself in accuracy; the
+// kernels are compiled for both paths.
+
+struct RLPlaneK {
+    float fx, fy;  // fraction of the anchor's offset on plane d
+    int ix, iy;    // integer part (plane not met in front of the view: ix = RL_PLANE_NONE)
+};
+#define RL_PLANE_NONE (-0x40000000)
+
+struct RLAnchor {
+    float mx, my, ez, Nx, Ny, Dc;  // anchor quantities (FP32) for the per-pixel differences
+    int u, v;                      // anchor pixel
+    RLPlaneK k[RL_DEV_MAX_PLANES];
+};
+
+// Fills A (shared memory) for view `view` of V at anchor pixel (u, v).  Every thread of the
+// block calls it (it synchronises the block twice); nthreads threads, index tid.
+__device__ __forceinline__ void rl_anchor_build(RLAnchor* A, const RLViews& V, int view, int u, int v, int D,
+                                                int tid, int nthreads) {
+    __shared__ double s_ab[4];
+    const RLViewParam64& P = V.v64[view];
+    if (tid == 0) {
+        const double mx = ((double)u - P.cxv) * P.inv_fxv, my = ((double)v - P.cyv) * P.inv_fyv;
+        const double ex = P.E[0] * mx + P.E[1] * my + P.E[2];
+        const double ey = P.E[3] * mx + P.E[4] * my + P.E[5];
+        const double ez = P.E[6] * mx + P.E[7] * my + P.E[8];
+        const double dz = 1.0 + ez;
+        const double Nx = ex - mx * ez, Ny = ey - my * ez;
+        // 1 / dz: the FP32 reciprocal refined by two Newton steps in FP64 (relative error far
+        // below FP64's 1e-16 after the second), cheaper than an FP64 division on this GPU
+        double inv = (double)__frcp_rn((float)dz);
+        inv = inv * (2.0 - dz * inv);
+        inv = inv * (2.0 - dz * inv);
+        const double rmx = Nx * inv, rmy = Ny * inv;
+        s_ab[0] = P.dcx + P.dfx * mx + P.fxr * rmx;
+        s_ab[1] = P.dcy + P.dfy * my + P.fyr * rmy;
+        s_ab[2] = P.fxr * (P.C[0] - P.C[2] * (mx + rmx));
+        s_ab[3] = P.fyr * (P.C[1] - P.C[2] * (my + rmy));
+        A->mx = (float)mx;
+        A->my = (float)my;
+        A->ez = (float)ez;
+        A->Nx = (float)Nx;
+        A->Ny = (float)Ny;
+        A->Dc = (float)dz;
+        A->u = u;
+        A->v = v;
+    }
+    __syncthreads();
+    for (int d = tid; d < D; d += nthreads) {
+        const double rho = V.rho64[d];
+        const double kx = s_ab[0] + rho * s_ab[2], ky = s_ab[1] + rho * s_ab[3];
+        RLPlaneK k;
+        if (1.0 - rho * P.C[2] > 0.0 && fabs(kx) < 1e9 && fabs(ky) < 1e9) {
+            const double fx = floor(kx), fy = floor(ky);
+            k.ix = (int)fx;
+            k.iy = (int)fy;
+            k.fx = (float)(kx - fx);
+            k.fy = (float)(ky - fy);
+        } else {
+            k.ix = k.iy = RL_PLANE_NONE;
+            k.fx = k.fy = 0.f;
+        }
+        A->k[d] = k;
+    }
+    __syncthreads();
+}
+
+// Per-pixel differences from the anchor.
+struct RLAnchorPix {
+    float dax, day, dbx, dby;
+    bool ok;  // the pixel's ray points into the reference half-space and its offsets are bounded
+};
+
+__device__ __forceinline__ RLAnchorPix rl_anchor_pixel(const RLAnchor& A, const RLViewParam& P, int qx, int qy) {
+    RLAnchorPix w;
+    const float dmx = (float)(qx - A.u) * P.inv_fxv, dmy = (float)(qy - A.v) * P.inv_fyv;
+    const float dex = fmaf(P.E[0], dmx, P.E[1] * dmy);
+    const float dey = fmaf(P.E[3], dmx, P.E[4] * dmy);
+    const float dez = fmaf(P.E[6], dmx, P.E[7] * dmy);
+    const float ez = A.ez + dez;
+    const float dNx = dex - fmaf(A.mx, dez, dmx * ez);
+    const float dNy = dey - fmaf(A.my, dez, dmy * ez);
+    const float Dn = A.Dc + dez;
+    const float inv = 1.0f / (Dn * A.Dc);
+    const float drx = fmaf(dNx, A.Dc, -A.Nx * dez) * inv;
+    const float dry = fmaf(dNy, A.Dc, -A.Ny * dez) * inv;
+    w.dax = fmaf(P.dfx, dmx, P.fxr * drx);
+    w.day = fmaf(P.dfy, dmy, P.fyr * dry);
+    w.dbx = -P.fxr * P.C[2] * (dmx + drx);
+    w.dby = -P.fyr * P.C[2] * (dmy + dry);
+    w.ok = Dn > 0.f && fabsf(w.dax) + fabsf(w.dbx) < 1.0e6f && fabsf(w.day) + fabsf(w.dby) < 1.0e6f;
+    return w;
+}
+
+// Taps of plane d (inverse depth rho, its FP32 value) at view pixel (qx, qy).
+__device__ __forceinline__ RLTaps rl_anchor_taps(const RLAnchor& A, const RLAnchorPix& w, int d, float rho, int qx,
+                                                 int qy) {
+    const RLPlaneK k = A.k[d];
+    RLTaps t;
+    const float sx = k.fx + fmaf(rho, w.dbx, w.dax), sy = k.fy + fmaf(rho, w.dby, w.day);
+    const float flx = floorf(sx), fly = floorf(sy);
+    t.fx = sx - flx;
+    t.fy = sy - fly;
+    t.x0 = qx + k.ix + (int)flx;
+    t.y0 = qy + k.iy + (int)fly;
+    t.ok = w.ok && k.ix != RL_PLANE_NONE;
+    return t;
+}
+
+// Warp state of one view pixel for either coordinate path (ANCH: the block's anchor A).
+template <bool ANCH>
+struct RLPixWarp;
+
+template <>
+struct RLPixWarp<false> {
+    RLWarp w;
+    __device__ __forceinline__ RLTaps taps(const RLAnchor&, int, float rho, int qx, int qy) const {
+        return rl_taps(w, rho, qx, qy);
+    }
+};
+
+template <>
+struct RLPixWarp<true> {
+    RLAnchorPix w;
+    __device__ __forceinline__ RLTaps taps(const RLAnchor& A, int d, float rho, int qx, int qy) const {
+        return rl_anchor_taps(A, w, d, rho, qx, qy);
+    }
+};
+
+template <bool ANCH>
+__device__ __forceinline__ RLPixWarp<ANCH> rl_pix_warp(const RLAnchor& A, const RLViewParam& P, int qx, int qy) {
+    RLPixWarp<ANCH> r;
+    if constexpr (ANCH)
+        r.w = rl_anchor_pixel(A, P, qx, qy);
+    else
+        r.w = rl_warp_coeffs(P, (float)qx, (float)qy);
+    return r;
 }
 
 // Inverse warp (reference -> view, the direction of Eq. eq_homo's H^{-1}).  The reference

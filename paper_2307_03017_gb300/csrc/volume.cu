@@ -59,20 +59,24 @@ __device__ __forceinline__ void sample_map(const float* __restrict__ img, int H,
     }
 }
 
-template <typename Tm>
+template <typename Tm, bool ANCH>
 __global__ void __launch_bounds__(kAlphaBX * kAlphaBY)
 k_view_alpha(const Tm* __restrict__ M, int D, int H, int W, const __grid_constant__ RLViews views,
              float* __restrict__ A) {
+    __shared__ RLAnchor sA;
     const int view = blockIdx.x;  // grid (views, tiles_x, tiles_y)
+    if (ANCH)
+        rl_anchor_build(&sA, views, view, blockIdx.y * kAlphaBX + kAlphaBX / 2, blockIdx.z * kAlphaBY + kAlphaBY / 2,
+                        D, threadIdx.y * kAlphaBX + threadIdx.x, kAlphaBX * kAlphaBY);
     const int qx = blockIdx.y * kAlphaBX + threadIdx.x;
     const int qy = blockIdx.z * kAlphaBY + threadIdx.y;
     if (qx >= W || qy >= H) return;
-    const RLWarp w = rl_warp_coeffs(views.v[view], (float)qx, (float)qy);
+    const RLPixWarp<ANCH> w = rl_pix_warp<ANCH>(sA, views.v[view], qx, qy);
     const size_t plane = (size_t)H * W * 4, hw = (size_t)H * W;
     float* out = A + (size_t)view * D * hw + (size_t)qy * W + qx;
     float T = 1.f;
     for (int d = D - 1; d >= 0; --d) {
-        const RLTaps t = rl_taps(w, views.rho[d], qx, qy);
+        const RLTaps t = w.taps(sA, d, views.rho[d], qx, qy);
         const float a = sample_alpha(M + d * plane, H, W, t);
         out[(size_t)d * hw] = a * T;
         T = T * (1.f - a);
@@ -211,10 +215,14 @@ rl_status rl_launch_view_alpha(const void* M, rl_dtype dt, int D, int H, int W, 
     const dim3 block(kAlphaBX, kAlphaBY);
     if (dt == RL_F32) {
         RLTraceScope ts("view_alpha_f32", s);
-        k_view_alpha<float><<<grid, block, 0, s>>>((const float*)M, D, H, W, views, A);
+        if (views.anchored) k_view_alpha<float, true><<<grid, block, 0, s>>>((const float*)M, D, H, W, views, A);
+        else k_view_alpha<float, false><<<grid, block, 0, s>>>((const float*)M, D, H, W, views, A);
     } else {
         RLTraceScope ts("view_alpha_bf16", s);
-        k_view_alpha<__nv_bfloat16><<<grid, block, 0, s>>>((const __nv_bfloat16*)M, D, H, W, views, A);
+        if (views.anchored)
+            k_view_alpha<__nv_bfloat16, true><<<grid, block, 0, s>>>((const __nv_bfloat16*)M, D, H, W, views, A);
+        else
+            k_view_alpha<__nv_bfloat16, false><<<grid, block, 0, s>>>((const __nv_bfloat16*)M, D, H, W, views, A);
     }
     return rl_check_launch("view_alpha");
 }

@@ -112,7 +112,8 @@ size_t reallife_workspace_bytes(int N, int D, int H, int W, int k, rl_dtype dtyp
  * sampling with zero padding, composite front to back with no background.
  *   tgt:  host array of T cameras.
  *   out:  device [T][H][W][3] FP32.
- * No workspace.  RL_EINVAL for T < 1, null pointers or invalid MPI/cameras. */
+ * No workspace.  RL_EINVAL for T < 1, null pointers or invalid MPI/cameras (including views
+ * whose rays at the image corners run nearly parallel to the planes). */
 rl_status reallife_render(const rl_mpi* m, const rl_camera* tgt, int T, float* out, cudaStream_t stream);
 
 /* One HSGD iteration on `m` in place (Sec. 3.3 with the analytic gradient of Sec. 3.1):

@@ -53,7 +53,8 @@ typedef enum {
     RL_ENOMEM = 2,    /* workspace too small */
     RL_ECUDA = 3,     /* a CUDA call or launch failed */
     RL_ETIMEOUT = 4,  /* a bounded device-side wait gave up */
-    RL_ENOTIMPL = 5
+    RL_ENOTIMPL = 5,
+    RL_EBOUNDS = 6    /* a bounds check of the debug build failed (reallife_device_status) */
 } rl_status;
 
 typedef enum { RL_F32 = 0, RL_BF16 = 1 } rl_dtype;
@@ -310,7 +311,9 @@ rl_status reallife_select_keys(const float* keys, int D, int H, int W, int k, in
  * gradient (warp + composite + loss + exact adjoint, Sec. 3.1/3.3):
  *   mask == NULL: dense G device [D][H][W][4] FP32;
  *   mask != NULL: compact G device [k][H][W][4] FP32, slot j of pixel p holding the
- *                 j-th kept plane of p in ascending order (mask device [H][W] uint64).
+ *                 j-th kept plane of p in ascending order (mask device [H][W] uint64; bits
+ *                 at or above D are ignored, and of a pixel with more than k bits set only
+ *                 the k lowest planes are kept).
  *   loss_out: device float[1] or NULL.  G is overwritten.
  *   ws: device workspace (256-byte aligned), at least reallife_workspace_bytes(N, D, H, W,
  *       1, dtype) bytes; RL_ENOMEM when smaller. */
@@ -355,9 +358,27 @@ rl_status reallife_set_kernel_path(int path);
 /* Device-side status: synchronises the device and reports the status word that kernels
  * set when a bounded wait (about one second) gives up; *flags_out receives its bits
  * (1 = timeout; 2 = a batched step was given a table it cannot serve, see
- * reallife_hsgd_step_batch).  Returns RL_ETIMEOUT when the timeout bit is set, RL_OK
- * otherwise; clear != 0 resets the word.  Results of launches that timed out are invalid. */
+ * reallife_hsgd_step_batch; 4 = a bounds check of the debug build failed).  Returns
+ * RL_ETIMEOUT when the timeout bit is set, else RL_EBOUNDS when the bounds bit is set, RL_OK
+ * otherwise; clear != 0 resets the word.  Results of launches that timed out are invalid.
+ *
+ * Debug build.  Compiled with -DRL_DEBUG (libreallife_debug.so), the warp, selection,
+ * gradient-volume and update kernels check the index of each data-dependent global access
+ * (bilinear taps, gradient slots taken from the slot map, plane indices written to S, batch
+ * items, loss partials, the voxels of an update) against the extent of its buffer before the
+ * access.  A failed check sets bit 4 and skips that access: no trap, the context stays usable.
+ * The release build compiles the checks out. */
 rl_status reallife_device_status(int clear, unsigned int* flags_out);
+
+/* 1 in the debug build (-DRL_DEBUG), 0 in the release build. */
+int reallife_debug_build(void);
+
+/* Self-test of the bounds reporting of the debug build (no fault): one launch whose threads
+ * 0 .. 32 store to a 32-element device buffer, each behind the bounds check; thread 32 fails
+ * it, sets bit 4 of the status word and stores nothing.  After the stream has run it,
+ * reallife_device_status reports RL_EBOUNDS.  The release build returns RL_ENOTIMPL and
+ * launches nothing. */
+rl_status reallife_selftest_bounds(cudaStream_t stream);
 
 /* Self-test of the failure reporting (no fault, no hang): one thread waits on a
  * shared-memory barrier that nothing completes, for at most wait_us microseconds of the

@@ -24,7 +24,8 @@ __all__ = [
     "reallife_sparse_update", "reallife_render_backward", "reallife_warp_offsets",
     "reallife_trace_enable", "reallife_trace_read", "reallife_strerror", "workspace", "library_path",
     "reallife_set_kernel_path", "reallife_device_status", "reallife_hsgd_step_noalloc",
-    "reallife_trace_release_captured", "reallife_selftest_wait_timeout",
+    "reallife_trace_release_captured", "reallife_selftest_wait_timeout", "reallife_selftest_bounds",
+    "reallife_debug_build",
     "BatchItem", "BatchTable", "batch_c_item", "reallife_batch_table_bytes", "reallife_batch_prepare", "reallife_hsgd_step_batch",
 ]
 
@@ -463,8 +464,21 @@ def reallife_selftest_wait_timeout(wait_us: int = 2000, stream=None) -> None:
                                                                                              _stream(stream)))
 
 
+def reallife_selftest_bounds(stream=None) -> None:
+    """Enqueue the bounds-check self-test of the debug build: a store one past the end of a
+    device buffer is stopped by its check, which sets the bounds bit (4) of the status word.
+    Raises RL_ENOTIMPL on the release build."""
+    _lib.check("reallife_selftest_bounds", _lib.lib().reallife_selftest_bounds(_stream(stream)))
+
+
+def reallife_debug_build() -> bool:
+    """True when the loaded library is the bounds-checked debug build (REALLIFE_DEBUG=1)."""
+    return bool(_lib.lib().reallife_debug_build())
+
+
 def reallife_device_status(clear: bool = True) -> int:
-    """Synchronise the device and return the device status bits (raises on a timeout)."""
+    """Synchronise the device and return the device status bits (raises on a timeout, and on
+    a failed bounds check of the debug build)."""
     flags = ctypes.c_uint()
     _lib.check("reallife_device_status", _lib.lib().reallife_device_status(int(bool(clear)), ctypes.byref(flags)))
     return int(flags.value)

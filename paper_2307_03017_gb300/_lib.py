@@ -8,7 +8,9 @@ import threading
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_LIB_PATH = os.path.join(_HERE, "libreallife.so")
+# REALLIFE_DEBUG=1 loads the bounds-checked debug build (libreallife_debug.so) instead
+DEBUG = os.environ.get("REALLIFE_DEBUG", "0") not in ("", "0")
+_LIB_PATH = os.path.join(_HERE, "libreallife_debug.so" if DEBUG else "libreallife.so")
 _lock = threading.Lock()
 _lib = None
 
@@ -23,6 +25,7 @@ EXPORTS = [
     "reallife_lgd_prepare", "reallife_lgd_workspace_bytes", "reallife_lgd_forward",
     "reallife_lgd_step_workspace_bytes", "reallife_lgd_step", "reallife_selftest_wait_timeout",
     "reallife_batch_table_bytes", "reallife_batch_prepare", "reallife_hsgd_step_batch",
+    "reallife_selftest_bounds", "reallife_debug_build",
 ]
 
 
@@ -107,6 +110,8 @@ def _declare(lib):
         "reallife_set_kernel_path": (c_int, [c_int]),
         "reallife_device_status": (c_int, [c_int, ctypes.POINTER(ctypes.c_uint)]),
         "reallife_selftest_wait_timeout": (c_int, [ctypes.c_uint, vp]),
+        "reallife_selftest_bounds": (c_int, [vp]),
+        "reallife_debug_build": (c_int, []),
         "reallife_last_error": (ctypes.c_char_p, []),
         "reallife_gradient_volume_workspace_bytes": (c_size_t, [c_int, c_int, c_int, c_int, c_int, c_int]),
         "reallife_gradient_volume": (c_int, [mpi_p, vp, cam_p, c_int, c_int, c_int, c_int, vp, vp, vp, c_size_t,
@@ -134,7 +139,7 @@ def lib():
         if _lib is None:
             from . import build as _build
             try:
-                p = _build.build()
+                p = _build.build(debug=DEBUG)
             except Exception as e:  # no silent fallback: the CUDA library is the product
                 raise RealLifeError(f"libreallife is not available and could not be built: {e}") from e
             l = ctypes.CDLL(p)

@@ -4,6 +4,10 @@ Each CUDA translation unit is compiled in parallel to ``_build/<machine>/`` and 
 into ``paper_2307_03017_gb300/libreallife.so`` (static CUDA runtime).  Rebuilds only
 when a source or header is newer than the library, and then recompiles only the
 translation units whose object is older than the unit or any header.
+
+``build(debug=True)`` makes the bounds-checked variant ``libreallife_debug.so``
+(``-DRL_DEBUG``, objects in ``_build/<machine>-debug/``), loaded instead of the release
+library when the environment sets ``REALLIFE_DEBUG=1``.
 """
 from __future__ import annotations
 
@@ -19,6 +23,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "libreallife.so")
+LIB_DEBUG = os.path.join(HERE, "libreallife_debug.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]
 
@@ -43,21 +48,24 @@ def _deps() -> list[str]:
     return sources() + _headers()
 
 
-def up_to_date() -> bool:
-    if not os.path.exists(LIB):
+def up_to_date(debug: bool = False) -> bool:
+    lib = LIB_DEBUG if debug else LIB
+    if not os.path.exists(lib):
         return False
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return all(os.path.getmtime(p) <= t for p in _deps())
 
 
-def build(force: bool = False, verbose: bool = False, extra_flags: list[str] | None = None) -> str:
-    """Compile and link the library if needed; returns its path."""
-    if not force and up_to_date():
-        return LIB
+def build(force: bool = False, verbose: bool = False, extra_flags: list[str] | None = None,
+          debug: bool = False) -> str:
+    """Compile and link the library (the debug variant with ``debug``) if needed; returns its path."""
+    lib = LIB_DEBUG if debug else LIB
+    if not force and up_to_date(debug):
+        return lib
     exe = nvcc()
-    objdir = os.path.join(HERE, "_build", platform.machine())
+    objdir = os.path.join(HERE, "_build", platform.machine() + ("-debug" if debug else ""))
     os.makedirs(objdir, exist_ok=True)
-    flags = NVCC_FLAGS + (extra_flags or [])
+    flags = NVCC_FLAGS + (["-DRL_DEBUG"] if debug else []) + (extra_flags or [])
     newest_header = max(os.path.getmtime(p) for p in _headers())
 
     def compile_one(src):
@@ -75,13 +83,13 @@ def build(force: bool = False, verbose: bool = False, extra_flags: list[str] | N
 
     with cf.ThreadPoolExecutor(max_workers=max(1, min(8, os.cpu_count() or 1))) as ex:
         objs = list(ex.map(compile_one, sources()))
-    tmp = LIB + f".tmp{os.getpid()}"
+    tmp = lib + f".tmp{os.getpid()}"
     cmd = [exe] + ARCH + ["-shared", "-o", tmp] + objs
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"nvcc link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

@@ -26,18 +26,18 @@ constexpr int kGradBX = 32, kGradBY = 4, kGradThreads = kGradBX * kGradBY;
 
 template <bool SPARSE>
 __device__ __forceinline__ void scatter_tap(float* __restrict__ G, const uint8_t* __restrict__ slots_d, int d,
-                                            unsigned hw, int H, int W, int x, int y, float wt, float4 g) {
+                                            unsigned hw, int H, int W, int x, int y, float wt, float4 g, unsigned ng) {
     if ((unsigned)x >= (unsigned)W || (unsigned)y >= (unsigned)H) return;
     const unsigned pix = (unsigned)(y * W + x);
     const unsigned slot = SPARSE ? (unsigned)__ldg(slots_d + pix) : (unsigned)d;
-    if (SPARSE && slot == RL_SLOT_NONE) return;
+    if ((SPARSE && slot == RL_SLOT_NONE) || !RL_IN(slot, ng)) return;
     atomicAdd(reinterpret_cast<float4*>(G) + (slot * hw + pix), make_float4(wt * g.x, wt * g.y, wt * g.z, wt * g.w));
 }
 
 // Bilinear transpose of one sample's gradient g onto its four taps.
 template <bool SPARSE>
 __device__ __forceinline__ void scatter4(float* __restrict__ G, const uint8_t* __restrict__ slots_d, int d,
-                                         unsigned hw, int H, int W, const RLTaps& t, float4 g) {
+                                         unsigned hw, int H, int W, const RLTaps& t, float4 g, unsigned ng) {
     const float w00 = (1.f - t.fx) * (1.f - t.fy), w10 = t.fx * (1.f - t.fy);
     const float w01 = (1.f - t.fx) * t.fy, w11 = t.fx * t.fy;
     if ((unsigned)t.x0 < (unsigned)(W - 1) && (unsigned)t.y0 < (unsigned)(H - 1)) {
@@ -50,20 +50,20 @@ __device__ __forceinline__ void scatter4(float* __restrict__ G, const uint8_t* _
             s11 = __ldg(slots_d + p + W + 1);
         }
         float4* G4 = reinterpret_cast<float4*>(G);
-        if (!SPARSE || s00 != RL_SLOT_NONE)
+        if ((!SPARSE || s00 != RL_SLOT_NONE) && RL_IN(s00, ng))
             atomicAdd(G4 + (s00 * hw + p), make_float4(w00 * g.x, w00 * g.y, w00 * g.z, w00 * g.w));
-        if (!SPARSE || s10 != RL_SLOT_NONE)
+        if ((!SPARSE || s10 != RL_SLOT_NONE) && RL_IN(s10, ng))
             atomicAdd(G4 + (s10 * hw + p + 1), make_float4(w10 * g.x, w10 * g.y, w10 * g.z, w10 * g.w));
-        if (!SPARSE || s01 != RL_SLOT_NONE)
+        if ((!SPARSE || s01 != RL_SLOT_NONE) && RL_IN(s01, ng))
             atomicAdd(G4 + (s01 * hw + p + W), make_float4(w01 * g.x, w01 * g.y, w01 * g.z, w01 * g.w));
-        if (!SPARSE || s11 != RL_SLOT_NONE)
+        if ((!SPARSE || s11 != RL_SLOT_NONE) && RL_IN(s11, ng))
             atomicAdd(G4 + (s11 * hw + p + W + 1), make_float4(w11 * g.x, w11 * g.y, w11 * g.z, w11 * g.w));
         return;
     }
-    scatter_tap<SPARSE>(G, slots_d, d, hw, H, W, t.x0, t.y0, w00, g);
-    scatter_tap<SPARSE>(G, slots_d, d, hw, H, W, t.x0 + 1, t.y0, w10, g);
-    scatter_tap<SPARSE>(G, slots_d, d, hw, H, W, t.x0, t.y0 + 1, w01, g);
-    scatter_tap<SPARSE>(G, slots_d, d, hw, H, W, t.x0 + 1, t.y0 + 1, w11, g);
+    scatter_tap<SPARSE>(G, slots_d, d, hw, H, W, t.x0, t.y0, w00, g, ng);
+    scatter_tap<SPARSE>(G, slots_d, d, hw, H, W, t.x0 + 1, t.y0, w10, g, ng);
+    scatter_tap<SPARSE>(G, slots_d, d, hw, H, W, t.x0, t.y0 + 1, w01, g, ng);
+    scatter_tap<SPARSE>(G, slots_d, d, hw, H, W, t.x0 + 1, t.y0 + 1, w11, g, ng);
 }
 
 // One block's tile of 32 x 4 view pixels of one view.  bid / nblocks index the block among
@@ -124,6 +124,7 @@ __device__ __forceinline__ void grad_tile(const Tm* __restrict__ M, int D, int H
         }
         float b0 = 0.f, b1 = 0.f, b2 = 0.f;
         const unsigned hw = (unsigned)(H * W);
+        const unsigned ng = views.gplanes ? (unsigned)views.gplanes : (unsigned)D;  // checked in debug builds
 #pragma unroll 1
         for (int d = 0; d < D; ++d) {
             const RLTaps t = w.taps(sA, d, views.rho[d], qx, qy);
@@ -136,7 +137,7 @@ __device__ __forceinline__ void grad_tile(const Tm* __restrict__ M, int D, int H
                 g.y = gc * r1;
                 g.z = gc * r2;
                 g.w = Td * fmaf(m.x - b0, r0, fmaf(m.y - b1, r1, (m.z - b2) * r2));
-                scatter4<SPARSE>(G, SPARSE ? slots + (size_t)d * hw : nullptr, d, hw, H, W, t, g);
+                scatter4<SPARSE>(G, SPARSE ? slots + (size_t)d * hw : nullptr, d, hw, H, W, t, g, ng);
             }
             const float om = 1.f - m.w;
             b0 = fmaf(m.x, m.w, om * b0);
@@ -297,3 +298,5 @@ rl_status rl_launch_loss_reduce(const float* partials, int n, float scale, float
     k_loss_reduce<<<1, 1024, 0, s>>>(partials, n, scale, out);
     return rl_check_launch("loss_reduce");
 }
+
+RL_DEBUG_READER(grad)

@@ -28,7 +28,8 @@ __device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b
 // Bilinear sample; interior samples use packed FMAs, border samples the checked path.
 template <typename Tm>
 __device__ __forceinline__ float4 sample_pp(const Tm* __restrict__ plane, int H, int W, const RLTaps& t) {
-    if (t.ok && (unsigned)t.x0 < (unsigned)(W - 1) && (unsigned)t.y0 < (unsigned)(H - 1)) {
+    if (t.ok && (unsigned)t.x0 < (unsigned)(W - 1) && (unsigned)t.y0 < (unsigned)(H - 1) &&
+        RL_IN((long long)t.y0 * W + t.x0 + W + 1, (long long)H * W)) {
         const Tm* p = plane + (unsigned)(t.y0 * W + t.x0) * 4u;
         const float4 v00 = RLStore<Tm>::load4(p), v10 = RLStore<Tm>::load4(p + 4);
         const float4 v01 = RLStore<Tm>::load4(p + 4 * W), v11 = RLStore<Tm>::load4(p + 4 * W + 4);
@@ -50,18 +51,18 @@ __device__ __forceinline__ float4 sample_pp(const Tm* __restrict__ plane, int H,
 template <bool SPARSE>
 __device__ __forceinline__ void scatter_tap_pp(float4* __restrict__ G4, const uint8_t* __restrict__ slots_d,
                                                unsigned d, unsigned hw, int H, int W, int x, int y, float wt,
-                                               float4 g) {
+                                               float4 g, unsigned ng) {
     if ((unsigned)x >= (unsigned)W || (unsigned)y >= (unsigned)H) return;
     const unsigned pix = (unsigned)(y * W + x);
     const unsigned slot = SPARSE ? (unsigned)__ldg(slots_d + pix) : d;
-    if (SPARSE && slot == RL_SLOT_NONE) return;
+    if ((SPARSE && slot == RL_SLOT_NONE) || !RL_IN(slot, ng)) return;
     atomicAdd(G4 + (slot * hw + pix), make_float4(wt * g.x, wt * g.y, wt * g.z, wt * g.w));
 }
 
 // Bilinear transpose of one sample's gradient onto its four taps (kept voxels only).
 template <bool SPARSE>
 __device__ __forceinline__ void scatter_pp(float* __restrict__ G, const uint8_t* __restrict__ slots_d, unsigned d,
-                                           unsigned hw, int H, int W, const RLTaps& t, float4 g) {
+                                           unsigned hw, int H, int W, const RLTaps& t, float4 g, unsigned ng) {
     const float w00 = (1.f - t.fx) * (1.f - t.fy), w10 = t.fx * (1.f - t.fy);
     const float w01 = (1.f - t.fx) * t.fy, w11 = t.fx * t.fy;
     float4* G4 = reinterpret_cast<float4*>(G);
@@ -75,28 +76,28 @@ __device__ __forceinline__ void scatter_pp(float* __restrict__ G, const uint8_t*
             s11 = __ldg(slots_d + p + W + 1);
         }
         const float2 gl = f2(g.x, g.y), gh = f2(g.z, g.w);
-        if (!SPARSE || s00 != RL_SLOT_NONE) {
+        if ((!SPARSE || s00 != RL_SLOT_NONE) && RL_IN(s00, ng)) {
             const float2 a = __fmul2_rn(f2(w00, w00), gl), b = __fmul2_rn(f2(w00, w00), gh);
             atomicAdd(G4 + (s00 * hw + p), make_float4(a.x, a.y, b.x, b.y));
         }
-        if (!SPARSE || s10 != RL_SLOT_NONE) {
+        if ((!SPARSE || s10 != RL_SLOT_NONE) && RL_IN(s10, ng)) {
             const float2 a = __fmul2_rn(f2(w10, w10), gl), b = __fmul2_rn(f2(w10, w10), gh);
             atomicAdd(G4 + (s10 * hw + p + 1), make_float4(a.x, a.y, b.x, b.y));
         }
-        if (!SPARSE || s01 != RL_SLOT_NONE) {
+        if ((!SPARSE || s01 != RL_SLOT_NONE) && RL_IN(s01, ng)) {
             const float2 a = __fmul2_rn(f2(w01, w01), gl), b = __fmul2_rn(f2(w01, w01), gh);
             atomicAdd(G4 + (s01 * hw + p + W), make_float4(a.x, a.y, b.x, b.y));
         }
-        if (!SPARSE || s11 != RL_SLOT_NONE) {
+        if ((!SPARSE || s11 != RL_SLOT_NONE) && RL_IN(s11, ng)) {
             const float2 a = __fmul2_rn(f2(w11, w11), gl), b = __fmul2_rn(f2(w11, w11), gh);
             atomicAdd(G4 + (s11 * hw + p + W + 1), make_float4(a.x, a.y, b.x, b.y));
         }
         return;
     }
-    scatter_tap_pp<SPARSE>(G4, slots_d, d, hw, H, W, t.x0, t.y0, w00, g);
-    scatter_tap_pp<SPARSE>(G4, slots_d, d, hw, H, W, t.x0 + 1, t.y0, w10, g);
-    scatter_tap_pp<SPARSE>(G4, slots_d, d, hw, H, W, t.x0, t.y0 + 1, w01, g);
-    scatter_tap_pp<SPARSE>(G4, slots_d, d, hw, H, W, t.x0 + 1, t.y0 + 1, w11, g);
+    scatter_tap_pp<SPARSE>(G4, slots_d, d, hw, H, W, t.x0, t.y0, w00, g, ng);
+    scatter_tap_pp<SPARSE>(G4, slots_d, d, hw, H, W, t.x0 + 1, t.y0, w10, g, ng);
+    scatter_tap_pp<SPARSE>(G4, slots_d, d, hw, H, W, t.x0, t.y0 + 1, w01, g, ng);
+    scatter_tap_pp<SPARSE>(G4, slots_d, d, hw, H, W, t.x0 + 1, t.y0 + 1, w11, g, ng);
 }
 
 struct PixelCoord {
@@ -255,6 +256,7 @@ __device__ __forceinline__ void grad_pp_tile(const Tm* __restrict__ M, int D, in
         }
         // adjoint over the chunk, farthest plane first
         const unsigned hw = (unsigned)(H * W);
+        const unsigned ng = views.gplanes ? (unsigned)views.gplanes : (unsigned)D;  // checked in debug builds
 #pragma unroll
         for (int i = 0; i < C; ++i) {
             const int d = pc.g * C + i;
@@ -270,7 +272,8 @@ __device__ __forceinline__ void grad_pp_tile(const Tm* __restrict__ M, int D, in
                         g.y = gc * r1;
                         g.z = gc * r2;
                         g.w = Td * fmaf(mi.x - b0, r0, fmaf(mi.y - b1, r1, (mi.z - b2) * r2));
-                        scatter_pp<SPARSE>(G, SPARSE ? slots + (size_t)d * hw : nullptr, (unsigned)d, hw, H, W, t, g);
+                        scatter_pp<SPARSE>(G, SPARSE ? slots + (size_t)d * hw : nullptr, (unsigned)d, hw, H, W, t, g,
+                                           ng);
                     }
                 }
                 const float om = 1.f - mi.w;
@@ -496,3 +499,5 @@ rl_status rl_launch_grad_pp_batch(const void* table, rl_dtype dt, cudaStream_t s
     }
     return rl_check_launch("grad_pp_batch");
 }
+
+RL_DEBUG_READER(pp)

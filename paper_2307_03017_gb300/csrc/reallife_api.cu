@@ -36,6 +36,7 @@ extern "C" const char* reallife_strerror(rl_status s) {
         case RL_ECUDA: return "CUDA error";
         case RL_ETIMEOUT: return "device wait timed out";
         case RL_ENOTIMPL: return "not implemented";
+        case RL_EBOUNDS: return "bounds check failed";
     }
     return "unknown status";
 }
@@ -439,6 +440,7 @@ rl_status enqueue_hsgd(rl_mpi* m, const float* images, const rl_camera* src, int
     RLViews views;
     rl_status st = make_views(m, src, N, level, views);
     if (st) return st;
+    views.gplanes = k;
     // coarse levels: the pyramid and the selection share one pass over M
     st = level ? rl_launch_pyramid_select(m->data, m->dtype, m->D, m->H, m->W, level, Ml, k, S, slots, G, counter,
                                           selection, s)
@@ -637,10 +639,11 @@ extern "C" rl_status reallife_loss_grad(const rl_mpi* m, const float* images, co
     if (((uintptr_t)ws & 255) != 0) return rl_fail(RL_EINVAL, "workspace must be 256-byte aligned");
     uint8_t* slots = mask ? (uint8_t*)ws + part : nullptr;
     const int nslots = mask ? k : m->D;
+    views.gplanes = nslots;
     st = launch_zero(G, (size_t)nslots * m->H * m->W * 4, stream);
     if (st) return st;
     if (mask) {
-        st = rl_launch_mask_to_slots(mask, m->D, m->H * m->W, slots, stream);
+        st = rl_launch_mask_to_slots(mask, m->D, k, m->H * m->W, slots, stream);
         if (st) return st;
     }
     int nb = 0;
@@ -733,6 +736,7 @@ extern "C" rl_status reallife_batch_prepare(const rl_batch_item* items, int n, v
         std::memset(&it, 0, sizeof(it));
         st = make_views(m, b.src, b.N, p->level, it.views);
         if (st) return rl_fail(st, "batch item %d: %s", i, reallife_last_error());
+        it.views.gplanes = p->k;
         char* base = static_cast<char*>(b.ws);
         const int l = p->level, h = m->H >> l, w = m->W >> l;
         it.M = m->data;

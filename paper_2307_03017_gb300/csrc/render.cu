@@ -214,3 +214,5 @@ rl_status rl_launch_warp_offsets(int D, int H, int W, const RLViews& views, floa
     k_warp_offsets<<<dim3((W + 127) / 128, H), 128, 0, s>>>(D, H, W, views, out);
     return rl_check_launch("warp_offsets");
 }
+
+RL_DEBUG_READER(render)

@@ -19,6 +19,40 @@
 #define RL_DEV_MAX_PLANES 64
 #define RL_DEV_MAX_VIEWS 16
 
+// Bounds checks of the debug build (-DRL_DEBUG, built by build.py as libreallife_debug.so):
+// the hot kernels check the computed index of each global access against its buffer before
+// the access; a failed check sets RL_DEVFLAG_BOUNDS in the translation unit's debug word and
+// skips the access, never a trap.  reallife_device_status reports the words of every
+// translation unit.  In the release build RL_IN is `true` and costs nothing.
+#define RL_DEVFLAG_BOUNDS 4u
+#ifdef RL_DEBUG
+static __device__ unsigned int rl_dbg_word;  // one per translation unit
+__device__ __forceinline__ bool rl_dbg_in(long long i, long long n) {
+    if (i >= 0 && i < n) return true;
+    atomicOr(&rl_dbg_word, RL_DEVFLAG_BOUNDS);
+    return false;
+}
+#define RL_IN(i, n) rl_dbg_in((long long)(i), (long long)(n))
+// Host reader of this translation unit's debug word (defined once per .cu by the macro).
+#define RL_DEBUG_READER(name)                                                       \
+    unsigned int rl_dbg_read_##name(int clear) {                                    \
+        unsigned int v = 0;                                                         \
+        if (cudaMemcpyFromSymbol(&v, rl_dbg_word, sizeof(v)) != cudaSuccess) {      \
+            cudaGetLastError();                                                     \
+            return 0;                                                               \
+        }                                                                           \
+        if (clear) {                                                                \
+            const unsigned int z = 0;                                               \
+            if (cudaMemcpyToSymbol(rl_dbg_word, &z, sizeof(z)) != cudaSuccess) cudaGetLastError(); \
+        }                                                                           \
+        return v;                                                                   \
+    }
+#else
+#define RL_IN(i, n) true
+#define RL_DEBUG_READER(name) \
+    unsigned int rl_dbg_read_##name(int) { return 0; }
+#endif
+
 struct RLViewParam {
     float E[9];          // R_rel^T - I (row-major)
     float C[3];          // view centre in the reference frame
@@ -42,6 +76,7 @@ struct RLViews {
     RLViewParam v[RL_DEV_MAX_VIEWS];
     double rho64[RL_DEV_MAX_PLANES];
     RLViewParam64 v64[RL_DEV_MAX_VIEWS];
+    int gplanes;  // planes of the gradient buffer a launch scatters into (0: D); debug-build bounds checks
 };
 
 // ------------------------------------------------------------------ batch work tables
@@ -107,7 +142,7 @@ __device__ __forceinline__ unsigned rl_batch_find(const RLBatchItem* __restrict_
         if (items[mid].*begin <= u) lo = mid;
         else hi = mid - 1;
     }
-    return lo;
+    return RL_IN(lo, n) ? lo : 0;
 }
 
 // Per-pixel warp coefficients of one view.
@@ -430,14 +465,14 @@ __device__ __forceinline__ float4 rl_sample(const Tm* __restrict__ plane, int H,
     const float w01 = (1.f - t.fx) * t.fy, w11 = t.fx * t.fy;
     const bool x0in = (unsigned)t.x0 < (unsigned)W, x1in = (unsigned)(t.x0 + 1) < (unsigned)W;
     const bool y0in = (unsigned)t.y0 < (unsigned)H, y1in = (unsigned)(t.y0 + 1) < (unsigned)H;
-    const size_t r0 = (size_t)t.y0 * W, r1 = r0 + W;
+    const size_t r0 = (size_t)t.y0 * W, r1 = r0 + W, hw = (size_t)H * W;
     if (y0in) {
-        if (x0in) { float4 v = RLStore<Tm>::load4(plane + (r0 + t.x0) * 4); acc.x = fmaf(w00, v.x, acc.x); acc.y = fmaf(w00, v.y, acc.y); acc.z = fmaf(w00, v.z, acc.z); acc.w = fmaf(w00, v.w, acc.w); }
-        if (x1in) { float4 v = RLStore<Tm>::load4(plane + (r0 + t.x0 + 1) * 4); acc.x = fmaf(w10, v.x, acc.x); acc.y = fmaf(w10, v.y, acc.y); acc.z = fmaf(w10, v.z, acc.z); acc.w = fmaf(w10, v.w, acc.w); }
+        if (x0in && RL_IN(r0 + t.x0, hw)) { float4 v = RLStore<Tm>::load4(plane + (r0 + t.x0) * 4); acc.x = fmaf(w00, v.x, acc.x); acc.y = fmaf(w00, v.y, acc.y); acc.z = fmaf(w00, v.z, acc.z); acc.w = fmaf(w00, v.w, acc.w); }
+        if (x1in && RL_IN(r0 + t.x0 + 1, hw)) { float4 v = RLStore<Tm>::load4(plane + (r0 + t.x0 + 1) * 4); acc.x = fmaf(w10, v.x, acc.x); acc.y = fmaf(w10, v.y, acc.y); acc.z = fmaf(w10, v.z, acc.z); acc.w = fmaf(w10, v.w, acc.w); }
     }
     if (y1in) {
-        if (x0in) { float4 v = RLStore<Tm>::load4(plane + (r1 + t.x0) * 4); acc.x = fmaf(w01, v.x, acc.x); acc.y = fmaf(w01, v.y, acc.y); acc.z = fmaf(w01, v.z, acc.z); acc.w = fmaf(w01, v.w, acc.w); }
-        if (x1in) { float4 v = RLStore<Tm>::load4(plane + (r1 + t.x0 + 1) * 4); acc.x = fmaf(w11, v.x, acc.x); acc.y = fmaf(w11, v.y, acc.y); acc.z = fmaf(w11, v.z, acc.z); acc.w = fmaf(w11, v.w, acc.w); }
+        if (x0in && RL_IN(r1 + t.x0, hw)) { float4 v = RLStore<Tm>::load4(plane + (r1 + t.x0) * 4); acc.x = fmaf(w01, v.x, acc.x); acc.y = fmaf(w01, v.y, acc.y); acc.z = fmaf(w01, v.z, acc.z); acc.w = fmaf(w01, v.w, acc.w); }
+        if (x1in && RL_IN(r1 + t.x0 + 1, hw)) { float4 v = RLStore<Tm>::load4(plane + (r1 + t.x0 + 1) * 4); acc.x = fmaf(w11, v.x, acc.x); acc.y = fmaf(w11, v.y, acc.y); acc.z = fmaf(w11, v.z, acc.z); acc.w = fmaf(w11, v.w, acc.w); }
     }
     return acc;
 }
@@ -446,7 +481,8 @@ __device__ __forceinline__ float4 rl_sample(const Tm* __restrict__ plane, int H,
 // skips the per-tap checks and addresses the taps with 32-bit offsets (D*H*W*4 < 2^31).
 template <typename Tm>
 __device__ __forceinline__ float4 rl_sample_fast(const Tm* __restrict__ plane, int H, int W, const RLTaps& t) {
-    if (t.ok && (unsigned)t.x0 < (unsigned)(W - 1) && (unsigned)t.y0 < (unsigned)(H - 1)) {
+    if (t.ok && (unsigned)t.x0 < (unsigned)(W - 1) && (unsigned)t.y0 < (unsigned)(H - 1) &&
+        RL_IN((long long)t.y0 * W + t.x0 + W + 1, (long long)H * W)) {
         const Tm* p = plane + (unsigned)(t.y0 * W + t.x0) * 4u;
         const float4 v00 = RLStore<Tm>::load4(p), v10 = RLStore<Tm>::load4(p + 4);
         const float4 v01 = RLStore<Tm>::load4(p + 4 * W), v11 = RLStore<Tm>::load4(p + 4 * W + 4);
@@ -485,7 +521,7 @@ __device__ __forceinline__ void rl_loss_epilogue(float s, float* __restrict__ pa
                                                  int tid, int nthreads, float* red) {
     __shared__ int rl_am_last;
     if (tid == 0) {
-        partials[bid] = s;
+        if (RL_IN(bid, nblocks)) partials[bid] = s;
         rl_am_last = 0;
         if (out) {
             __threadfence();

@@ -92,8 +92,9 @@ rl_status rl_launch_select(const void* M, rl_dtype dt, const float* keys, int D,
 rl_status rl_launch_pyramid_select(const void* M, rl_dtype dt, int D, int H, int W, int level, void* Ml, int k,
                                    uint8_t* S, uint8_t* slots, float* Gzero, unsigned* counter_zero, int mode,
                                    cudaStream_t s);
-// Slot map [D][h][w] from a selection mask [h][w].
-rl_status rl_launch_mask_to_slots(const uint64_t* mask, int D, int hw, uint8_t* slots, cudaStream_t s);
+// Slot map [D][h][w] from a selection mask [h][w]: the kept planes of a pixel in ascending order
+// take slots 0 .. k-1; kept planes beyond the first k get no slot.
+rl_status rl_launch_mask_to_slots(const uint64_t* mask, int D, int k, int hw, uint8_t* slots, cudaStream_t s);
 rl_status rl_launch_downsample_f32(const float* x, int P, int H, int W, int C, int level, float* y,
                                    cudaStream_t s);
 // With Ml (level MPI) and lambda_s != 0 the sparsity prior joins the alpha step.

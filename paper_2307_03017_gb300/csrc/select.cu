@@ -132,7 +132,7 @@ __device__ __forceinline__ void write_selection(uint64_t mk, int D, int k, long 
     for (int j = 0; j < k; ++j) {
         const int d = __ffsll((long long)rem) - 1;
         rem &= rem - 1ull;
-        if (S) S[(size_t)j * hw + p] = (uint8_t)d;
+        if (S && RL_IN(d, D)) S[(size_t)j * hw + p] = (uint8_t)d;
         if (Gzero) *reinterpret_cast<float4*>(Gzero + ((size_t)j * hw + p) * 4) = make_float4(0.f, 0.f, 0.f, 0.f);
     }
 }
@@ -366,13 +366,14 @@ void launch_pyramid_select_t(const void* M, int D, int H, int W, int level, void
                                         mode, s);
 }
 
-__global__ void k_mask_to_slots(const uint64_t* __restrict__ mask, int D, int hw, uint8_t* __restrict__ slots) {
+__global__ void k_mask_to_slots(const uint64_t* __restrict__ mask, int D, int k, int hw,
+                                uint8_t* __restrict__ slots) {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= hw) return;
     const uint64_t mk = mask[p];
     int j = 0;
     for (int d = 0; d < D; ++d) {
-        const bool kept = (mk >> d) & 1ull;
+        const bool kept = ((mk >> d) & 1ull) && j < k;  // the compact gradient holds k slots
         slots[(size_t)d * hw + p] = kept ? (uint8_t)j : (uint8_t)RL_SLOT_NONE;
         j += kept;
     }
@@ -442,9 +443,9 @@ rl_status rl_launch_select_batch(const void* table, rl_dtype dt, cudaStream_t s)
     return rl_check_launch("select_batch");
 }
 
-rl_status rl_launch_mask_to_slots(const uint64_t* mask, int D, int hw, uint8_t* slots, cudaStream_t s) {
+rl_status rl_launch_mask_to_slots(const uint64_t* mask, int D, int k, int hw, uint8_t* slots, cudaStream_t s) {
     RLTraceScope ts("mask_to_slots", s);
-    k_mask_to_slots<<<(hw + 255) / 256, 256, 0, s>>>(mask, D, hw, slots);
+    k_mask_to_slots<<<(hw + 255) / 256, 256, 0, s>>>(mask, D, k, hw, slots);
     return rl_check_launch("mask_to_slots");
 }
 
@@ -455,3 +456,5 @@ rl_status rl_launch_downsample_f32(const float* x, int P, int H, int W, int C, i
     k_downsample_f32<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(x, P, H, W, C, level, y);
     return rl_check_launch("downsample");
 }
+
+RL_DEBUG_READER(select)

@@ -114,6 +114,46 @@ extern "C" rl_status reallife_selftest_wait_timeout(unsigned int wait_us, cudaSt
     return rl_check_launch("selftest_wait");
 }
 
+// Debug words of the translation units that carry bounds checks (zero in the release build).
+unsigned int rl_dbg_read_grad(int clear);
+unsigned int rl_dbg_read_pp(int clear);
+unsigned int rl_dbg_read_render(int clear);
+unsigned int rl_dbg_read_select(int clear);
+unsigned int rl_dbg_read_update(int clear);
+unsigned int rl_dbg_read_volume(int clear);
+RL_DEBUG_READER(status)
+
+#ifdef RL_DEBUG
+namespace {
+__device__ unsigned int g_rl_selftest_buf[32];
+
+// Threads 0 .. 32 each store to element i of a 32-element buffer, each behind the bounds check:
+// thread 32 fails it, sets the bounds bit and stores nothing.
+__global__ void k_selftest_bounds() {
+    const unsigned i = threadIdx.x;
+    if (i <= 32u && RL_IN(i, 32u)) g_rl_selftest_buf[i] = i;
+}
+}  // namespace
+#endif
+
+extern "C" rl_status reallife_selftest_bounds(cudaStream_t stream) {
+#ifdef RL_DEBUG
+    k_selftest_bounds<<<1, 64, 0, stream>>>();
+    return rl_check_launch("selftest_bounds");
+#else
+    (void)stream;
+    return rl_fail(RL_ENOTIMPL, "bounds checks are compiled into the debug build only");
+#endif
+}
+
+extern "C" int reallife_debug_build(void) {
+#ifdef RL_DEBUG
+    return 1;
+#else
+    return 0;
+#endif
+}
+
 extern "C" rl_status reallife_device_status(int clear, unsigned int* flags_out) {
     unsigned int* p = rl_device_status_ptr();
     if (!p) return rl_fail(RL_ECUDA, "device status word unavailable");
@@ -122,7 +162,10 @@ extern "C" rl_status reallife_device_status(int clear, unsigned int* flags_out) 
     if (e == cudaSuccess) e = cudaMemcpy(&v, p, sizeof(v), cudaMemcpyDeviceToHost);
     if (e == cudaSuccess && clear) e = cudaMemset(p, 0, sizeof(v));
     if (e != cudaSuccess) return rl_fail(RL_ECUDA, "device status: %s", cudaGetErrorString(e));
+    v |= rl_dbg_read_grad(clear) | rl_dbg_read_pp(clear) | rl_dbg_read_render(clear) | rl_dbg_read_select(clear) |
+         rl_dbg_read_update(clear) | rl_dbg_read_volume(clear) | rl_dbg_read_status(clear);
     if (flags_out) *flags_out = v;
     if (v & RL_DEVFLAG_TIMEOUT) return rl_fail(RL_ETIMEOUT, "a device-side wait timed out (flags 0x%x)", v);
+    if (v & RL_DEVFLAG_BOUNDS) return rl_fail(RL_EBOUNDS, "a bounds check of the debug build failed (flags 0x%x)", v);
     return RL_OK;
 }

@@ -31,7 +31,9 @@ __device__ __forceinline__ void update_pixel(Tm* __restrict__ M, int D, int H, i
             const float sg = a < 0.5f ? 1.f : (a > 0.5f ? -1.f : 0.f);
             g.w += prior_scale * sg / (1.5f - fabsf(0.5f - a));
         }
-        Tm* ptr = M + (((size_t)d * H + y) * W + x) * 4;
+        const size_t e = ((size_t)d * H + y) * W + x;
+        if (!RL_IN(e, (size_t)D * H * W)) continue;
+        Tm* ptr = M + e * 4;
         float4 v = RLStore<Tm>::load4_nc(ptr);
         v.x = fmaf(-lambda, g.x, v.x);
         v.y = fmaf(-lambda, g.y, v.y);
@@ -106,3 +108,5 @@ rl_status rl_launch_update_batch(const void* table, rl_dtype dt, cudaStream_t s)
     }
     return rl_check_launch("update_batch");
 }
+
+RL_DEBUG_READER(update)

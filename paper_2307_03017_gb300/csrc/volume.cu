@@ -136,6 +136,7 @@ k_volume(const Tm* __restrict__ Ml, int D, int h, int w, int level, const uint8_
             for (int c = 0; c < 4; ++c) out[(size_t)(4 * N + c) * cstride] = 0.f;
         return;
     }
+    if (!RL_IN(d, D)) return;
     float a, psv[3];
     voxel_view(A, images, iv, D, h, w, level, x, y, d, i, a, psv);
     out[(size_t)(3 * N + i) * cstride] = a;
@@ -256,3 +257,5 @@ rl_status rl_launch_volume(const void* Ml, rl_dtype dt, int D, int h, int w, int
     }
     return rl_check_launch("volume");
 }
+
+RL_DEBUG_READER(volume)

@@ -22,6 +22,7 @@ import argparse
 import hashlib
 import glob
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -63,6 +64,7 @@ def parse():
     ap.add_argument("--no-extras", action="store_true",
                     help="paper workload: skip the BF16, display and serving keys of the default line")
     ap.add_argument("--no-clocks", action="store_true")
+    ap.add_argument("--no-quality", action="store_true", help="skip the PSNR / SSIM / kept-mass report")
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--stage", choices=["hsgd", "volume", "lgd"], default="hsgd",
                     help="hsgd: refinement + renders (default); volume: gradient volumes; lgd: learned refinement")
@@ -331,6 +333,10 @@ def run_ours(args, world, rank, local):
     step_bytes = step_algorithmic_bytes(cfg, sc, elt)
     kernels = {n: {"launches": c, "ms_per_step": round(t / args.steps, 4)} for n, (c, t) in sorted(trace.items())}
 
+    qual = None
+    if rank == 0 and args.workload in ("paper", "paper_bf16", "small") and not args.no_quality:
+        qual = quality(rl, sc, k, sched, M0, mpi, out, loss, dev)
+
     launch_mode = "direct" if graph is None else "CUDA graph replay of the step"
     if graph is not None:
         del graph
@@ -356,9 +362,36 @@ def run_ours(args, world, rank, local):
             "roofline": roofline, "kernels": kernels, "gpu_launches": int(launches),
             "clocks": clk, "e2e": e2e,
         }
+        if qual is not None:
+            result["quality"] = qual
     if dist:
         dist.destroy_process_group()
     return result
+
+
+def quality(rl, sc, k, sched, M0, mpi, out, loss, dev) -> dict:
+    """Render quality of the coarse and the refined MPI on the novel views against noise-free
+    ray casts of the scene (PSNR, SSIM), the share of the reference view's alpha weight that
+    the level-0 top-k selection keeps, and the loss of each iteration of the last refinement.
+    Runs after the timed region on the refined MPI that the last step left."""
+    import numpy as np
+    import scenegen as sg
+    import torch
+    truth = np.stack([sg.raycast(sc.layers, sc.ref.K, c, sc.H, sc.W)[0] for c in sc.novel]).astype(np.float32)
+    truth = torch.from_numpy(truth).to(dev)
+    coarse = rl.make_mpi(M0, sc.near, sc.far, sc.ref)
+    res = {}
+    for name, m, r in (("coarse", coarse, rl.reallife_render(coarse, sc.novel)), ("refined", mpi, out)):
+        q = rl.reallife_image_metrics(r, truth).cpu().tolist()
+        _, mask = rl.reallife_select(m, k)
+        km = rl.reallife_kept_mass(m, mask).cpu().tolist()
+        res[name] = {"psnr_db": round(10.0 * math.log10(1.0 / q[0]), 3), "ssim": round(q[1], 5),
+                     "kept_mass": round(km[0] / km[1], 5)}
+    res["loss_per_iteration"] = [round(v, 6) for v in loss.cpu().tolist()]
+    res["levels"] = list(sched)
+    res["reference"] = (f"{len(sc.novel)} novel views against noise-free ray casts of the scene; SSIM 11x11 "
+                        "Gaussian window (sigma 1.5); kept mass = top-k alpha weight / all alpha weight at level 0")
+    return res
 
 
 def volume_kernel_bytes(sc, k: int, level: int, elt: int) -> dict:
@@ -815,7 +848,7 @@ def run_reference(args, world, rank):
 def _summary(r: dict) -> dict:
     """The keys of a secondary workload's line that the default line carries."""
     keep = ("value", "unit", "ms_per_step", "steps", "dtype", "config", "roofline", "kernels", "gpu_launches",
-            "hbm_gbs_step", "e2e")
+            "hbm_gbs_step", "e2e", "quality")
     return {k: r[k] for k in keep if k in r}
 
 

@@ -341,6 +341,32 @@ rl_status reallife_render_backward(const rl_mpi* m, const rl_camera* views, int 
  * (Eq. eq_homo inverted); NaN where the plane is not met in front of the view. */
 rl_status reallife_warp_offsets(const rl_mpi* m, const rl_camera* view, float* out, cudaStream_t stream);
 
+/* ----------------------------------------------------------------- metrics */
+
+/* Bytes of device workspace that reallife_image_metrics (N images of H x W) and
+ * reallife_kept_mass (N = 1, an H x W MPI) need; 0 for non-positive sizes. */
+size_t reallife_metrics_workspace_bytes(int N, int H, int W);
+
+/* Quality of renders (Sec. 5.1 names PSNR and SSIM): x, y device [N][H][W][3] FP32 in [0, 1].
+ * out device double[2]: out[0] = mean squared difference over all N H W 3 values (PSNR =
+ * 10 log10(1 / out[0])); out[1] = mean SSIM in the form of Wang et al. (2004): per colour
+ * channel, over every 11 x 11 window inside the image, Gaussian window weights (sigma 1.5,
+ * normalised), weighted means, variances and covariance, C1 = 0.01^2, C2 = 0.03^2, averaged
+ * over windows, channels and images.  FP32 per window, FP64 sums in a fixed order
+ * (deterministic).  ws: at least reallife_metrics_workspace_bytes(N, H, W) bytes, 8-byte
+ * aligned.  RL_EINVAL unless N >= 1 and H, W >= 11; RL_ENOMEM when ws is smaller. */
+rl_status reallife_image_metrics(const float* x, const float* y, int N, int H, int W, double* out, void* ws,
+                                 size_t ws_bytes, cudaStream_t stream);
+
+/* Kept mass of a selection (Sec. 3.3; the selection keeps the planes with the largest alpha
+ * weights A_d = alpha_d prod_{j>d} (1 - alpha_j) of Eq. eq_gradient at the reference view,
+ * formed in FP32 as the selection forms them): out device double[2] = {sum of A over the
+ * voxels whose bit d is set in mask device [H][W] uint64, sum of A over all voxels}, FP64
+ * sums in a fixed order.  The fraction out[0] / out[1] is the share of the reference view's
+ * alpha weight that the k kept planes carry.  ws as for reallife_image_metrics with N = 1. */
+rl_status reallife_kept_mass(const rl_mpi* m, const uint64_t* mask, double* out, void* ws, size_t ws_bytes,
+                             cudaStream_t stream);
+
 /* ------------------------------------------------------------------ utilities */
 
 /* Kernel family for the warp kernels (render, gradient):

@@ -25,7 +25,7 @@ __all__ = [
     "reallife_trace_enable", "reallife_trace_read", "reallife_strerror", "workspace", "library_path",
     "reallife_set_kernel_path", "reallife_device_status", "reallife_hsgd_step_noalloc",
     "reallife_trace_release_captured", "reallife_selftest_wait_timeout", "reallife_selftest_bounds",
-    "reallife_debug_build",
+    "reallife_debug_build", "reallife_metrics_workspace_bytes", "reallife_image_metrics", "reallife_kept_mass",
     "BatchItem", "BatchTable", "batch_c_item", "reallife_batch_table_bytes", "reallife_batch_prepare", "reallife_hsgd_step_batch",
 ]
 
@@ -428,6 +428,40 @@ def reallife_warp_offsets(m: Mpi, cam, stream=None) -> torch.Tensor:
     ms = m.c_struct()
     _lib.check("reallife_warp_offsets", _lib.lib().reallife_warp_offsets(
         ctypes.byref(ms), _lib.cameras([cam]), _ptr(out), _stream(stream)))
+    return out
+
+
+def reallife_metrics_workspace_bytes(N: int, H: int, W: int) -> int:
+    return int(_lib.lib().reallife_metrics_workspace_bytes(int(N), int(H), int(W)))
+
+
+def reallife_image_metrics(x: torch.Tensor, y: torch.Tensor, ws: torch.Tensor | None = None,
+                           stream=None) -> torch.Tensor:
+    """Device ``double[2]``: (mean squared difference, mean SSIM) of ``x, y [N][H][W][3]`` float32."""
+    if x.dim() != 4 or x.shape[3] != 3:
+        raise ValueError("x must be [N][H][W][3]")
+    N, H, W = (int(v) for v in x.shape[:3])
+    _check_f32(x, (N, H, W, 3), "x")
+    _check_f32(y, (N, H, W, 3), "y")
+    out = torch.empty(2, dtype=torch.float64, device=x.device)
+    if ws is None:
+        ws = torch.empty(max(reallife_metrics_workspace_bytes(N, H, W), 8), dtype=torch.uint8, device=x.device)
+    _lib.check("reallife_image_metrics", _lib.lib().reallife_image_metrics(
+        _ptr(x), _ptr(y), N, H, W, _ptr(out), _ptr(ws), ws.numel(), _stream(stream)))
+    return out
+
+
+def reallife_kept_mass(m: Mpi, mask: torch.Tensor, ws: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """Device ``double[2]``: (alpha weight of the planes kept by ``mask [H][W]`` int64, all alpha weight)."""
+    if mask.dtype != torch.int64 or tuple(mask.shape) != (m.H, m.W):
+        raise ValueError(f"mask must be int64 {(m.H, m.W)}")
+    out = torch.empty(2, dtype=torch.float64, device=m.data.device)
+    if ws is None:
+        ws = torch.empty(max(reallife_metrics_workspace_bytes(1, m.H, m.W), 8), dtype=torch.uint8,
+                         device=m.data.device)
+    ms = m.c_struct()
+    _lib.check("reallife_kept_mass", _lib.lib().reallife_kept_mass(
+        ctypes.byref(ms), _ptr(mask), _ptr(out), _ptr(ws), ws.numel(), _stream(stream)))
     return out
 
 

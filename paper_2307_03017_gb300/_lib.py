@@ -26,6 +26,7 @@ EXPORTS = [
     "reallife_lgd_step_workspace_bytes", "reallife_lgd_step", "reallife_selftest_wait_timeout",
     "reallife_batch_table_bytes", "reallife_batch_prepare", "reallife_hsgd_step_batch",
     "reallife_selftest_bounds", "reallife_debug_build",
+    "reallife_metrics_workspace_bytes", "reallife_image_metrics", "reallife_kept_mass",
 ]
 
 
@@ -111,6 +112,9 @@ def _declare(lib):
         "reallife_device_status": (c_int, [c_int, ctypes.POINTER(ctypes.c_uint)]),
         "reallife_selftest_wait_timeout": (c_int, [ctypes.c_uint, vp]),
         "reallife_selftest_bounds": (c_int, [vp]),
+        "reallife_metrics_workspace_bytes": (c_size_t, [c_int, c_int, c_int]),
+        "reallife_image_metrics": (c_int, [vp, vp, c_int, c_int, c_int, vp, vp, c_size_t, vp]),
+        "reallife_kept_mass": (c_int, [mpi_p, vp, vp, vp, c_size_t, vp]),
         "reallife_debug_build": (c_int, []),
         "reallife_last_error": (ctypes.c_char_p, []),
         "reallife_gradient_volume_workspace_bytes": (c_size_t, [c_int, c_int, c_int, c_int, c_int, c_int]),

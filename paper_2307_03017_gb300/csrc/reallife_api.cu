@@ -694,6 +694,34 @@ extern "C" rl_status reallife_warp_offsets(const rl_mpi* m, const rl_camera* vie
 
 // ------------------------------------------------------------- batched step
 
+extern "C" size_t reallife_metrics_workspace_bytes(int N, int H, int W) {
+    if (N < 1 || H < 1 || W < 1) return 0;
+    return align_up(rl_metrics_partials(N, H, W) * sizeof(double));
+}
+
+extern "C" rl_status reallife_image_metrics(const float* x, const float* y, int N, int H, int W, double* out,
+                                            void* ws, size_t ws_bytes, cudaStream_t stream) {
+    if (!x || !y || !out || N < 1 || H < 11 || W < 11 || (long long)N * H * W * 3 >= (1ll << 40))
+        return rl_fail(RL_EINVAL, "image_metrics: need x, y, out and N >= 1, H >= 11, W >= 11 (N=%d H=%d W=%d)", N, H,
+                       W);
+    if (!ws || ((uintptr_t)ws & 7) != 0) return rl_fail(RL_EINVAL, "image_metrics: workspace NULL or not 8-byte aligned");
+    const size_t need = rl_metrics_partials(N, H, W) * sizeof(double);
+    if (ws_bytes < need) return rl_fail(RL_ENOMEM, "workspace %zu bytes < %zu needed", ws_bytes, need);
+    return rl_launch_image_metrics(x, y, N, H, W, out, static_cast<double*>(ws), stream);
+}
+
+extern "C" rl_status reallife_kept_mass(const rl_mpi* m, const uint64_t* mask, double* out, void* ws, size_t ws_bytes,
+                                        cudaStream_t stream) {
+    rl_status st = check_mpi(m);
+    if (st) return st;
+    if (!mask || !out) return rl_fail(RL_EINVAL, "kept_mass: mask and out are required");
+    if (((uintptr_t)mask & 7) != 0) return rl_fail(RL_EINVAL, "kept_mass: mask must be 8-byte aligned");
+    if (!ws || ((uintptr_t)ws & 7) != 0) return rl_fail(RL_EINVAL, "kept_mass: workspace NULL or not 8-byte aligned");
+    const size_t need = rl_metrics_partials(1, m->H, m->W) * sizeof(double);
+    if (ws_bytes < need) return rl_fail(RL_ENOMEM, "workspace %zu bytes < %zu needed", ws_bytes, need);
+    return rl_launch_kept_mass(m->data, m->dtype, m->D, m->H, m->W, mask, out, static_cast<double*>(ws), stream);
+}
+
 extern "C" size_t reallife_batch_table_bytes(int max_items) {
     if (max_items < 1 || max_items > RL_BATCH_MAX_ITEMS) return 0;
     return align_up(sizeof(RLBatchHeader) + (size_t)max_items * sizeof(RLBatchItem));

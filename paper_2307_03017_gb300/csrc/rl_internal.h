@@ -134,6 +134,17 @@ inline int rl_persistent_grid(int threads, size_t smem) {
 unsigned rl_grad_batch_tiles_x(int w);
 unsigned rl_grad_batch_tiles_y(int h);
 
+// Metrics (metrics.cu): FP64 partial sums of the SSIM windows, squared differences and kept
+// mass, and the number of partials the two metric calls need.
+size_t rl_ssim_blocks(int N, int H, int W);
+size_t rl_metrics_partials(int N, int H, int W);
+// out[0] = mean squared difference, out[1] = mean SSIM of x, y [N][H][W][3] (H, W >= 11).
+rl_status rl_launch_image_metrics(const float* x, const float* y, int N, int H, int W, double* out, double* partials,
+                                  cudaStream_t s);
+// out[0] = sum of the kept alpha weights, out[1] = sum of all alpha weights.
+rl_status rl_launch_kept_mass(const void* M, rl_dtype dt, int D, int H, int W, const uint64_t* mask, double* out,
+                              double* partials, cudaStream_t s);
+
 // Alpha weights of the MPI warped into each view (Eq. eq_gradient): A device [N][D][H][W].
 rl_status rl_launch_view_alpha(const void* M, rl_dtype dt, int D, int H, int W, const RLViews& views, float* A,
                                cudaStream_t s);

@@ -99,6 +99,16 @@ def test_invalid_arguments_rejected_on_host(cpu_only):
     assert lib.reallife_hsgd_step(ctypes.byref(m), img, cams, 1, ctypes.byref(P), None, None, ws, 1 << 30, None) == 1
     P.selection, P.lambda_s = 0, -1.0
     assert lib.reallife_hsgd_step(ctypes.byref(m), img, cams, 1, ctypes.byref(P), None, None, ws, 1 << 30, None) == 1
+    # metrics: windows need 11 x 11 pixels, workspace sizing, kept mass needs a mask
+    out = ctypes.c_void_p(4096)
+    need = lib.reallife_metrics_workspace_bytes(2, 32, 40)
+    assert need >= 8 * (2 * 2 * 3 + 1024) and need % 256 == 0
+    assert lib.reallife_metrics_workspace_bytes(0, 32, 40) == 0
+    assert lib.reallife_image_metrics(img, img, 1, 10, 40, out, ws, 1 << 30, None) == 1
+    assert lib.reallife_image_metrics(img, img, 2, 32, 40, out, ws, 8 * 1024, None) == 2
+    assert lib.reallife_image_metrics(img, img, 2, 32, 40, out, ctypes.c_void_p((1 << 20) + 4), 1 << 30, None) == 1
+    assert lib.reallife_kept_mass(ctypes.byref(m), None, out, ws, 1 << 30, None) == 1
+    assert lib.reallife_kept_mass(ctypes.byref(m), ctypes.c_void_p(4096), out, ws, 8, None) == 2
 
 
 def test_learned_update_workspace_sizes():

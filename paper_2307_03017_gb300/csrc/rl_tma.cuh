@@ -1,4 +1,5 @@
-// rl_tma.cuh -- mbarrier and TMA (cp.async.bulk.tensor) helpers in inline PTX (sm_103a).
+// rl_tma.cuh -- mbarrier helpers in inline PTX (sm_103a), shared by the learned update's
+// TMA pipeline and the bounded-wait self-test.
 //
 // Every wait on an mbarrier is bounded in time; a wait that gives up returns false, and the
 // caller records RL_DEVFLAG_TIMEOUT in the device status word and stops.
@@ -46,13 +47,6 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
     while (!mbar_try_wait(bar, parity))
         if (clock64() - t0 > kWaitCycles) return false;
     return true;
-}
-
-__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y, int z) {
-    asm volatile(
-        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5}], [%2];"
-        ::"r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y), "r"(z)
-        : "memory");
 }
 
 }  // namespace rltma

@@ -138,6 +138,21 @@ def request_bytes(D, H, W, N, k, dtype) -> int:
             + _align(reallife_workspace_bytes(N, D, H, W, k, dtype)))
 
 
+def reject_oversized(requests, arena_bytes: int):
+    """Split ``requests`` into (rejected, admissible): a request whose buffers alone exceed the
+    whole arena could never be admitted and would hold up every request behind it, so it is
+    marked failed (``error`` set, done at its arrival) instead of queued."""
+    rejected, fits = [], []
+    for r in requests:
+        if request_bytes(*r.shape[:4], r.k, r.coarse.dtype) > arena_bytes:
+            r.error = "needs more device memory than the whole arena"
+            r.t_done = r.arrival
+            rejected.append(r)
+        else:
+            fits.append(r)
+    return rejected, fits
+
+
 class ServeEngine:
     """Admits requests by device memory into up to ``max_slots`` concurrent slots."""
 
@@ -250,15 +265,7 @@ class ServeEngine:
         """Serve ``requests`` (sorted by arrival, seconds).  ``realtime``: admit a request no
         earlier than its arrival time; otherwise all are available at once (closed loop)."""
         requests = sorted(requests, key=lambda r: r.arrival)
-        done = []
-        fits = []
-        for r in requests:
-            if request_bytes(*r.shape[:4], r.k, r.coarse.dtype) > self.arena.size:
-                r.error = "needs more device memory than the whole arena"
-                r.t_done = r.arrival
-                done.append(r)
-            else:
-                fits.append(r)
+        done, fits = reject_oversized(requests, self.arena.size)
         if self.batched:
             return done + self._run_batched(fits, realtime, poll_s)
         pending = collections.deque(fits)

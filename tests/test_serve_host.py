@@ -1,7 +1,7 @@
 """Host-side logic of the serving engine (no GPU): the device-memory arena allocator."""
 import pytest
 
-from paper_2307_03017_gb300.serve import DeviceArena, _align
+from paper_2307_03017_gb300.serve import DeviceArena, Request, _align, reject_oversized, request_bytes
 
 
 def test_arena_first_fit_release_and_merge():
@@ -28,3 +28,24 @@ def test_arena_views_are_aligned_typed_windows():
     v = a.view(off, (8, 16), torch.float32)
     v.fill_(2.0)
     assert v.shape == (8, 16) and float(a.buf[off:off + 4].view(torch.float32)[0]) == 2.0
+
+
+def test_oversized_requests_are_rejected_and_the_rest_kept():
+    import numpy as np
+    import torch
+    import scenegen as sg
+    cam = sg.Camera(sg.intrinsics(64, 48), np.eye(3), np.zeros(3))
+
+    def req(i, H, W, D):
+        return Request(id=i, arrival=0.01 * i, coarse=torch.zeros((D, H, W, 4)), images=torch.zeros((2, H, W, 3)),
+                       ref=cam, src=[cam, cam], near=1.0, far=10.0, schedule=(2, 1, 0))
+
+    small = request_bytes(8, 48, 64, 2, 5, torch.float32)
+    big = request_bytes(32, 384, 512, 2, 5, torch.float32)
+    arena = small * 4
+    assert big > arena
+    reqs = [req(0, 48, 64, 8), req(1, 384, 512, 32), req(2, 48, 64, 8)]
+    rejected, fits = reject_oversized(reqs, arena)
+    assert [r.id for r in rejected] == [1] and [r.id for r in fits] == [0, 2]
+    assert rejected[0].error and rejected[0].t_done == rejected[0].arrival
+    assert all(r.error is None for r in fits)

@@ -69,7 +69,8 @@ def parse():
     ap.add_argument("--stage", choices=["hsgd", "volume", "lgd"], default="hsgd",
                     help="hsgd: refinement + renders (default); volume: gradient volumes; lgd: learned refinement")
     ap.add_argument("--kernel-path", type=int, default=0,
-                    help="warp-kernel family: 0 automatic, 1 TMA windows, 2 per-pixel gather, 3/4 plane-parallel")
+                    help="warp-kernel family: 0 automatic, 2 per-pixel gather, 3-5 plane-parallel (3 and 5: 8 warps a "
+                         "block, 4: 4 warps where D <= 32)")
     return ap.parse_args()
 
 

@@ -354,7 +354,8 @@ size_t reallife_metrics_workspace_bytes(int N, int H, int W);
  * normalised), weighted means, variances and covariance, C1 = 0.01^2, C2 = 0.03^2, averaged
  * over windows, channels and images.  FP32 per window, FP64 sums in a fixed order
  * (deterministic).  ws: at least reallife_metrics_workspace_bytes(N, H, W) bytes, 8-byte
- * aligned.  RL_EINVAL unless N >= 1 and H, W >= 11; RL_ENOMEM when ws is smaller. */
+ * aligned.  RL_EINVAL unless 1 <= N <= 65535 and 11 <= H, W <= 65535; RL_ENOMEM when ws is
+ * smaller. */
 rl_status reallife_image_metrics(const float* x, const float* y, int N, int H, int W, double* out, void* ws,
                                  size_t ws_bytes, cudaStream_t stream);
 

@@ -701,9 +701,9 @@ extern "C" size_t reallife_metrics_workspace_bytes(int N, int H, int W) {
 
 extern "C" rl_status reallife_image_metrics(const float* x, const float* y, int N, int H, int W, double* out,
                                             void* ws, size_t ws_bytes, cudaStream_t stream) {
-    if (!x || !y || !out || N < 1 || H < 11 || W < 11 || (long long)N * H * W * 3 >= (1ll << 40))
-        return rl_fail(RL_EINVAL, "image_metrics: need x, y, out and N >= 1, H >= 11, W >= 11 (N=%d H=%d W=%d)", N, H,
-                       W);
+    if (!x || !y || !out || N < 1 || N > 65535 || H < 11 || W < 11 || H > 65535 || W > 65535)
+        return rl_fail(RL_EINVAL, "image_metrics: need x, y, out, 1 <= N <= 65535 and 11 <= H, W <= 65535 (N=%d H=%d "
+                       "W=%d)", N, H, W);
     if (!ws || ((uintptr_t)ws & 7) != 0) return rl_fail(RL_EINVAL, "image_metrics: workspace NULL or not 8-byte aligned");
     const size_t need = rl_metrics_partials(N, H, W) * sizeof(double);
     if (ws_bytes < need) return rl_fail(RL_ENOMEM, "workspace %zu bytes < %zu needed", ws_bytes, need);

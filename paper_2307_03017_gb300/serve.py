@@ -383,7 +383,8 @@ class ServeEngine:
         citem, keep = batch_c_item(BatchItem(mpi, images, req.src, req.k, ws, level=req.schedule[0],
                                              loss_out=loss[0:1]))
         return {"req": req, "off": off, "n": n, "M": M, "loss": loss, "citem": citem, "keep": keep,
-                "loss_ptr": loss.data_ptr(), "it": 0, "ev_in": ev, "waited": False, "lane": self._lane_of(req)}
+                "loss_ptr": loss.data_ptr(), "it": 0, "ev_in": ev, "waited": False, "ready": False,
+                "lane": self._lane_of(req)}
 
     def _step_batched(self, lane, group):
         ln = self._lane_state[lane]
@@ -451,8 +452,13 @@ class ServeEngine:
                 a["req"].slot = a["slot"]
                 active.append(a)
                 progressed = True
+            for a in active:
+                # a request joins the steps once its upload has landed, so that one large upload
+                # never holds up the other requests of its lane
+                if not a["ready"] and a["ev_in"].query():
+                    a["ready"] = True
             for lane in range(self.lanes):
-                group = [a for a in active if a["lane"] == lane]
+                group = [a for a in active if a["lane"] == lane and a["ready"]]
                 ln = self._lane_state[lane]
                 if not group or sum(1 for e in ln["ev"] if e is not None and not e.query()) >= 2:
                     continue

@@ -352,7 +352,8 @@ def run_ours(args, world, rank, local):
         result = {
             "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(total_ms / args.steps, 4), "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32" if elt == 4 else "bf16",
+            # the arithmetic is FP32 for either storage type (BF16 values are widened on load)
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic (seeded ray-cast layered scenes; no dataset)",
             "config": {"workload": f"{args.workload}: {sc.W}x{sc.H} D={sc.D} N={N} k={k} levels={list(sched)} "
                                    f"+ {len(sc.novel)} novel views", "storage": cfg["dtype"],
@@ -525,7 +526,8 @@ def run_stage(args, world, rank, local):
         result = {
             "metric": metric, "value": round(value, 3), "unit": unit, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(total_ms / args.steps, 4), "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32" if elt == 4 else "bf16",
+            # the network multiplies BF16 operands (FP32 accumulation); everything else is FP32
+            "scaling": "weak", "vs_baseline": None, "dtype": "bf16" if args.stage == "lgd" else "f32",
             "data": "synthetic (seeded ray-cast layered scenes; random network weights; no dataset)",
             "config": {"workload": f"{args.workload}: {sc.W}x{sc.H} D={sc.D} N={N} k={k} levels={list(sched)}",
                        "stage": args.stage, "storage": cfg["dtype"],
@@ -706,10 +708,10 @@ def run_serve(args, world, rank, local, pool=None):
         "queue_p50_ms": round(poisson["queue_p50_ms"], 3), "queue_p99_ms": round(poisson["queue_p99_ms"], 3),
         "reconstructions_per_s": round(poisson["reconstructions_per_s"], 2),
         "closed_loop_reconstructions_per_s": round(closed["reconstructions_per_s"], 2),
-        "dtype": "bf16", "data": "synthetic (seeded ray-cast layered scenes; no dataset)",
+        "dtype": "f32", "data": "synthetic (seeded ray-cast layered scenes; no dataset)",
         "config": {"workload": f"serve: {args.requests} requests, Poisson {args.rate}/s, res in {SERVE_RES}, "
                                f"D in {SERVE_D}, N 2-6, 2-3 iterations, k=5, BF16",
-                   "slots": args.slots, "arena_gb": args.arena_gb, "graphs": bool(args.graphs),
+                   "storage": "bf16", "slots": args.slots, "arena_gb": args.arena_gb, "graphs": bool(args.graphs),
                    "mode": args.serve_mode, "lanes": args.lanes if args.serve_mode == "batched" else None,
                    "latency": "arrival -> refined MPI and losses on the host (queueing, H2D, compute, D2H)",
                    "mean_pixels": mean_px, "scene_pool_s": round(t_gen, 1)},

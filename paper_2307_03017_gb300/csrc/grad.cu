@@ -178,8 +178,11 @@ k_grad(const Tm* __restrict__ M, int D, int H, int W, const __grid_constant__ RL
 // item, in the order of k_grad's grid), each item with its own loss epilogue over its own
 // units.  The dynamic shared memory holds `planes` planes; an item with more sets the batch bit
 // of the status word and is skipped.
+#ifndef RL_GRAD_BATCH_MIN_BLOCKS
+#define RL_GRAD_BATCH_MIN_BLOCKS 8  // the table lookups need registers: at 10 blocks the kernel spills
+#endif
 template <typename Tm>
-__global__ void __launch_bounds__(kGradThreads, RL_GRAD_MIN_BLOCKS)
+__global__ void __launch_bounds__(kGradThreads, RL_GRAD_BATCH_MIN_BLOCKS)
 k_grad_batch(const RLBatchHeader* __restrict__ hdr, const RLBatchItem* __restrict__ items, int planes) {
     extern __shared__ float sT[];  // [planes][kGradThreads]
     const unsigned n = hdr->n, total = hdr->grad_units;

@@ -111,7 +111,9 @@ __device__ __forceinline__ void grad_tile(const Tm* __restrict__ M, int D, int H
                     i2 += __ldg(px + 2);
                 }
             const float inv_area = 1.f / (float)(s * s);
-            const float e0 = c0 - i0 * inv_area, e1 = c1 - i1 * inv_area, e2 = c2 - i2 * inv_area;
+            // the image mean is rounded on its own (as the level images of the pyramid pass are)
+            const float e0 = c0 - __fmul_rn(i0, inv_area), e1 = c1 - __fmul_rn(i1, inv_area),
+                        e2 = c2 - __fmul_rn(i2, inv_area);
             lsum = fmaf(e0, e0, fmaf(e1, e1, e2 * e2));
             r0 = e0 * inv_n;
             r1 = e1 * inv_n;

@@ -376,11 +376,11 @@ size_t elt_size(rl_dtype dt) { return dt == RL_F32 ? 4 : 2; }
 size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct WsLayout {
-    size_t Ml, S, slots, G, partials, counter, total;
+    size_t Ml, S, slots, G, partials, counter, Il, total;
 };
 
 // One workspace serves every level of a schedule: level 0 has the largest selection and
-// gradient buffers, level 1 the largest downsampled MPI.
+// gradient buffers, level 1 the largest downsampled MPI and source images.
 WsLayout ws_layout(int N, int D, int H, int W, int k, rl_dtype dt) {
     WsLayout L;
     size_t off = 0;
@@ -396,6 +396,8 @@ WsLayout ws_layout(int N, int D, int H, int W, int k, rl_dtype dt) {
     off += align_up(rl_grad_num_blocks(H, W, N) * sizeof(float));
     L.counter = off;
     off += align_up(sizeof(unsigned));
+    L.Il = off;  // the level-l source images of a coarse level [N][h][w][3]
+    if (H % 2 == 0 && W % 2 == 0) off += align_up((size_t)N * (H / 2) * (W / 2) * 3 * sizeof(float));
     L.total = off;
     return L;
 }
@@ -441,16 +443,17 @@ rl_status enqueue_hsgd(rl_mpi* m, const float* images, const rl_camera* src, int
     rl_status st = make_views(m, src, N, level, views);
     if (st) return st;
     views.gplanes = k;
-    // coarse levels: the pyramid and the selection share one pass over M
+    // coarse levels: the pyramid, the level source images and the selection share one pass
+    float* Il = level ? (float*)(base + L.Il) : nullptr;
     st = level ? rl_launch_pyramid_select(m->data, m->dtype, m->D, m->H, m->W, level, Ml, k, S, slots, G, counter,
-                                          selection, s)
+                                          selection, s, images, N, Il)
                : rl_launch_select(Ml, m->dtype, nullptr, m->D, h, w, k, S, nullptr, slots, G, s, counter, selection);
     if (st) return st;
     int nb = 0;
     // the gradient kernel's last block reduces the loss partials (fixed order) into loss_out
     // (measured 1.2% faster per step than a separate reduction launch)
-    st = rl_launch_grad(Ml, m->dtype, m->D, h, w, views, true, images, level, nullptr, slots, G, 1.0f / (float)N,
-                        partials, &nb, s, loss_out, counter, 0.5f / (float)N);
+    st = rl_launch_grad(Ml, m->dtype, m->D, h, w, views, true, level ? Il : images, 0, nullptr, slots, G,
+                        1.0f / (float)N, partials, &nb, s, loss_out, counter, 0.5f / (float)N);
     if (st) return st;
     return rl_launch_update(m->data, m->dtype, m->D, m->H, m->W, level, S, G, k, lambda, clamp01, s, Ml, lambda_s);
 }

@@ -88,10 +88,12 @@ rl_status rl_launch_select(const void* M, rl_dtype dt, const float* keys, int D,
                            uint64_t* mask, uint8_t* slots, float* Gzero, cudaStream_t s,
                            unsigned* counter_zero = nullptr, int mode = 0);
 // Level-l MPI Ml [D][H>>l][W>>l][4] = Down^l(M) (level >= 1) and the selection on it in one pass: outputs as
-// rl_launch_select without the mask, identical values.
+// rl_launch_select without the mask, identical values.  With images and Il != NULL it also writes the
+// level-l source images Il [N][H>>l][W>>l][3] (2^l x 2^l means of images [N][H][W][3], formed exactly as
+// the gradient kernels form them on the fly), which the gradient then reads at img_level 0.
 rl_status rl_launch_pyramid_select(const void* M, rl_dtype dt, int D, int H, int W, int level, void* Ml, int k,
                                    uint8_t* S, uint8_t* slots, float* Gzero, unsigned* counter_zero, int mode,
-                                   cudaStream_t s);
+                                   cudaStream_t s, const float* images = nullptr, int N = 0, float* Il = nullptr);
 // Slot map [D][h][w] from a selection mask [h][w]: the kept planes of a pixel in ascending order
 // take slots 0 .. k-1; kept planes beyond the first k get no slot.
 rl_status rl_launch_mask_to_slots(const uint64_t* mask, int D, int k, int hw, uint8_t* slots, cudaStream_t s);

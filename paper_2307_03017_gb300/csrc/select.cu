@@ -232,12 +232,67 @@ __device__ __forceinline__ void pyramid_select_tile(const Tm* __restrict__ M, in
     }
 }
 
+// The level-l source images Il [N][h][w][3]: each value the mean of the 2^l x 2^l
+// full-resolution pixels, summed row by row and scaled by 1 / 4^l -- exactly what the gradient
+// kernels form on the fly from full-resolution images -- for the tile's kTile pixels.
+template <int LOG>
+__device__ __forceinline__ void level_image_means(const float* __restrict__ images, int N, int H, int W, int level,
+                                                  float* __restrict__ Il, long long p0) {
+    const int s = LOG >= 0 ? (1 << LOG) : (1 << level), h = H >> level, w = W >> level;
+    const long long hw = (long long)h * w;
+    const float inv_area = 1.f / (float)(s * s);
+    for (int i = threadIdx.x; i < N * kTile; i += blockDim.x) {
+        const int v = i / kTile;
+        const long long p = p0 + i % kTile;
+        if (p >= hw) continue;
+        const int y = (int)(p / w), x = (int)(p % w);
+        const float* img = images + (size_t)v * H * W * 3;
+        float i0 = 0.f, i1 = 0.f, i2 = 0.f;
+        if constexpr (LOG >= 0) {
+            // every load of the 4^l children issued before the first add (same sums, same order)
+            constexpr int SS = 1 << LOG;
+            float c[SS * SS * 3];
+#pragma unroll
+            for (int yy = 0; yy < SS; ++yy)
+#pragma unroll
+                for (int xx = 0; xx < SS; ++xx) {
+                    const float* px = img + ((size_t)(y * SS + yy) * W + (x * SS + xx)) * 3;
+                    c[(yy * SS + xx) * 3] = __ldg(px);
+                    c[(yy * SS + xx) * 3 + 1] = __ldg(px + 1);
+                    c[(yy * SS + xx) * 3 + 2] = __ldg(px + 2);
+                }
+#pragma unroll
+            for (int q = 0; q < SS * SS; ++q) {
+                i0 += c[q * 3];
+                i1 += c[q * 3 + 1];
+                i2 += c[q * 3 + 2];
+            }
+        } else {
+            for (int yy = 0; yy < s; ++yy)
+                for (int xx = 0; xx < s; ++xx) {
+                    const float* px = img + ((size_t)(y * s + yy) * W + (x * s + xx)) * 3;
+                    i0 += __ldg(px);
+                    i1 += __ldg(px + 1);
+                    i2 += __ldg(px + 2);
+                }
+        }
+        float* o = Il + ((size_t)v * hw + p) * 3;
+        o[0] = __fmul_rn(i0, inv_area);
+        o[1] = __fmul_rn(i1, inv_area);
+        o[2] = __fmul_rn(i2, inv_area);
+    }
+}
+
+// With Il != NULL the block also writes the tile's level images (level_image_means), so that
+// the gradient that follows reads one pixel per view instead of 4^l.
 template <typename Tm, int K, int LOG>
 __global__ void __launch_bounds__(256)
 k_pyramid_select(const Tm* __restrict__ M, int D, int H, int W, int level, Tm* __restrict__ Ml, int k,
                  uint8_t* __restrict__ S, uint8_t* __restrict__ slots, float* __restrict__ Gzero,
-                 unsigned* __restrict__ counter_zero, int mode) {
+                 unsigned* __restrict__ counter_zero, int mode, const float* __restrict__ images, int N,
+                 float* __restrict__ Il) {
     __shared__ float alpha[RL_DEV_MAX_PLANES][kTile];
+    if (Il) level_image_means<LOG>(images, N, H, W, level, Il, (long long)blockIdx.x * kTile);
     pyramid_select_tile<Tm, K, LOG>(M, D, H, W, level, Ml, k, S, slots, Gzero, counter_zero, mode,
                                     (long long)blockIdx.x * kTile, alpha);
 }
@@ -333,11 +388,13 @@ void launch_select_t(const void* M, const float* keys, int D, int h, int w, int 
 
 template <typename Tm, int LOG>
 void launch_pyramid_select_l(const Tm* M, int D, int H, int W, int level, Tm* Ml, int k, uint8_t* S,
-                             uint8_t* slots, float* Gzero, unsigned* counter_zero, int mode, cudaStream_t s) {
+                             uint8_t* slots, float* Gzero, unsigned* counter_zero, int mode, cudaStream_t s,
+                             const float* images, int N, float* Il) {
     const long long hw = (long long)(H >> level) * (W >> level);
     const unsigned blocks = (unsigned)((hw + kTile - 1) / kTile);
-#define RL_PS(KK) \
-    k_pyramid_select<Tm, KK, LOG><<<blocks, 256, 0, s>>>(M, D, H, W, level, Ml, k, S, slots, Gzero, counter_zero, mode)
+#define RL_PS(KK)                                                                                                 \
+    k_pyramid_select<Tm, KK, LOG><<<blocks, 256, 0, s>>>(M, D, H, W, level, Ml, k, S, slots, Gzero, counter_zero, mode, \
+                                                         images, N, Il)
     switch (mode == 1 ? 1 : k) {
         case 1: RL_PS(1); break;
         case 2: RL_PS(2); break;
@@ -354,16 +411,17 @@ void launch_pyramid_select_l(const Tm* M, int D, int H, int W, int level, Tm* Ml
 
 template <typename Tm>
 void launch_pyramid_select_t(const void* M, int D, int H, int W, int level, void* Ml, int k, uint8_t* S,
-                             uint8_t* slots, float* Gzero, unsigned* counter_zero, int mode, cudaStream_t s) {
+                             uint8_t* slots, float* Gzero, unsigned* counter_zero, int mode, cudaStream_t s,
+                             const float* images, int N, float* Il) {
     if (level == 1)
         launch_pyramid_select_l<Tm, 1>((const Tm*)M, D, H, W, level, (Tm*)Ml, k, S, slots, Gzero, counter_zero,
-                                       mode, s);
+                                       mode, s, images, N, Il);
     else if (level == 2)
         launch_pyramid_select_l<Tm, 2>((const Tm*)M, D, H, W, level, (Tm*)Ml, k, S, slots, Gzero, counter_zero,
-                                       mode, s);
+                                       mode, s, images, N, Il);
     else
         launch_pyramid_select_l<Tm, -1>((const Tm*)M, D, H, W, level, (Tm*)Ml, k, S, slots, Gzero, counter_zero,
-                                        mode, s);
+                                        mode, s, images, N, Il);
 }
 
 __global__ void k_mask_to_slots(const uint64_t* __restrict__ mask, int D, int k, int hw,
@@ -417,13 +475,16 @@ rl_status rl_launch_select(const void* M, rl_dtype dt, const float* keys, int D,
 
 rl_status rl_launch_pyramid_select(const void* M, rl_dtype dt, int D, int H, int W, int level, void* Ml, int k,
                                    uint8_t* S, uint8_t* slots, float* Gzero, unsigned* counter_zero, int mode,
-                                   cudaStream_t s) {
+                                   cudaStream_t s, const float* images, int N, float* Il) {
+    if (!images) Il = nullptr;
     if (dt == RL_F32) {
         RLTraceScope ts("pyramid_select_f32", s);
-        launch_pyramid_select_t<float>(M, D, H, W, level, Ml, k, S, slots, Gzero, counter_zero, mode, s);
+        launch_pyramid_select_t<float>(M, D, H, W, level, Ml, k, S, slots, Gzero, counter_zero, mode, s, images, N,
+                                       Il);
     } else {
         RLTraceScope ts("pyramid_select_bf16", s);
-        launch_pyramid_select_t<__nv_bfloat16>(M, D, H, W, level, Ml, k, S, slots, Gzero, counter_zero, mode, s);
+        launch_pyramid_select_t<__nv_bfloat16>(M, D, H, W, level, Ml, k, S, slots, Gzero, counter_zero, mode, s,
+                                               images, N, Il);
     }
     return rl_check_launch("pyramid_select");
 }

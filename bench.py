@@ -191,10 +191,11 @@ def load_scene(name: str, seed: int):
 
 def k3_algorithmic_bytes(cfg, sc, level: int, elt: int) -> int:
     """Minimal DRAM bytes of one fused warp/composite/adjoint launch at `level`:
-    read the level MPI once, the full-resolution source images once, the selection mask
-    once, write the compact gradient once."""
+    read the level MPI once, the level source images once (the full-resolution images at
+    level 0; the pyramid pass writes the coarser ones), the selection mask once, write the
+    compact gradient once."""
     h, w = sc.H >> level, sc.W >> level
-    return (sc.D * h * w * 4 * elt + cfg["N"] * sc.H * sc.W * 3 * 4 + h * w * 8 + cfg["k"] * h * w * 16)
+    return (sc.D * h * w * 4 * elt + cfg["N"] * h * w * 3 * 4 + h * w * 8 + cfg["k"] * h * w * 16)
 
 
 RENDER_VIEWS_PER_LAUNCH = 16  # RL_MAX_VIEWS: target views per render launch
@@ -210,12 +211,14 @@ def render_algorithmic_bytes(sc, elt: int, n_views: int) -> int:
 
 def step_algorithmic_bytes(cfg, sc, elt: int) -> int:
     """Minimal DRAM bytes of one step: per level-l iteration read M (select / pyramid),
-    write M_l (l > 0), the fused kernel's traffic, read-modify-write the kept k/D of M;
-    then the renders."""
+    write M_l and read the full-resolution images and write the level images (l > 0), the
+    fused kernel's traffic, read-modify-write the kept k/D of M; then the renders."""
     Mb = sc.D * sc.H * sc.W * 4 * elt
+    Ib = cfg["N"] * sc.H * sc.W * 3 * 4
     tot = 0
     for l in cfg["schedule"]:
-        tot += Mb + (Mb >> (2 * l) if l else 0) + k3_algorithmic_bytes(cfg, sc, l, elt) + 2 * cfg["k"] * Mb // sc.D
+        tot += Mb + ((Mb >> (2 * l)) + Ib + (Ib >> (2 * l)) if l else 0) + k3_algorithmic_bytes(cfg, sc, l, elt) \
+            + 2 * cfg["k"] * Mb // sc.D
     return tot + render_algorithmic_bytes(sc, elt, len(sc.novel))
 
 

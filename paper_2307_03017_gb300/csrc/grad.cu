@@ -203,7 +203,8 @@ k_grad_batch(const RLBatchHeader* __restrict__ hdr, const RLBatchItem* __restric
         const int h = it.H >> it.level, w = it.W >> it.level;
 #define RL_GB(A) grad_tile<Tm, true, true, A>(static_cast<const Tm*>(it.Ml), it.D, h, w, it.views, (int)view,    \
                                              tx * kGradBX + threadIdx.x, ty * kGradBY + threadIdx.y, tid, sT,       \
-                                             it.images, it.level, nullptr, it.slots, it.G, it.inv_n, it.partials,   \
+                                             it.level ? it.Il : it.images, 0, nullptr, it.slots, it.G, it.inv_n,    \
+                                             it.partials,                                                           \
                                              local, it.grad_units, it.loss_out, it.counter, it.loss_scale)
         if (it.views.anchored) RL_GB(true);
         else RL_GB(false);

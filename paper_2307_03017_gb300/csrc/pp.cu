@@ -333,7 +333,8 @@ k_grad_pp_batch(const RLBatchHeader* __restrict__ hdr, const RLBatchItem* __rest
         const PixelCoord pc =
             pixel_coord_at(h, w, (int)view, (int)(tile % it.pp_tiles_x), (int)(tile / it.pp_tiles_x));
         const Tm* Ml = static_cast<const Tm*>(it.Ml);
-#define RL_PPB(CC, A) grad_pp_tile<Tm, CC, 8, true, true, A>(Ml, it.D, h, w, it.views, pc, it.images, it.level,   \
+#define RL_PPB(CC, A) grad_pp_tile<Tm, CC, 8, true, true, A>(Ml, it.D, h, w, it.views, pc,                       \
+                                                             it.level ? it.Il : it.images, 0,                       \
                                                              nullptr, it.slots, it.G, it.inv_n, it.partials, local, \
                                                              it.pp_units, it.loss_out, it.counter, it.loss_scale,   \
                                                              xch, red)

@@ -773,6 +773,7 @@ extern "C" rl_status reallife_batch_prepare(const rl_batch_item* items, int n, v
         it.M = m->data;
         it.Ml = l == 0 ? m->data : (void*)(base + L.Ml);
         it.images = b.images;
+        it.Il = l == 0 ? nullptr : (float*)(base + L.Il);
         it.S = (uint8_t*)(base + L.S);
         it.slots = (uint8_t*)(base + L.slots);
         it.G = (float*)(base + L.G);

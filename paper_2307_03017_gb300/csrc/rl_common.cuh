@@ -120,6 +120,7 @@ struct RLBatchItem {
     float* partials;         // loss partials, one per gradient unit
     unsigned* counter;       // last-block counter of the loss epilogue
     float* loss_out;         // device [1] or NULL
+    float* Il;               // level-l source images [N][h][w][3] (levels >= 1; written by the selection)
     int D, H, W, level, k, mode, clamp01, N;
     float lambda, prior_scale, inv_n, loss_scale;
     unsigned sel_begin, sel_units;    // first unit and unit count of each stage

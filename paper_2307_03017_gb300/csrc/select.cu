@@ -355,9 +355,9 @@ k_select_batch(const RLBatchHeader* __restrict__ hdr, const RLBatchItem* __restr
     else                                                                                                           \
         pyramid_select_tile<Tm, 8, LL>(M, it.D, it.H, it.W, it.level, Ml, it.k, it.S, it.slots, it.G, it.counter,     \
                                        it.mode, local * kTile, alpha)
-            if (it.level == 1) { RL_PSB(1); }
-            else if (it.level == 2) { RL_PSB(2); }
-            else { RL_PSB(-1); }
+            if (it.level == 1) { level_image_means<1>(it.images, it.N, it.H, it.W, 1, it.Il, local * kTile); RL_PSB(1); }
+            else if (it.level == 2) { level_image_means<2>(it.images, it.N, it.H, it.W, 2, it.Il, local * kTile); RL_PSB(2); }
+            else { level_image_means<-1>(it.images, it.N, it.H, it.W, it.level, it.Il, local * kTile); RL_PSB(-1); }
 #undef RL_PSB
         }
         __syncthreads();  // alpha is reused by the next unit

@@ -185,6 +185,18 @@ __device__ __forceinline__ void grad_pp_tile(const Tm* __restrict__ M, int D, in
     const RLPixWarp<ANCH> w = rl_pix_warp<ANCH>(sA, views.v[pc.view], qx, qy);
     const size_t plane = (size_t)H * W * 4;
 
+    // a level image that is already averaged (img_level 0: one pixel a view) is read by one warp
+    // before its gathers and handed to the others through shared memory at the chunk exchange
+    __shared__ float ximg[kPix][3];
+    const bool img_early = LOSS && img_level == 0;
+    float li0 = 0.f, li1 = 0.f, li2 = 0.f;
+    if (img_early && pc.g == kGroups - 1 && pc.active) {
+        const float* px = images + (((size_t)pc.view * H + pc.qy) * W + pc.qx) * 3;
+        li0 = __ldg(px);
+        li1 = __ldg(px + 1);
+        li2 = __ldg(px + 2);
+    }
+
     // forward over this thread's chunk, nearest plane first; samples stay in registers
     float4 m[C];
     float Tloc[C];
@@ -205,6 +217,11 @@ __device__ __forceinline__ void grad_pp_tile(const Tm* __restrict__ M, int D, in
         }
     }
     xch[pc.g][pc.lane] = make_float4(c0, c1, c2, Tl);
+    if (img_early && pc.g == kGroups - 1) {
+        ximg[pc.lane][0] = li0;
+        ximg[pc.lane][1] = li1;
+        ximg[pc.lane][2] = li2;
+    }
     __syncthreads();
     // combine the chunks: pixel colour, transmittance in front of this chunk and the
     // composite of everything behind it
@@ -235,13 +252,19 @@ __device__ __forceinline__ void grad_pp_tile(const Tm* __restrict__ M, int D, in
             const int Wf = W << img_level, Hf = H << img_level;
             const float* img = images + (size_t)pc.view * Hf * Wf * 3;
             float i0 = 0.f, i1 = 0.f, i2 = 0.f;
-            for (int yy = 0; yy < s; ++yy)
-                for (int xx = 0; xx < s; ++xx) {
-                    const float* px = img + ((size_t)(pc.qy * s + yy) * Wf + (pc.qx * s + xx)) * 3;
-                    i0 += __ldg(px);
-                    i1 += __ldg(px + 1);
-                    i2 += __ldg(px + 2);
-                }
+            if (img_early) {
+                i0 = ximg[pc.lane][0];
+                i1 = ximg[pc.lane][1];
+                i2 = ximg[pc.lane][2];
+            } else {
+                for (int yy = 0; yy < s; ++yy)
+                    for (int xx = 0; xx < s; ++xx) {
+                        const float* px = img + ((size_t)(pc.qy * s + yy) * Wf + (pc.qx * s + xx)) * 3;
+                        i0 += __ldg(px);
+                        i1 += __ldg(px + 1);
+                        i2 += __ldg(px + 2);
+                    }
+            }
             const float inv_area = 1.f / (float)(s * s);
             // the image mean is rounded on its own (as the level images of the pyramid pass are)
             const float e0 = C0 - __fmul_rn(i0, inv_area), e1 = C1 - __fmul_rn(i1, inv_area),
@@ -299,7 +322,7 @@ __device__ __forceinline__ void grad_pp_tile(const Tm* __restrict__ M, int D, in
 }
 
 template <typename Tm, int C, int kGroups, bool SPARSE, bool LOSS, bool ANCH>
-__global__ void __launch_bounds__(kGroups * kPix)
+__global__ void __launch_bounds__(kGroups * kPix, C <= 4 ? 1024 / (kGroups * kPix) : 1)
 k_grad_pp(const Tm* __restrict__ M, int D, int H, int W, const __grid_constant__ RLViews views, int tiles_x,
           const float* __restrict__ images, int img_level, const float* __restrict__ grad_out,
           const uint8_t* __restrict__ slots, float* __restrict__ G, float inv_n, float* __restrict__ partials,

@@ -4,7 +4,9 @@
 // Per view pixel q (one thread), with T_d = prod_{j>d}(1 - alpha_j) (Eq. eq_over):
 //   pass 1, d = D-1 .. 0:  m_d = bilinear(M[d], p_d(q)); T_d -> shared memory;
 //                           C += T_d alpha_d c_d; T *= (1 - alpha_d)
-//   residual:               r = (C - I(q)) / N  (loss mode; L = 1/(2N) sum |C - I|^2)
+//   residual:               r = (C - I(q)) / N  (loss mode; L = 1/(2N) sum |C - I|^2; I the
+//                           level image: given at the level's resolution, img_level 0, or formed
+//                           on the fly from its 2^l x 2^l full-resolution pixels)
 //                           or r = dL/dC given by the caller (backward mode)
 //   pass 2, d = 0 .. D-1:  dL/dc_d = T_d alpha_d r;  dL/dalpha_d = T_d <c_d - B_d, r>,
 //                           B_d the composite of the planes below d (B_0 = 0,

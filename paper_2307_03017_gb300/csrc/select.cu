@@ -18,6 +18,8 @@
 // (ties to the lower d), shifted to stay within [0, D).
 // On the coarse levels of an HSGD step the pyramid and the selection run as one kernel: the
 // level voxels of a tile of pixels go to Ml and, through shared memory, to the selection.
+// The same pass writes the level source images (2^l x 2^l means of the full-resolution
+// images) that the gradient of that level reads, one pixel a view.
 #include <type_traits>
 
 #include "rl_internal.h"

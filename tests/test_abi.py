@@ -182,3 +182,28 @@ def test_batch_table_sizes_and_validation(cpu_only):
     # a table that reallife_batch_prepare did not write is refused before anything is enqueued
     blank = (ctypes.c_uint8 * tb)()
     assert lib.reallife_hsgd_step_batch(blank, ctypes.c_void_p(1 << 20), tb, None) == 1
+
+
+def test_header_is_plain_c(tmp_path):
+    """include/reallife.h is a C header: a C11 translation unit that includes it and names its
+    types and entry points compiles with gcc (no C++ in the interface)."""
+    import shutil
+    import subprocess
+    gcc = shutil.which("gcc")
+    cuda_inc = next((d for d in ("/usr/local/cuda/include", os.path.join(os.environ.get("CUDA_HOME", ""), "include"))
+                     if d and os.path.exists(os.path.join(d, "cuda_runtime_api.h"))), None)
+    if not gcc or not cuda_inc:
+        pytest.skip("gcc or the CUDA headers are not available")
+    src = tmp_path / "use_header.c"
+    src.write_text(
+        '#include "reallife.h"\n'
+        "int main(void) {\n"
+        "    rl_mpi m; rl_camera c; rl_hsgd_params p; rl_batch_item b; rl_status s = RL_EBOUNDS;\n"
+        "    (void)m; (void)c; (void)p; (void)b; (void)s;\n"
+        "    rl_status (*render)(const rl_mpi*, const rl_camera*, int, float*, cudaStream_t) = reallife_render;\n"
+        "    (void)render;\n"
+        "    return (int)(reallife_workspace_bytes(1, 1, 2, 2, 1, RL_F32) == 0);\n"
+        "}\n")
+    r = subprocess.run([gcc, "-std=c11", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"), "-I", cuda_inc,
+                        "-c", str(src), "-o", str(tmp_path / "use_header.o")], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr

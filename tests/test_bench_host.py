@@ -45,3 +45,15 @@ def test_reference_arm_prints_one_json_line():
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
     assert d["cpu_baseline"]["value"] == d["value"]
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+
+
+def test_default_launch_mode_and_traced_steps(monkeypatch):
+    """No flags: the step is replayed as a CUDA graph and the per-kernel events are recorded on
+    every 10th timed step; --direct and --trace-every change both."""
+    b = _bench()
+    monkeypatch.setattr(sys, "argv", ["bench.py"])
+    a = b.parse()
+    assert a.graph and not a.direct and a.trace_every == 10 and a.steps >= 20 and a.warmup >= 3
+    monkeypatch.setattr(sys, "argv", ["bench.py", "--direct", "--trace-every", "1"])
+    a = b.parse()
+    assert not a.graph and a.trace_every == 1

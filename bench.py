@@ -228,6 +228,29 @@ def step_algorithmic_bytes(cfg, sc, elt: int) -> int:
     return tot + render_algorithmic_bytes(sc, elt, len(sc.novel))
 
 
+def kernel_algorithmic_bytes(cfg, sc, elt: int) -> dict:
+    """Minimal DRAM bytes per step of each kernel family of the step (the trace names' prefixes):
+    the fused gradient (all levels), the renders, the coarse pyramid + selection passes (read M
+    and the full-resolution images, write M_l, the level images, S, the slot map and the zeroed
+    compact gradient), the level-0 selection (read M, write S, the slot map and the zeroed compact
+    gradient) and the masked updates (read-modify-write the kept k/D of M, read G_s and S)."""
+    Mb = sc.D * sc.H * sc.W * 4 * elt
+    Ib = cfg["N"] * sc.H * sc.W * 3 * 4
+    k, D = cfg["k"], sc.D
+    out = {"grad": 0, "render": render_algorithmic_bytes(sc, elt, len(sc.novel)), "pyramid_select": 0, "select": 0,
+           "update": 0}
+    for l in cfg["schedule"]:
+        hw = (sc.H >> l) * (sc.W >> l)
+        out["grad"] += k3_algorithmic_bytes(cfg, sc, l, elt)
+        sel = k * hw + D * hw + 16 * k * hw
+        if l:
+            out["pyramid_select"] += Mb + (Mb >> (2 * l)) + Ib + (Ib >> (2 * l)) + sel
+        else:
+            out["select"] += Mb + sel
+        out["update"] += 2 * k * Mb // D + 16 * k * hw + k * hw
+    return out
+
+
 def run_ours(args, world, rank, local):
     import torch
     import paper_2307_03017_gb300 as rl
@@ -352,6 +375,16 @@ def run_ours(args, world, rank, local):
                 "avg_launch_us": round(dom_ms / dom_n * 1e3, 2), "peak_source": peak_src}
     step_bytes = step_algorithmic_bytes(cfg, sc, elt)
     kernels = {n: {"launches": c, "ms_per_step": round(t / n_traced, 4)} for n, (c, t) in sorted(trace.items())}
+    # per-kernel useful bandwidth: algorithmic bytes per step over the traced steps' time
+    fam_bytes = kernel_algorithmic_bytes(cfg, sc, elt)
+    for n, kd in kernels.items():
+        fam = next((f for f in ("pyramid_select", "select", "grad", "render", "update") if n.startswith(f)), None)
+        if fam and kd["ms_per_step"] > 0:
+            gbs = fam_bytes[fam] / (kd["ms_per_step"] / 1e3) / 1e9
+            kd["alg_gbs"] = round(gbs, 1)
+            kd["alg_frac"] = round(gbs / peak_gbs, 4)
+    render_ms = sum(kd["ms_per_step"] for n, kd in kernels.items() if n.startswith("render"))
+    render_views_per_s = round(len(sc.novel) / (render_ms / 1e3), 1) if render_ms > 0 else None
 
     qual = None
     if rank == 0 and args.workload in ("paper", "paper_bf16", "small") and not args.no_quality:
@@ -382,6 +415,7 @@ def run_ours(args, world, rank, local):
                                 f"{every}th); kernels' ms_per_step and launches are theirs",
                        "l2": "flushed (512 MB write) before every timed step", "parallelism": f"replicas{world}"},
             "hbm_gbs_step": round(step_bytes / (total_ms / args.steps / 1e3) / 1e9, 1),
+            "render_views_per_s": render_views_per_s,
             "roofline": roofline, "kernels": kernels, "gpu_launches": int(launches),
             "clocks": clk, "e2e": e2e,
         }
@@ -876,7 +910,7 @@ def run_reference(args, world, rank):
 def _summary(r: dict) -> dict:
     """The keys of a secondary workload's line that the default line carries."""
     keep = ("value", "unit", "ms_per_step", "steps", "dtype", "config", "roofline", "kernels", "gpu_launches",
-            "hbm_gbs_step", "e2e", "quality")
+            "hbm_gbs_step", "render_views_per_s", "e2e", "quality")
     return {k: r[k] for k in keep if k in r}
 
 

@@ -290,23 +290,34 @@ def run_ours(args, world, rank, local):
     traced = lambda i: i % every == 0  # steps whose kernels are bracketed by CUDA events
     n_traced = sum(1 for i in range(args.steps) if traced(i))
     graph = graph_plain = None
+    capture_error = None
     if args.graph:
         # one step captured as a CUDA graph with the tracer's event nodes around each kernel, and
-        # one without them for the untraced steps
-        rl.reallife_trace_enable(True)
-        graph = torch.cuda.CUDAGraph()
-        with torch.cuda.graph(graph):
-            step()
-        rl.reallife_trace_enable(False)
-        graph_plain = torch.cuda.CUDAGraph()
-        with torch.cuda.graph(graph_plain):
-            step()
-        rl.reallife_trace_read()
-        for g in (graph, graph_plain):  # first replays (untimed)
-            M.copy_(M0)
-            g.replay()
-        torch.cuda.synchronize()
-        rl.reallife_trace_read()
+        # one without them for the untraced steps.  Only this thread's CUDA calls are checked
+        # during capture (other threads of the process, such as a process group's watchdog, may
+        # keep polling); should capture fail all the same, the steps are launched directly.
+        try:
+            rl.reallife_trace_enable(True)
+            graph = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(graph, capture_error_mode="thread_local"):
+                step()
+            rl.reallife_trace_enable(False)
+            graph_plain = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(graph_plain, capture_error_mode="thread_local"):
+                step()
+            rl.reallife_trace_read()
+            for g in (graph, graph_plain):  # first replays (untimed)
+                M.copy_(M0)
+                g.replay()
+            torch.cuda.synchronize()
+            rl.reallife_trace_read()
+        except Exception as e:  # noqa: BLE001 -- any capture failure falls back to direct launches
+            rl.reallife_trace_enable(False)
+            graph = graph_plain = None
+            capture_error = (str(e).splitlines() or [type(e).__name__])[0][:200]
+            torch.cuda.synchronize()
+            rl.reallife_trace_read()
+            rl.reallife_trace_release_captured()
 
     clocks = ClockSampler(local) if not args.no_clocks else None
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
@@ -390,7 +401,8 @@ def run_ours(args, world, rank, local):
     if rank == 0 and args.workload in ("paper", "paper_bf16", "small") and not args.no_quality:
         qual = quality(rl, sc, k, sched, M0, mpi, out, loss, dev)
 
-    launch_mode = "direct" if graph is None else "CUDA graph replay of the step"
+    launch_mode = "CUDA graph replay of the step" if graph is not None else (
+        f"direct (graph capture failed: {capture_error})" if capture_error else "direct")
     if graph is not None:
         del graph, graph_plain
         torch.cuda.synchronize()
